@@ -1,0 +1,345 @@
+"""Benchmark of the matrix-free operator apply on one macro-tetrahedron at level 8.
+
+Workload (synthetic, seeded): the reference macro-tetrahedron refined to
+level 8 (2,862,209 P1 / 22,632,705 P2 points), variable coefficient
+k(x) = 1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z) at quadrature points
+(4-point degree-2 rule for P1, 14-point rule for P2), zero Dirichlet
+boundary, x ~ U[-1, 1] from seed 0, FP64 and FP32 applies.  One step applies
+every leg once; each apply runs after an L2 flush (a 512 MB write), timed with
+CUDA events on the launching stream.  Metric: updated (interior) DoFs per
+second over the whole step, in MDoF/s.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (the apply of one mesh
+needs no data from other GPUs); value = DoFs of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "operator apply MDoF/s & % HBM roofline; FMG time-to-1e-10 residual, FP32-mixed vs FP64"
+LEVEL = 8
+
+# (name, degree, coefficient, quad_degree, dtype)
+LEGS = [
+    ("p1_sin3_f64", 1, ("sin3",), 2, "f64"),
+    ("p1_sin3_f32", 1, ("sin3",), 2, "f32"),
+    ("p2_sin3_f64", 2, ("sin3",), 4, "f64"),
+    ("p2_sin3_f32", 2, ("sin3",), 4, "f32"),
+]
+# Legs that stand in while a kernel of the list above is not built yet.
+FALLBACK_LEGS = {
+    "p1_sin3_f64": ("p1_const_f64", 1, ("const", 1.0), 2, "f64"),
+    "p1_sin3_f32": ("p1_const_f32", 1, ("const", 1.0), 2, "f32"),
+}
+
+# Algorithmic FLOPs per micro-tet of each apply variant ("algorithmic work").
+def flops_per_unit(name: str, degree: int, nq: int):
+    if name.startswith("p1_const"):
+        return ("dof", 30.0)                       # 15-point stencil: 15 FMA per point
+    if name.startswith("p1_sin3"):
+        return ("tet", 2.0 * (nq * 8 + 16))        # k at nq points + 4x4 scaled apply
+    if name.startswith("p2_const"):
+        return ("tet", 2.0 * 100)
+    if name.startswith("p2_sin3"):
+        return ("tet", 2.0 * nq * (30 + 10 + 30 + 8))
+    return ("dof", 0.0)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# FP64 / FP32 FMA-chain rates measured on this GPU type (see profiles/alu_peaks.md)
+ALU_PEAK_TFLOPS = {"f64": 1.01, "f32": 73.1}
+
+
+def load_traffic():
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(seconds_budget: float = 20.0):
+    """The oracle as it stands on the host: element-by-element CSR assembly + SpMV (FP64, 1 thread).
+
+    Bounded sample: the same macro and coefficients at level 6 (P1) and
+    level 5 (P2); MDoF/s of one apply = interior DoFs / SpMV time, plus the
+    assembly time per DoF reported separately.
+    """
+    import workloads as W
+    from oracle import assemble as OA, mesh as OM
+    v, t = W.reference_tet()
+    mm = OM.MacroMesh(v, t)
+    res = {}
+    tot_dofs, tot_spmv, tot_asm = 0, 0.0, 0.0
+    for name, degree, level, qd in [("p1_sin3", 1, 6, 2), ("p2_sin3", 2, 5, 4)]:
+        t0 = time.perf_counter()
+        S = OA.Space(mm, level, degree)
+        A = OA.diffusion_matrix(S, ("sin3",), qd, "dirichlet")
+        t_asm = time.perf_counter() - t0
+        x = W.uniform(S.ndof, seed=0)
+        reps = 0
+        t0 = time.perf_counter()
+        while True:
+            A @ x
+            reps += 1
+            if time.perf_counter() - t0 > 1.0 and reps >= 3:
+                break
+        t_spmv = (time.perf_counter() - t0) / reps
+        nint = int(S.interior.sum())
+        res[name] = {"level": level, "dofs": nint, "spmv_mdofs": nint / t_spmv / 1e6,
+                     "assembly_s": t_asm, "assembly_plus_spmv_mdofs": nint / (t_asm + t_spmv) / 1e6}
+        tot_dofs += nint
+        tot_spmv += t_spmv
+        tot_asm += t_asm
+    return {"value": tot_dofs / tot_spmv / 1e6, "unit": "MDoF/s", "cores": 1, "kind": "oracle",
+            "sample": "reference macro, P1 sin3 at level 6 + P2 sin3 at level 5, FP64 CSR SpMV (assembly timed "
+                      "separately: %.1f s)" % tot_asm,
+            "legs": res}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    times = []
+    cb = None
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline()
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MDoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "reference macro-tetrahedron, variable-coefficient P1/P2 diffusion (bounded "
+                                   "sample of the level-8 workload: P1 level 6, P2 level 5)"},
+            "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample", "value", "unit")},
+            "e2e": {"value": cb["value"], "unit": "MDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hhg", choices=["hhg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import workloads as W
+    import paper_2404_08371_gb300 as hhg
+    from paper_2404_08371_gb300 import _lib
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    v, t = W.reference_tet()
+    mesh = hhg.Mesh(v, t, LEVEL)
+    legs = []
+    for leg in LEGS:
+        name, degree, coeff, qd, dt = leg
+        try:
+            op = hhg.Operator(mesh, degree=degree, coeff=coeff, bc="dirichlet", quad_degree=qd)
+            x0 = torch.empty(mesh.vec_size(degree), dtype=torch.float64, device=dev)
+            x0.copy_(torch.from_numpy(W.uniform(mesh.vec_size(degree), seed=0)))
+            x = x0 if dt == "f64" else x0.float()
+            op.apply(x)
+            torch.cuda.synchronize()
+        except _lib.HHGError as e:
+            if e.code != _lib.HHG_E_UNSUPPORTED or name not in FALLBACK_LEGS:
+                raise
+            name, degree, coeff, qd, dt = FALLBACK_LEGS[name]
+            op = hhg.Operator(mesh, degree=degree, coeff=coeff, bc="dirichlet", quad_degree=qd)
+            x0 = torch.from_numpy(W.uniform(mesh.vec_size(degree), seed=0)).to(dev)
+            x = x0 if dt == "f64" else x0.float()
+        y = torch.empty_like(x)
+        tot, inner = mesh.dof_count(degree)
+        legs.append({"name": name, "op": op, "x": x, "y": y, "dofs": inner, "npts": x.numel(),
+                     "esize": x.element_size(), "dt": dt, "degree": degree,
+                     "nq": 4 if qd == 2 else 14, "ms": []})
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def run_step(record: bool):
+        for L in legs:
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L["op"].apply(L["x"], out=L["y"])
+            e1.record(stream)
+            if record:
+                L["ev"].append((e0, e1))
+
+    for L in legs:
+        L["ev"] = []
+    for _ in range(args.warmup):
+        run_step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        run_step(True)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = 0.0
+    for L in legs:
+        L["ms"] = [a.elapsed_time(b) for a, b in L["ev"]]
+        step_ms += sum(L["ms"]) / args.steps
+    t_step = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
+    step_ms = float(t_step.item())
+    dofs_step = sum(L["dofs"] for L in legs)
+    value = world * dofs_step / (step_ms * 1e-3) / 1e6
+
+    # end to end through the C-ABI with host buffers: pinned H2D of x, apply, D2H of y
+    h2d = d2h = 0
+    for L in legs:
+        L["hx"] = L["x"].cpu().pin_memory()
+        L["hy"] = torch.empty_like(L["hx"]).pin_memory()
+        h2d += L["hx"].numel() * L["esize"]
+        d2h += L["hy"].numel() * L["esize"]
+    e2e_ms = []
+    for s in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for L in legs:
+            L["x"].copy_(L["hx"], non_blocking=True)
+            L["op"].apply(L["x"], out=L["y"])
+            L["hy"].copy_(L["y"], non_blocking=True)
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = world * dofs_step / (statistics.mean(e2e_ms) * 1e-3) / 1e6
+
+    peaks = load_peaks()
+    traffic = load_traffic()
+    details = {}
+    dom = None
+    for L in legs:
+        ms = statistics.mean(L["ms"])
+        nbytes = 2 * L["npts"] * L["esize"]          # read x, write y (algorithmic minimum)
+        unit, fpu = flops_per_unit(L["name"], L["degree"], L["nq"])
+        ntets = 8 ** LEVEL
+        flops = fpu * (L["dofs"] if unit == "dof" else ntets)
+        d = {"ms": ms, "mdofs": L["dofs"] / (ms * 1e-3) / 1e6, "gbs": nbytes / (ms * 1e-3) / 1e9,
+             "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+             "tflops": flops / (ms * 1e-3) / 1e12,
+             "alu_frac": flops / (ms * 1e-3) / 1e12 / ALU_PEAK_TFLOPS[L["dt"]],
+             "dofs": L["dofs"], "bytes": nbytes, "flops": flops}
+        details[L["name"]] = d
+        if dom is None or ms > details[dom]["ms"]:
+            dom = L["name"]
+    D = details[dom]
+    dom_leg = [L for L in legs if L["name"] == dom][0]
+    if D["alu_frac"] > D["hbm_frac"]:
+        roof = {"bound": "alu", "achieved": D["tflops"], "peak": ALU_PEAK_TFLOPS[dom_leg["dt"]], "unit": "TFLOP/s",
+                "frac": D["alu_frac"], "peak_src": "measured FMA-chain rate (profiles/alu_peaks.md)"}
+    else:
+        roof = {"bound": "hbm", "achieved": D["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": D["hbm_frac"],
+                "peak_src": peaks["src"] + " (burst copy)"}
+    tr = traffic.get(dom)
+    roof["traffic"] = tr["bytes_per_launch"] if tr else None
+    roof["kernel"] = dom
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+    launches = sum(1 for _ in legs) * args.steps   # one kernel per apply on a single macro
+    line = {"metric": METRIC, "value": value, "unit": "MDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "+".join(sorted({L["dt"] for L in legs})), "data": "synthetic",
+            "config": {"workload": "reference macro-tetrahedron at level %d, legs: %s" % (
+                LEVEL, ", ".join(L["name"] for L in legs)), "level": LEVEL, "bc": "dirichlet",
+                "l2": "flushed before every apply (512 MB write)", "parallelism": "replicas" if world > 1 else "1gpu"},
+            "legs": details, "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "MDoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk, "wall_s_timed": wall}
+    if cb is not None:
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"]["legs"] = cb["legs"]
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

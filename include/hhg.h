@@ -1,0 +1,225 @@
+/*
+ * hhg.h -- C interface of the GB300 matrix-free finite-element library for
+ * hybrid tetrahedral grids (Boehm et al., "Code Generation and Performance
+ * Engineering for Matrix-Free Finite Element Methods on Hybrid Tetrahedral
+ * Grids").
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Status: every call returns HHG_OK (0) or a negative HHG_E_* code;
+ *   hhg_last_error() then gives a message (per calling thread).  A failed
+ *   call leaves its outputs unspecified but the handles valid.
+ * Handles: hhg_mesh_t and hhg_op_t are opaque, owned by the library, freed
+ *   by their *_destroy call.  A mesh must outlive the operators made on it.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Unless stated otherwise a call only enqueues work on that
+ *   stream and returns; its device outputs are ready when the stream is.
+ * Vectors: device pointers owned by the caller, contiguous, of dtype
+ *   HHG_F32 (float) or HHG_F64 (double) as the call's `dtype` says.  The
+ *   library never keeps a vector pointer beyond the call (coefficient fields
+ *   are the one exception, see hhg_coeff_t).
+ *
+ * Packed vector layout ("level l, degree p")
+ * ------------------------------------------
+ * Each macro-tetrahedron (P0,P1,P2,P3) refined l times has n = 2^l intervals
+ * per edge (Section 2).  A degree-p vector stores, for macro 0, 1, ..., all
+ * lattice points (i,j,k), i,j,k >= 0, i+j+k <= N with N = p*n (P2 nodes are
+ * the vertices of the grid refined once more), at position
+ *     macro*V(N) + V(N) - V(N-k) + j*(N-k+1) - j*(j-1)/2 + i,
+ *     V(s) = (s+1)(s+2)(s+3)/6,
+ * i.e. k slowest, i fastest.  Point (i,j,k) sits at P0 + (i/N)(P1-P0) +
+ * (j/N)(P2-P0) + (k/N)(P3-P0).  Points on faces, edges and vertices of a
+ * macro are stored once per macro containing them; a vector is
+ * "consistent" when all copies of a point hold the same value.  Inputs
+ * must be consistent and outputs are consistent.  Vector-valued fields
+ * (HHG_EPSILON) store 3 components per point, and a batch of nrhs vectors
+ * stores the batch index fastest: element ((point*ncomp + c)*nrhs + r).
+ *
+ * Boundary conditions: HHG_DIRICHLET applies A_D = [[A_II, 0], [0, I]] --
+ * rows of interior points use interior columns only and boundary rows return
+ * their input; HHG_NEUMANN applies the full matrix.  Boundary points are the
+ * points on macro faces that belong to exactly one macro.
+ */
+#ifndef HHG_H
+#define HHG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HHG_OK 0
+#define HHG_E_ARG (-1)           /* invalid argument: null pointer, size, enum out of range */
+#define HHG_E_DEGENERATE (-2)    /* a macro-tetrahedron has (numerically) zero volume */
+#define HHG_E_NONMANIFOLD (-3)   /* a macro face is shared by more than two macros */
+#define HHG_E_OOM (-4)           /* host or device allocation failed */
+#define HHG_E_CUDA (-5)          /* a CUDA call or a kernel launch failed */
+#define HHG_E_NOT_CONVERGED (-6) /* mg_solve reached max_iters above its tolerance */
+#define HHG_E_NAN (-7)           /* a NaN or Inf appeared in a residual norm */
+#define HHG_E_UNSUPPORTED (-8)   /* valid but not implemented combination */
+
+enum { HHG_F32 = 0, HHG_F64 = 1 };
+enum { HHG_DIFFUSION = 0, HHG_EPSILON = 1 };
+enum { HHG_DIRICHLET = 0, HHG_NEUMANN = 1 };
+enum {
+  HHG_COEFF_CONST = 0,    /* k(x) = value */
+  HHG_COEFF_SIN3 = 1,     /* k(x) = 1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z), at quadrature points */
+  HHG_COEFF_FIELD_P1 = 2, /* k = sum_v k_v phi_v, a P1 field (packed degree-1 vector at the op's level) */
+  HHG_COEFF_FIELD_P2 = 3  /* k = sum_m k_m psi_m, a P2 field (packed degree-2 vector at the op's level) */
+};
+
+typedef struct hhg_mesh hhg_mesh_t;
+typedef struct hhg_op hhg_op_t;
+
+/* Coefficient of an operator.  For FIELD types `field` is a device pointer
+ * of dtype `field_dtype` that the operator BORROWS: it is read at every
+ * apply, so the caller keeps it alive and may change its values between
+ * applies.  Applies must use dtype == field_dtype. */
+typedef struct {
+  int type;
+  double value;
+  const void* field;
+  int field_dtype;
+} hhg_coeff_t;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* hhg_last_error(void);
+
+/* Build the refined hierarchy of a macro mesh (Section 2).
+ * macro_vertices: host, nv x 3 doubles (copied).  macro_tets: host, nt x 4
+ * vertex indices (copied), either orientation.  level: finest refinement
+ * level, 0..10; levels 0..level are all available.
+ * Errors: HHG_E_ARG (sizes, indices), HHG_E_DEGENERATE, HHG_E_NONMANIFOLD,
+ * HHG_E_OOM, HHG_E_CUDA (device set-up).  The current CUDA device at this
+ * call is the mesh's device. */
+int hhg_mesh_create(const double* macro_vertices, int64_t nv, const int32_t* macro_tets, int64_t nt,
+                    int level, hhg_mesh_t** out);
+int hhg_mesh_destroy(hhg_mesh_t* mesh);
+
+/* Number of packed entries of a degree-p scalar vector at `level`
+ * (nmacro * V(p * 2^level)); multiply by ncomp * nrhs for batched or vector fields. */
+int hhg_vec_size(const hhg_mesh_t* mesh, int level, int degree, int64_t* n);
+
+/* Number of distinct points (DoFs) of a degree-p scalar space at `level`,
+ * and how many of them are not Dirichlet boundary points. */
+int hhg_dof_count(const hhg_mesh_t* mesh, int level, int degree, int64_t* total, int64_t* interior);
+
+/* Create a matrix-free operator (Eq. 4.1) at `level` (-1 = finest).
+ * kind HHG_DIFFUSION: a(u,v) = int k grad u . grad v, degree 1 or 2
+ *   (Eq. P1, Eq. P2V).  kind HHG_EPSILON: a(u,v) = int 2 mu eps(u):eps(v),
+ *   eps(u) = (grad u + grad u^T)/2, degree 2, vector valued.
+ * quad_degree: degree of the quadrature rule for variable coefficients
+ *   (1: centroid, 2: 4-point, 4: 14-point rule exact to degree 5); for
+ *   constant coefficients the local matrices are exact whatever its value.
+ * Errors: HHG_E_ARG, HHG_E_UNSUPPORTED, HHG_E_OOM, HHG_E_CUDA. */
+int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, const hhg_coeff_t* coeff, int bc,
+                  int quad_degree, hhg_op_t** out);
+int hhg_op_destroy(hhg_op_t* op);
+
+/* Replace the borrowed coefficient field pointer of a FIELD operator. */
+int hhg_op_set_field(hhg_op_t* op, const void* field, int field_dtype);
+
+/* y = A x (Eq. 4.1, Algorithm 1 summed over all micro-tets).  x, y: packed
+ * vectors of the op's space (ncomp = 3 for EPSILON), nrhs right-hand sides
+ * (nrhs >= 1; > 1 only for EPSILON).  y is overwritten; x and y must not
+ * overlap.  The apply computes every local matrix on the fly. */
+int hhg_op_apply(hhg_op_t* op, const void* x, void* y, int dtype, int nrhs, void* stream);
+
+/* Adjoint in the coefficient of a FIELD operator (A is linear in k):
+ * dk_m = g^T (dA/dk_m) u, summed over the nrhs pairs (u_r, g_r).  Under
+ * HHG_DIRICHLET only interior rows and columns of A depend on k, so the
+ * boundary entries of u and g do not contribute.  dk: packed vector of the
+ * coefficient space, overwritten.  The gradient of L(u) with respect to u
+ * is A^T g = A g (A symmetric) -- use hhg_op_apply.
+ * Errors: HHG_E_UNSUPPORTED for non-FIELD coefficients. */
+int hhg_op_apply_adjoint_coeff(hhg_op_t* op, const void* u, const void* g, void* dk, int dtype, int nrhs,
+                               void* stream);
+
+/* d = diag(A) (Dirichlet rows: 1), packed, overwritten (scalar ops). */
+int hhg_op_diagonal(hhg_op_t* op, void* d, int dtype, void* stream);
+
+/* Make a packed vector consistent: every copy of a shared point takes the
+ * value of its copy in the lowest-numbered macro.  n_per_point = ncomp*nrhs. */
+int hhg_vec_make_consistent(const hhg_mesh_t* mesh, int level, int degree, void* x, int dtype,
+                            int n_per_point, void* stream);
+
+/* Inner product over distinct points (each shared point counted once) of
+ * two consistent packed vectors; synchronous, result on the host. */
+int hhg_vec_dot(const hhg_mesh_t* mesh, int level, int degree, const void* x, const void* y, int dtype,
+                int n_per_point, double* result, void* stream);
+
+/* Grid transfers between level l-1 and level l (Section 8; the spaces are
+ * nested).  Prolongation xf = P xc evaluates the coarse FE function at the
+ * fine points.  Restriction rc = P^T rf sums over distinct fine points and
+ * leaves the coarse Dirichlet boundary entries zero.  Both overwrite their
+ * output. */
+int hhg_prolongate(const hhg_mesh_t* mesh, int level_fine, int degree, const void* xc, void* xf, int dtype,
+                   void* stream);
+int hhg_restrict(const hhg_mesh_t* mesh, int level_fine, int degree, const void* rf, void* rc, int dtype,
+                 void* stream);
+
+/* Load vector b_i = int f phi_i for f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
+ * (the manufactured Poisson right-hand side), by the 14-point rule per
+ * micro-tet; Dirichlet entries zero.  FP64 output, packed, overwritten. */
+int hhg_rhs_sin3_poisson(const hhg_mesh_t* mesh, int level, int degree, double* b, void* stream);
+
+/* || u_h - u ||_L2 for u = sin(pi x) sin(pi y) sin(pi z), 14-point rule
+ * per micro-tet; synchronous. */
+int hhg_l2_error_sin3(const hhg_mesh_t* mesh, int level, int degree, const double* uh, double* err,
+                      void* stream);
+
+/* One Chebyshev smoothing step of order `order` on D^{-1} A over
+ * [lo*lam, hi*lam] (Section 8): x <- x + p(D^{-1}A) D^{-1}(b - A x).
+ * dinv: packed inverse diagonal.  x updated in place. */
+int hhg_cheb_smooth(hhg_op_t* op, const void* b, void* x, const void* dinv, double lam, double lo, double hi,
+                    int order, int dtype, void* stream);
+
+/* Power iteration for the largest eigenvalue of D^{-1} A from start vector
+ * v (consistent, overwritten by the last iterate): iters steps of
+ * v <- D^{-1} A v / ||D^{-1} A v||; returns the last norm.  Synchronous. */
+int hhg_power_iteration(hhg_op_t* op, const void* dinv, void* v, int iters, int dtype, double* lam,
+                        void* stream);
+
+typedef struct {
+  int nu1, nu2;          /* pre / post smoothing steps per V-cycle (each a Chebyshev step) */
+  int cheb_order;        /* Chebyshev polynomial order (applications of A per step) */
+  int power_iters;       /* power-iteration steps for lambda_max of D^{-1}A per level */
+  double cheb_lo, cheb_hi; /* smoothing interval [lo*lam, hi*lam] */
+  double tol;            /* stop when ||b - A x||_2 / ||b||_2 <= tol */
+  int max_iters;         /* maximum number of outer iterations after FMG */
+  int mixed;             /* 0: all FP64; 1: FP32 cycles inside FP64 iterative refinement */
+  int fmg;               /* 1: start from full multigrid; 0: start from the given x */
+  int coarse_level;      /* level solved exactly (dense Cholesky in FP64) */
+} hhg_mg_opts_t;
+
+typedef struct {
+  int iterations;        /* outer iterations after FMG */
+  double rel_residual;   /* final ||b - A x||_2 / ||b||_2 (FP64) */
+  double residual_history[64]; /* relative residual after FMG and after each outer iteration */
+  double setup_ms;       /* hierarchy set-up time (first call on an op only) */
+  double solve_ms;       /* FMG + iterations, device time */
+} hhg_mg_stats_t;
+
+/* Fill `opts` with the defaults: V(2,2), order 2, 15 power iterations,
+ * [0.1, 1.1], tol 1e-10, 50 iterations, FP64, FMG on, coarse level 0. */
+int hhg_mg_default_opts(hhg_mg_opts_t* opts);
+
+/* Solve A x = b with geometric multigrid (Section 8): FMG, then outer
+ * iterations x <- x + V(b - A x) until the relative residual reaches tol.
+ * op: a scalar DIFFUSION operator with DIRICHLET boundary and a CONST or
+ * SIN3 coefficient; the hierarchy (coarser operators, inverse diagonals,
+ * eigenvalue estimates, coarse factor) is built on the first call and kept
+ * with op.  b, x: FP64 packed vectors; x is the initial guess when fmg = 0
+ * and is overwritten with the solution.  In mixed mode smoothing,
+ * restriction and prolongation run in FP32; the outer residual, the update
+ * of x and the coarse solve are FP64.  Synchronous.
+ * Errors: HHG_E_NOT_CONVERGED (x holds the last iterate), HHG_E_NAN,
+ * HHG_E_UNSUPPORTED, HHG_E_ARG, HHG_E_CUDA. */
+int hhg_mg_solve(hhg_op_t* op, const double* b, double* x, const hhg_mg_opts_t* opts, hhg_mg_stats_t* stats,
+                 void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HHG_H */

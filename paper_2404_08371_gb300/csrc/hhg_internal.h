@@ -1,0 +1,128 @@
+// Internal declarations of the hhg library (not part of the public C interface).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "hhg.h"
+
+namespace hhg {
+
+int fail(int code, const char* fmt, ...);
+void clear_error();
+
+#define HHG_CUDA_TRY(call)                                                                       \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return ::hhg::fail(HHG_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define HHG_TRY(call)          \
+  do {                         \
+    int s_ = (call);           \
+    if (s_ != HHG_OK) return s_; \
+  } while (0)
+
+// Number of lattice points with i+j+k <= s.
+__host__ __device__ inline int64_t lattice_size(int64_t s) { return (s + 1) * (s + 2) * (s + 3) / 6; }
+
+// Index-space vertex offsets of the six micro-tet classes in the cube at origin c
+// (white up, four octahedron tets split along (0,1,0)-(1,0,1), white down; Section 2, Fig. 3).
+extern const int kClassOffsets[6][4][3];
+// B(o, m) = m - kClassShrink[o] (Section 5.1).
+extern const int kClassShrink[6];
+// P2 local node order: 4 vertices then edges (0,1),(0,2),(0,3),(1,2),(1,3),(2,3).
+extern const int kP2Edges[6][2];
+
+// Geometry and boundary description of one macro-tetrahedron.
+struct MacroGeom {
+  double p0[3];
+  double e[3][3];        // e[a] = P_{a+1} - P_0
+  int32_t vid[4];
+  uint32_t bnd_table;    // bit z set: a point whose zero-weight set is z lies on the domain boundary
+};
+
+// Interface groups of one (level, degree): the copies of every point shared by several macros.
+struct Interface {
+  int64_t ngroups = 0;
+  int64_t nmembers = 0;
+  int64_t* d_ptr = nullptr;    // ngroups + 1 offsets into d_idx
+  int64_t* d_idx = nullptr;    // scalar packed positions, sorted (the first is the owner copy)
+  uint8_t* d_bnd = nullptr;    // 1 if the point is a Dirichlet boundary point
+  int64_t ndof_total = 0;
+  int64_t ndof_interior = 0;
+  ~Interface();
+};
+
+// Quadrature rule on the reference tetrahedron (volume 1/6).
+struct QuadRule {
+  std::vector<double> xi;   // nq x 3
+  std::vector<double> w;    // nq
+  int nq() const { return (int)w.size(); }
+};
+int quad_rule(int degree, QuadRule* out);
+
+}  // namespace hhg
+
+struct hhg_mesh {
+  int level = 0;            // finest level
+  int device = 0;
+  std::vector<double> vertices;
+  std::vector<int32_t> tets;
+  std::vector<hhg::MacroGeom> macros;
+  hhg::MacroGeom* d_macros = nullptr;
+  std::map<int, std::unique_ptr<hhg::Interface>> iface;   // key: level * 8 + degree
+  void* d_scratch = nullptr;   // reduction scratch, grown on demand (set-up time, not in applies)
+  size_t scratch_bytes = 0;
+  int nmacro() const { return (int)macros.size(); }
+  int interface(int level, int degree, const hhg::Interface** out);
+  int scratch_reserve(size_t bytes);
+  ~hhg_mesh();
+};
+
+namespace hhg {
+
+// Per-macro constants of an operator, in the compute type T (one block per macro, in device memory).
+template <typename T>
+struct OpConst {
+  int64_t base;          // offset of the macro in a packed scalar vector
+  int64_t kbase;         // offset of the macro in the packed coefficient vector
+  uint32_t bnd_table;
+  int N;                 // lattice resolution of the space (degree * 2^level)
+  int n;                 // cubes per edge (2^level)
+  T A[6][10][10];        // hoisted constant-coefficient local matrices per class (P1 uses [4][4])
+  T S[15];               // P1 interior 15-point stencil (offset order kStencil)
+  T M[6][6];             // per class |det J| J^{-1} J^{-T} (xx, yy, zz, xy, xz, yz)
+  T adet[6];             // per class |det J| of the micro-tet map
+  double x0[3];          // physical position of lattice point (0,0,0)
+  double h[3][3];        // h[a] = e[a] / n: physical step of one cube along index axis a
+};
+
+extern const int kStencil[15][3];
+
+// Launchers (ops.cu).
+template <typename T>
+int launch_apply(const struct ::hhg_op* op, const T* x, T* y, cudaStream_t s);
+template <typename T>
+int launch_interface_sum(const Interface* itf, T* y, int per_point, bool dirichlet, cudaStream_t s);
+template <typename T>
+int launch_make_consistent(const Interface* itf, T* x, int per_point, cudaStream_t s);
+
+}  // namespace hhg
+
+struct hhg_op {
+  hhg_mesh* mesh = nullptr;
+  int level = 0, kind = 0, degree = 1, bc = 0, quad_degree = 2;
+  hhg_coeff_t coeff{};
+  int N = 0, n = 0;
+  int64_t npts = 0;          // packed scalar entries of the space
+  void* d_const64 = nullptr; // OpConst<double>[nmacro]
+  void* d_const32 = nullptr; // OpConst<float>[nmacro]
+  hhg::QuadRule rule;
+  std::vector<hhg::OpConst<double>> h_const;
+  ~hhg_op();
+};

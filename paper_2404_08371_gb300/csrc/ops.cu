@@ -1,0 +1,540 @@
+// Operator set-up and the P1 constant-coefficient apply; interface reconciliation kernels.
+//
+// Eq. 4.1: A = sum_T P_T A_T R_T.  All micro-tets of one class are translates
+// of each other, so their Jacobians -- and, for a constant coefficient, their
+// local matrices -- are loop invariants (Section 6.1).  They are computed once
+// per macro and class on the host in FP64 ("hoisted") and handed to the kernels.
+// For P1 with a constant coefficient the six per-class 4x4 matrices fold into
+// one 15-point stencil at points whose incident micro-tets all lie in the
+// macro; points next to the macro boundary use the per-class matrices with an
+// explicit validity test of each incident micro-tet.  The apply gathers into
+// each output point (no atomics); every point is written by exactly one thread.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "hhg_internal.h"
+#include "lattice.cuh"
+
+namespace hhg {
+
+// ---------------------------------------------------------------------------
+// Host: hoisted per-class invariants (Section 6.1) and local matrices.
+// ---------------------------------------------------------------------------
+static void inv3(const double J[3][3], double Ji[3][3], double* det) {
+  double d = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+             J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  *det = d;
+  Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / d;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / d;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / d;
+  Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / d;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / d;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / d;
+  Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / d;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / d;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / d;
+}
+
+// Reference gradients of the P1 / P2 basis at a reference point.
+static void ref_grads(int degree, const double* xi, double g[10][3]) {
+  const double gl[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  double lam[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
+  if (degree == 1) {
+    for (int a = 0; a < 4; ++a)
+      for (int d = 0; d < 3; ++d) g[a][d] = gl[a][d];
+    return;
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int d = 0; d < 3; ++d) g[a][d] = (4.0 * lam[a] - 1.0) * gl[a][d];
+  for (int e = 0; e < 6; ++e) {
+    int a = kP2Edges[e][0], b = kP2Edges[e][1];
+    for (int d = 0; d < 3; ++d) g[4 + e][d] = 4.0 * (lam[a] * gl[b][d] + lam[b] * gl[a][d]);
+  }
+}
+
+static void build_const(hhg_op* op) {
+  const hhg_mesh* mesh = op->mesh;
+  const int n = op->n;
+  const int nloc = op->degree == 1 ? 4 : 10;
+  const double kval = op->coeff.type == HHG_COEFF_CONST ? op->coeff.value : 1.0;
+  QuadRule r2;
+  quad_rule(2, &r2);   // exact for the degree-2 integrand of the constant P2 matrix
+  const int Nk = op->coeff.type == HHG_COEFF_FIELD_P2 ? 2 * n : n;
+  op->h_const.assign(mesh->nmacro(), OpConst<double>{});
+  for (int m = 0; m < mesh->nmacro(); ++m) {
+    const MacroGeom& g = mesh->macros[m];
+    OpConst<double>& c = op->h_const[m];
+    std::memset(&c, 0, sizeof(c));
+    c.base = (int64_t)m * lattice_size(op->N);
+    c.kbase = (int64_t)m * lattice_size(Nk);
+    c.bnd_table = g.bnd_table;
+    c.N = op->N;
+    c.n = n;
+    for (int d = 0; d < 3; ++d) c.x0[d] = g.p0[d];
+    for (int a = 0; a < 3; ++a)
+      for (int d = 0; d < 3; ++d) c.h[a][d] = g.e[a][d] / n;
+    for (int o = 0; o < 6; ++o) {
+      // J = H D with H columns h_a and D columns off_b - off_0 (index space)
+      double J[3][3], Ji[3][3], det;
+      for (int r = 0; r < 3; ++r)
+        for (int b = 0; b < 3; ++b) {
+          double s = 0;
+          for (int a = 0; a < 3; ++a) s += c.h[a][r] * (kClassOffsets[o][b + 1][a] - kClassOffsets[o][0][a]);
+          J[r][b] = s;
+        }
+      inv3(J, Ji, &det);
+      const double adet = std::fabs(det);
+      double Mm[3][3];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double s = 0;
+          for (int t = 0; t < 3; ++t) s += Ji[a][t] * Ji[b][t];
+          Mm[a][b] = adet * s;
+        }
+      c.adet[o] = adet;
+      c.M[o][0] = Mm[0][0];
+      c.M[o][1] = Mm[1][1];
+      c.M[o][2] = Mm[2][2];
+      c.M[o][3] = Mm[0][1];
+      c.M[o][4] = Mm[0][2];
+      c.M[o][5] = Mm[1][2];
+      // constant-coefficient local matrix: sum_q w_q grad_ref_i^T M grad_ref_j (times k)
+      for (int q = 0; q < r2.nq(); ++q) {
+        double gr[10][3];
+        ref_grads(op->degree, &r2.xi[3 * q], gr);
+        for (int i = 0; i < nloc; ++i)
+          for (int j = 0; j < nloc; ++j) {
+            double s = 0;
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b) s += gr[i][a] * Mm[a][b] * gr[j][b];
+            c.A[o][i][j] += kval * r2.w[q] * s;
+          }
+      }
+    }
+    if (op->degree == 1) {
+      // fold the six per-class matrices into the 15-point stencil of a point whose incident tets all exist
+      for (int o = 0; o < 6; ++o)
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) {
+            int d[3];
+            for (int t = 0; t < 3; ++t) d[t] = kClassOffsets[o][b][t] - kClassOffsets[o][a][t];
+            for (int s = 0; s < 15; ++s)
+              if (d[0] == kStencil[s][0] && d[1] == kStencil[s][1] && d[2] == kStencil[s][2]) c.S[s] += c.A[o][a][b];
+          }
+    }
+  }
+}
+
+template <typename T>
+static OpConst<T> convert_const(const OpConst<double>& c) {
+  OpConst<T> o;
+  std::memset(&o, 0, sizeof(o));
+  o.base = c.base;
+  o.kbase = c.kbase;
+  o.bnd_table = c.bnd_table;
+  o.N = c.N;
+  o.n = c.n;
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 10; ++b)
+      for (int d = 0; d < 10; ++d) o.A[a][b][d] = (T)c.A[a][b][d];
+  for (int s = 0; s < 15; ++s) o.S[s] = (T)c.S[s];
+  for (int a = 0; a < 6; ++a) {
+    o.adet[a] = (T)c.adet[a];
+    for (int b = 0; b < 6; ++b) o.M[a][b] = (T)c.M[a][b];
+  }
+  std::memcpy(o.x0, c.x0, sizeof(c.x0));
+  std::memcpy(o.h, c.h, sizeof(c.h));
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// Device: P1 constant-coefficient apply (gather; one thread per output point).
+// ---------------------------------------------------------------------------
+template <typename T, bool DIRICHLET>
+__global__ void __launch_bounds__(256) p1_const_apply_kernel(const OpConst<T>* __restrict__ cst,
+                                                              const T* __restrict__ x, T* __restrict__ y) {
+  const OpConst<T>& c = cst[blockIdx.y];
+  const int N = c.N;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= dV(N)) return;
+  int i, j, k;
+  decode_point(p, N, i, j, k);
+  const T* __restrict__ xm = x + c.base;
+  T* __restrict__ ym = y + c.base;
+  const uint32_t table = c.bnd_table;
+  if (DIRICHLET && on_dirichlet(table, N, i, j, k)) {
+    ym[p] = xm[p];
+    return;
+  }
+  const int s = N - k;
+  const bool fast = DIRICHLET ? (i >= 2 && j >= 2 && k >= 2 && i + j + k <= N - 2)
+                              : (i >= 1 && j >= 1 && k >= 1 && i + j + k <= N - 1);
+  T acc;
+  if (fast) {
+    // rows of the 15-point stencil
+    const int64_t r00 = p - i;                                     // (j, k)
+    const int64_t rp0 = r00 + (s + 1 - j);                         // (j+1, k)
+    const int64_t rm0 = r00 - (s + 2 - j);                         // (j-1, k)
+    const int64_t pk1 = plane_start(N, k + 1);
+    const int64_t r01 = pk1 + row_start(s - 1, j);                 // (j, k+1)
+    const int64_t rm1 = pk1 + row_start(s - 1, j - 1);             // (j-1, k+1)
+    const int64_t pkm = plane_start(N, k - 1);
+    const int64_t r0m = pkm + row_start(s + 1, j);                 // (j, k-1)
+    const int64_t rpm = pkm + row_start(s + 1, j + 1);             // (j+1, k-1)
+    acc = c.S[0] * __ldg(xm + r00 + i);
+    acc += c.S[1] * __ldg(xm + r00 + i + 1);
+    acc += c.S[2] * __ldg(xm + r00 + i - 1);
+    acc += c.S[3] * __ldg(xm + rp0 + i);
+    acc += c.S[4] * __ldg(xm + rm0 + i);
+    acc += c.S[5] * __ldg(xm + r01 + i);
+    acc += c.S[6] * __ldg(xm + r0m + i);
+    acc += c.S[7] * __ldg(xm + rm0 + i + 1);
+    acc += c.S[8] * __ldg(xm + rp0 + i - 1);
+    acc += c.S[9] * __ldg(xm + r0m + i + 1);
+    acc += c.S[10] * __ldg(xm + r01 + i - 1);
+    acc += c.S[11] * __ldg(xm + rpm + i);
+    acc += c.S[12] * __ldg(xm + rm1 + i);
+    acc += c.S[13] * __ldg(xm + rm1 + i + 1);
+    acc += c.S[14] * __ldg(xm + rpm + i - 1);
+  } else {
+    // near the macro boundary: sum the incident micro-tets that exist (Algorithm 1 per tet)
+    acc = T(0);
+    const int n = N;   // P1: one lattice step per cube
+#pragma unroll 1
+    for (int o = 0; o < 6; ++o) {
+      const int lim = n - 1 - (o == 0 ? 0 : (o == 5 ? 2 : 1));
+#pragma unroll 1
+      for (int a = 0; a < 4; ++a) {
+        const int ci = i - kClassOffsetsD[o][a][0], cj = j - kClassOffsetsD[o][a][1], ck = k - kClassOffsetsD[o][a][2];
+        if (ci < 0 || cj < 0 || ck < 0 || ci + cj + ck > lim) continue;
+        for (int b = 0; b < 4; ++b) {
+          const int pi = ci + kClassOffsetsD[o][b][0], pj = cj + kClassOffsetsD[o][b][1], pk = ck + kClassOffsetsD[o][b][2];
+          if (DIRICHLET && on_dirichlet(table, N, pi, pj, pk)) continue;
+          acc += c.A[o][a][b] * __ldg(xm + packed_index(N, pi, pj, pk));
+        }
+      }
+    }
+  }
+  ym[p] = acc;
+}
+
+// diag(A) for the constant-coefficient operators: sum of A_T[a][a] over the incident micro-tets.
+template <typename T>
+__global__ void const_diag_kernel(const OpConst<T>* __restrict__ cst, int degree, bool dirichlet, T* __restrict__ d) {
+  const OpConst<T>& c = cst[blockIdx.y];
+  const int N = c.N, n = c.n;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= dV(N)) return;
+  int i, j, k;
+  decode_point(p, N, i, j, k);
+  if (dirichlet && on_dirichlet(c.bnd_table, N, i, j, k)) {
+    d[c.base + p] = T(1);
+    return;
+  }
+  T acc = T(0);
+  const int nloc = degree == 1 ? 4 : 10;
+  for (int o = 0; o < 6; ++o) {
+    const int lim = n - 1 - (o == 0 ? 0 : (o == 5 ? 2 : 1));
+    for (int a = 0; a < nloc; ++a) {
+      // lattice point (resolution N) of local node a relative to the cube origin, in units of 1/degree cubes
+      int off[3];
+      if (a < 4) {
+        for (int t = 0; t < 3; ++t) off[t] = degree * kClassOffsetsD[o][a][t];
+      } else {
+        const int e0 = kP2EdgesD[a - 4][0], e1 = kP2EdgesD[a - 4][1];
+        for (int t = 0; t < 3; ++t) off[t] = kClassOffsetsD[o][e0][t] + kClassOffsetsD[o][e1][t];
+      }
+      const int qi = i - off[0], qj = j - off[1], qk = k - off[2];
+      if (qi % degree || qj % degree || qk % degree) continue;
+      const int ci = qi / degree, cj = qj / degree, ck = qk / degree;
+      if (qi < 0 || qj < 0 || qk < 0 || ci + cj + ck > lim) continue;
+      acc += c.A[o][a][a];
+    }
+  }
+  d[c.base + p] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Interface reconciliation between macros (on-device replacement of the
+// paper's MPI communication of shared macro-primitives).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void iface_sum_kernel(const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
+                                 const uint8_t* __restrict__ bnd, int64_t ngroups, int per_point, bool dirichlet,
+                                 T* __restrict__ y) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ngroups) return;
+  if (dirichlet && bnd[g]) return;    // boundary rows already hold x in every copy
+  const int64_t a = ptr[g], b = ptr[g + 1];
+  for (int c = 0; c < per_point; ++c) {
+    T s = T(0);
+    for (int64_t t = a; t < b; ++t) s += y[idx[t] * per_point + c];
+    for (int64_t t = a; t < b; ++t) y[idx[t] * per_point + c] = s;
+  }
+}
+
+template <typename T>
+__global__ void iface_copy_owner_kernel(const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
+                                        int64_t ngroups, int per_point, T* __restrict__ x) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ngroups) return;
+  const int64_t a = ptr[g], b = ptr[g + 1];
+  for (int c = 0; c < per_point; ++c) {
+    const T v = x[idx[a] * per_point + c];
+    for (int64_t t = a + 1; t < b; ++t) x[idx[t] * per_point + c] = v;
+  }
+}
+
+template <typename T>
+int launch_interface_sum(const Interface* itf, T* y, int per_point, bool dirichlet, cudaStream_t s) {
+  if (itf->ngroups == 0) return HHG_OK;
+  const int th = 128;
+  iface_sum_kernel<T><<<(unsigned)((itf->ngroups + th - 1) / th), th, 0, s>>>(itf->d_ptr, itf->d_idx, itf->d_bnd,
+                                                                             itf->ngroups, per_point, dirichlet, y);
+  HHG_CUDA_TRY(cudaGetLastError());
+  return HHG_OK;
+}
+
+template <typename T>
+int launch_make_consistent(const Interface* itf, T* x, int per_point, cudaStream_t s) {
+  if (itf->ngroups == 0) return HHG_OK;
+  const int th = 128;
+  iface_copy_owner_kernel<T><<<(unsigned)((itf->ngroups + th - 1) / th), th, 0, s>>>(itf->d_ptr, itf->d_idx,
+                                                                                    itf->ngroups, per_point, x);
+  HHG_CUDA_TRY(cudaGetLastError());
+  return HHG_OK;
+}
+
+// Dot product over distinct points: the sum over all entries minus the non-owner copies.
+template <typename T>
+__global__ void dot_partial_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
+                                   const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
+                                   int64_t ngroups, int per_point, double* __restrict__ partial) {
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride)
+    acc += (double)x[t] * (double)y[t];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride)
+    for (int64_t t = ptr[g] + 1; t < ptr[g + 1]; ++t)
+      for (int c = 0; c < per_point; ++c) {
+        const int64_t e = idx[t] * per_point + c;
+        acc -= (double)x[e] * (double)y[e];
+      }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) acc += partial[t];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+constexpr int kDotBlocks = 304;   // 2 x 152 SMs
+
+template <typename T>
+int launch_dot(const Interface* itf, const T* x, const T* y, int64_t n, int per_point, double* d_scratch,
+               cudaStream_t s) {
+  dot_partial_kernel<T><<<kDotBlocks, 256, 0, s>>>(x, y, n, itf->d_ptr, itf->d_idx, itf->ngroups, per_point,
+                                                   d_scratch + 1);
+  sum_partials_kernel<<<1, 256, 0, s>>>(d_scratch + 1, kDotBlocks, d_scratch);
+  HHG_CUDA_TRY(cudaGetLastError());
+  return HHG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Dispatch
+// ---------------------------------------------------------------------------
+template <typename T>
+const OpConst<T>* dconst(const hhg_op* op);
+template <>
+const OpConst<double>* dconst<double>(const hhg_op* op) {
+  return (const OpConst<double>*)op->d_const64;
+}
+template <>
+const OpConst<float>* dconst<float>(const hhg_op* op) {
+  return (const OpConst<float>*)op->d_const32;
+}
+
+template <typename T>
+int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
+  const int64_t V = lattice_size(op->N);
+  const int nm = op->mesh->nmacro();
+  if (op->kind == HHG_DIFFUSION && op->degree == 1 && op->coeff.type == HHG_COEFF_CONST) {
+    dim3 grid((unsigned)((V + 255) / 256), nm);
+    if (op->bc == HHG_DIRICHLET)
+      p1_const_apply_kernel<T, true><<<grid, 256, 0, s>>>(dconst<T>(op), x, y);
+    else
+      p1_const_apply_kernel<T, false><<<grid, 256, 0, s>>>(dconst<T>(op), x, y);
+    HHG_CUDA_TRY(cudaGetLastError());
+    return HHG_OK;
+  }
+  return fail(HHG_E_UNSUPPORTED, "apply: operator kind %d degree %d coefficient %d not implemented", op->kind,
+              op->degree, op->coeff.type);
+}
+
+template <typename T>
+int launch_diag(const hhg_op* op, T* d, cudaStream_t s) {
+  const int64_t V = lattice_size(op->N);
+  if (op->kind == HHG_DIFFUSION && op->coeff.type == HHG_COEFF_CONST) {
+    dim3 grid((unsigned)((V + 255) / 256), op->mesh->nmacro());
+    const_diag_kernel<T><<<grid, 256, 0, s>>>(dconst<T>(op), op->degree, op->bc == HHG_DIRICHLET, d);
+    HHG_CUDA_TRY(cudaGetLastError());
+    return HHG_OK;
+  }
+  return fail(HHG_E_UNSUPPORTED, "diagonal: operator not implemented");
+}
+
+}  // namespace hhg
+
+using namespace hhg;
+
+hhg_op::~hhg_op() {
+  cudaFree(d_const64);
+  cudaFree(d_const32);
+}
+
+static int check_dtype(int dtype) {
+  if (dtype != HHG_F32 && dtype != HHG_F64) return fail(HHG_E_ARG, "dtype must be HHG_F32 or HHG_F64");
+  return HHG_OK;
+}
+
+extern "C" int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, const hhg_coeff_t* coeff, int bc,
+                             int quad_degree, hhg_op_t** out) {
+  clear_error();
+  if (!mesh || !coeff || !out) return fail(HHG_E_ARG, "op_create: null pointer");
+  *out = nullptr;
+  if (level < 0) level = mesh->level;
+  if (level > mesh->level) return fail(HHG_E_ARG, "op_create: level %d above the mesh's %d", level, mesh->level);
+  if (kind != HHG_DIFFUSION && kind != HHG_EPSILON) return fail(HHG_E_ARG, "op_create: unknown kind %d", kind);
+  if (degree != 1 && degree != 2) return fail(HHG_E_ARG, "op_create: degree must be 1 or 2");
+  if (kind == HHG_EPSILON && degree != 2) return fail(HHG_E_ARG, "op_create: EPSILON needs degree 2");
+  if (bc != HHG_DIRICHLET && bc != HHG_NEUMANN) return fail(HHG_E_ARG, "op_create: unknown boundary mode %d", bc);
+  if (coeff->type < HHG_COEFF_CONST || coeff->type > HHG_COEFF_FIELD_P2)
+    return fail(HHG_E_ARG, "op_create: unknown coefficient type %d", coeff->type);
+  std::unique_ptr<hhg_op> op(new hhg_op());
+  op->mesh = mesh;
+  op->level = level;
+  op->kind = kind;
+  op->degree = degree;
+  op->bc = bc;
+  op->quad_degree = quad_degree;
+  op->coeff = *coeff;
+  op->n = 1 << level;
+  op->N = degree << level;
+  op->npts = (int64_t)mesh->nmacro() * lattice_size(op->N);
+  HHG_TRY(quad_rule(quad_degree, &op->rule));
+  const Interface* itf = nullptr;
+  HHG_TRY(mesh->interface(level, degree, &itf));
+  if (coeff->type == HHG_COEFF_FIELD_P1 || coeff->type == HHG_COEFF_FIELD_P2)
+    HHG_TRY(mesh->interface(level, coeff->type == HHG_COEFF_FIELD_P1 ? 1 : 2, &itf));
+  build_const(op.get());
+  const int nm = mesh->nmacro();
+  std::vector<OpConst<float>> c32(nm);
+  for (int m = 0; m < nm; ++m) c32[m] = convert_const<float>(op->h_const[m]);
+  HHG_CUDA_TRY(cudaMalloc(&op->d_const64, sizeof(OpConst<double>) * nm));
+  HHG_CUDA_TRY(cudaMalloc(&op->d_const32, sizeof(OpConst<float>) * nm));
+  HHG_CUDA_TRY(cudaMemcpy(op->d_const64, op->h_const.data(), sizeof(OpConst<double>) * nm, cudaMemcpyHostToDevice));
+  HHG_CUDA_TRY(cudaMemcpy(op->d_const32, c32.data(), sizeof(OpConst<float>) * nm, cudaMemcpyHostToDevice));
+  *out = op.release();
+  return HHG_OK;
+}
+
+extern "C" int hhg_op_destroy(hhg_op_t* op) {
+  delete op;
+  return HHG_OK;
+}
+
+extern "C" int hhg_op_set_field(hhg_op_t* op, const void* field, int field_dtype) {
+  clear_error();
+  if (!op) return fail(HHG_E_ARG, "op_set_field: null op");
+  if (op->coeff.type != HHG_COEFF_FIELD_P1 && op->coeff.type != HHG_COEFF_FIELD_P2)
+    return fail(HHG_E_ARG, "op_set_field: operator has no coefficient field");
+  HHG_TRY(check_dtype(field_dtype));
+  op->coeff.field = field;
+  op->coeff.field_dtype = field_dtype;
+  return HHG_OK;
+}
+
+extern "C" int hhg_op_apply(hhg_op_t* op, const void* x, void* y, int dtype, int nrhs, void* stream) {
+  clear_error();
+  if (!op || !x || !y) return fail(HHG_E_ARG, "op_apply: null pointer");
+  HHG_TRY(check_dtype(dtype));
+  if (nrhs < 1 || (nrhs > 1 && op->kind != HHG_EPSILON)) return fail(HHG_E_ARG, "op_apply: bad nrhs %d", nrhs);
+  if (x == y) return fail(HHG_E_ARG, "op_apply: x and y must not overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Interface* itf = nullptr;
+  HHG_TRY(op->mesh->interface(op->level, op->degree, &itf));
+  if (dtype == HHG_F64) {
+    HHG_TRY(launch_apply<double>(op, (const double*)x, (double*)y, s));
+    HHG_TRY(launch_interface_sum<double>(itf, (double*)y, 1, op->bc == HHG_DIRICHLET, s));
+  } else {
+    HHG_TRY(launch_apply<float>(op, (const float*)x, (float*)y, s));
+    HHG_TRY(launch_interface_sum<float>(itf, (float*)y, 1, op->bc == HHG_DIRICHLET, s));
+  }
+  return HHG_OK;
+}
+
+extern "C" int hhg_op_diagonal(hhg_op_t* op, void* d, int dtype, void* stream) {
+  clear_error();
+  if (!op || !d) return fail(HHG_E_ARG, "op_diagonal: null pointer");
+  HHG_TRY(check_dtype(dtype));
+  if (op->kind != HHG_DIFFUSION) return fail(HHG_E_UNSUPPORTED, "op_diagonal: scalar operators only");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Interface* itf = nullptr;
+  HHG_TRY(op->mesh->interface(op->level, op->degree, &itf));
+  if (dtype == HHG_F64) {
+    HHG_TRY(launch_diag<double>(op, (double*)d, s));
+    HHG_TRY(launch_interface_sum<double>(itf, (double*)d, 1, op->bc == HHG_DIRICHLET, s));
+  } else {
+    HHG_TRY(launch_diag<float>(op, (float*)d, s));
+    HHG_TRY(launch_interface_sum<float>(itf, (float*)d, 1, op->bc == HHG_DIRICHLET, s));
+  }
+  return HHG_OK;
+}
+
+extern "C" int hhg_vec_make_consistent(const hhg_mesh_t* mesh, int level, int degree, void* x, int dtype,
+                                       int n_per_point, void* stream) {
+  clear_error();
+  if (!mesh || !x || n_per_point < 1) return fail(HHG_E_ARG, "vec_make_consistent: bad argument");
+  HHG_TRY(check_dtype(dtype));
+  const Interface* itf = nullptr;
+  HHG_TRY(const_cast<hhg_mesh_t*>(mesh)->interface(level, degree, &itf));
+  if (dtype == HHG_F64) return launch_make_consistent<double>(itf, (double*)x, n_per_point, (cudaStream_t)stream);
+  return launch_make_consistent<float>(itf, (float*)x, n_per_point, (cudaStream_t)stream);
+}
+
+extern "C" int hhg_vec_dot(const hhg_mesh_t* mesh, int level, int degree, const void* x, const void* y, int dtype,
+                           int n_per_point, double* result, void* stream) {
+  clear_error();
+  if (!mesh || !x || !y || !result || n_per_point < 1) return fail(HHG_E_ARG, "vec_dot: bad argument");
+  HHG_TRY(check_dtype(dtype));
+  const Interface* itf = nullptr;
+  hhg_mesh_t* m = const_cast<hhg_mesh_t*>(mesh);
+  HHG_TRY(m->interface(level, degree, &itf));
+  HHG_TRY(m->scratch_reserve((kDotBlocks + 1) * sizeof(double)));
+  const int64_t n = (int64_t)m->nmacro() * lattice_size((int64_t)degree << level) * n_per_point;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* d = (double*)m->d_scratch;
+  if (dtype == HHG_F64)
+    HHG_TRY(launch_dot<double>(itf, (const double*)x, (const double*)y, n, n_per_point, d, s));
+  else
+    HHG_TRY(launch_dot<float>(itf, (const float*)x, (const float*)y, n, n_per_point, d, s));
+  HHG_CUDA_TRY(cudaMemcpyAsync(result, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+  HHG_CUDA_TRY(cudaStreamSynchronize(s));
+  return HHG_OK;
+}
