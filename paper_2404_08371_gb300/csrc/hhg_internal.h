@@ -44,6 +44,7 @@ struct MacroGeom {
   double e[3][3];        // e[a] = P_{a+1} - P_0
   int32_t vid[4];
   uint32_t bnd_table;    // bit z set: a point whose zero-weight set is z lies on the domain boundary
+  uint32_t own_table;    // bit z set: this macro is the lowest-numbered macro holding such a point
 };
 
 // Interface groups of one (level, degree): the copies of every point shared by several macros.
@@ -55,6 +56,13 @@ struct Interface {
   uint8_t* d_bnd = nullptr;    // 1 if the point is a Dirichlet boundary point
   int64_t ndof_total = 0;
   int64_t ndof_interior = 0;
+  std::vector<int64_t> h_ptr, h_idx;   // host copies of the groups (set-up code)
+  std::vector<uint8_t> h_bnd;
+  // launch tables of the gather kernels: CTAs of 256 points never cross a plane
+  int64_t ncta = 0;
+  int* d_cta_plane = nullptr;   // plane of each CTA
+  int* d_cta_start = nullptr;   // first CTA of each plane (N + 2 entries)
+  int* d_pstart = nullptr;      // first packed position of each plane (N + 2 entries)
   ~Interface();
 };
 
@@ -86,9 +94,15 @@ struct hhg_mesh {
 
 namespace hhg {
 
+constexpr int kMaxQ = 14;
+struct MGHierarchy;
+struct OpWork;
+void destroy_mg(MGHierarchy* h);
+void destroy_work(OpWork* w);
+
 // Per-macro constants of an operator, in the compute type T (one block per macro, in device memory).
 template <typename T>
-struct OpConst {
+struct alignas(16) OpConst {
   int64_t base;          // offset of the macro in a packed scalar vector
   int64_t kbase;         // offset of the macro in the packed coefficient vector
   uint32_t bnd_table;
@@ -98,8 +112,20 @@ struct OpConst {
   T S[15];               // P1 interior 15-point stencil (offset order kStencil)
   T M[6][6];             // per class |det J| J^{-1} J^{-T} (xx, yy, zz, xy, xz, yz)
   T adet[6];             // per class |det J| of the micro-tet map
+  uint32_t own_table;    // see MacroGeom
   double x0[3];          // physical position of lattice point (0,0,0)
   double h[3][3];        // h[a] = e[a] / n: physical step of one cube along index axis a
+  // quadrature (variable coefficients): nq points, weights, barycentric coordinates,
+  // P2 basis values psi_m(xi_q), and for the analytic coefficient the cosine / sine of
+  // 2 pi delta, delta = H (off_o[0] + D_o xi_q): the offset of point q of class o from the cube origin.
+  int nq;
+  T w[kMaxQ];
+  T lam[kMaxQ][4];
+  T psi[kMaxQ][10];
+  T cs[6][kMaxQ][3][2];
+  T qoff[6][kMaxQ][3];   // physical offset delta of point q of class o from the cube origin
+  T X0[3];               // x0 and H in the compute type
+  T H[3][3];             // H[a][d]: component d of the step along index axis a
 };
 
 extern const int kStencil[15][3];
@@ -111,6 +137,14 @@ template <typename T>
 int launch_interface_sum(const Interface* itf, T* y, int per_point, bool dirichlet, cudaStream_t s);
 template <typename T>
 int launch_make_consistent(const Interface* itf, T* x, int per_point, cudaStream_t s);
+// Element-centric kernels (march.cu); mode 0 apply, 1 diagonal, 2 coefficient adjoint,
+// 3 load vector of f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z).
+template <typename T>
+int launch_march(const struct ::hhg_op* op, const OpConst<T>* cst, int mode, const T* x, const T* g, const T* kf,
+                 T* out, cudaStream_t s);
+// Squared L2 error of u_h against sin(pi x) sin(pi y) sin(pi z): per-CTA partial sums.
+int64_t launch_l2_blocks(const struct ::hhg_op* op);
+int launch_l2_error(const struct ::hhg_op* op, const double* uh, double* partial, cudaStream_t s);
 
 }  // namespace hhg
 
@@ -124,5 +158,8 @@ struct hhg_op {
   void* d_const32 = nullptr; // OpConst<float>[nmacro]
   hhg::QuadRule rule;
   std::vector<hhg::OpConst<double>> h_const;
+  const hhg::Interface* itf = nullptr;   // per-level data of the op's space (owned by the mesh)
+  hhg::MGHierarchy* mg = nullptr;         // multigrid hierarchy, built by the first mg_solve
+  hhg::OpWork* work = nullptr;            // work vectors of the standalone smoother calls
   ~hhg_op();
 };

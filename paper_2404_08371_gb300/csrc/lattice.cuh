@@ -15,6 +15,10 @@ static __constant__ int kClassOffsetsD[6][4][3] = {
     {{0, 1, 0}, {1, 0, 1}, {0, 0, 1}, {1, 0, 0}},
     {{1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}},
 };
+// The 15 P1 stencil offsets (same order as kStencil in mesh.cpp).
+static __constant__ int kStencilD[15][3] = {
+    {0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1}, {1, -1, 0},
+    {-1, 1, 0}, {1, 0, -1}, {-1, 0, 1}, {0, 1, -1}, {0, -1, 1}, {1, -1, 1}, {-1, 1, -1}};
 static __constant__ int kP2EdgesD[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
 
 // Number of lattice points with i+j+k <= s (V(s) = (s+1)(s+2)(s+3)/6; V(-1) = 0).

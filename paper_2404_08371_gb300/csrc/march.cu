@@ -1,0 +1,470 @@
+// Element-centric "marching" kernels: apply, diagonal and coefficient adjoint of the
+// variable-coefficient and P2 operators.
+//
+// Eq. 4.1 / Algorithm 1 per micro-tet, traversed in the spirit of the cubes loop
+// strategy (Section 5.2, Algorithm 3): one thread owns one cube of the index-space
+// lattice and evaluates all six micro-tets in it, so every DoF of the cube is
+// loaded once per cube and stays in registers.  A CTA of 32 lanes (i) x kWarps
+// warps (j) marches upward through the cube layers k.  Element results are summed
+// into points without atomics:
+//   i: a lane adds the low-i face of its right neighbour (warp shuffle);
+//   j: a warp adds the low-j face of the warp above it (shared memory);
+//   k: the top face of a cube is carried in registers to the next layer.
+// Adjacent CTAs overlap by one cube in i and j; the overlapping cube's points are
+// written by exactly one of them, so every point is written once.
+//
+// Local matrices are never stored: the quadrature is fused with the local apply
+// (Remark 4.1): grad u at each point from the 10 nodal values, scaled by
+// k w |det J| J^{-1} J^{-T} (the hoisted per-class metric, Section 6.1), tested
+// against the basis gradients.  Gradients of the P2 basis are written through the
+// barycentric coordinates, so grad u = sum_a grad lambda_a s_a with
+// s_a = u_a (4 lambda_a - 1) + 4 sum_b u_ab lambda_b.
+#include "hhg_internal.h"
+#include "lattice.cuh"
+
+namespace hhg {
+
+constexpr int kWarps = 8;     // warps per CTA along j
+constexpr int kChunk = 32;    // cube layers per CTA along k
+
+enum { MODE_APPLY = 0, MODE_DIAG = 1, MODE_ADJ = 2, MODE_RHS = 3 };
+
+__host__ __device__ constexpr int coff(int o, int v, int d) {
+  constexpr int t[6][4][3] = {
+      {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, {{0, 1, 0}, {1, 0, 1}, {1, 0, 0}, {1, 1, 0}},
+      {{0, 1, 0}, {1, 0, 1}, {1, 1, 0}, {0, 1, 1}}, {{0, 1, 0}, {1, 0, 1}, {0, 1, 1}, {0, 0, 1}},
+      {{0, 1, 0}, {1, 0, 1}, {0, 0, 1}, {1, 0, 0}}, {{1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}}};
+  return t[o][v][d];
+}
+__host__ __device__ constexpr int edge_end(int e, int s) {
+  constexpr int t[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+  return t[e][s];
+}
+__host__ __device__ constexpr int class_shrink(int o) { return o == 0 ? 0 : (o == 5 ? 2 : 1); }
+// Position (0..R per axis) of local node `node` of class o inside the cube block, linearised.
+template <int R>
+__host__ __device__ constexpr int node_slot(int o, int node) {
+  int p[3] = {0, 0, 0};
+  for (int d = 0; d < 3; ++d) {
+    if (R == 1 || node < 4)
+      p[d] = R * coff(o, node, d);
+    else
+      p[d] = coff(o, edge_end(node - 4, 0), d) + coff(o, edge_end(node - 4, 1), d);
+  }
+  return p[0] + (R + 1) * (p[1] + (R + 1) * p[2]);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_down(T v) {
+  return __shfl_down_sync(0xffffffffu, v, 1);
+}
+
+// grad_ref u at quadrature point q from the 10 P2 nodal values.
+template <typename T>
+__device__ __forceinline__ void p2_ref_grad(const T* u, const T lam[4], T g[3]) {
+  T s[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) s[a] = u[a] * (T(4) * lam[a] - T(1));
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const int a = edge_end(e, 0), b = edge_end(e, 1);
+    s[a] += T(4) * u[4 + e] * lam[b];
+    s[b] += T(4) * u[4 + e] * lam[a];
+  }
+  g[0] = s[1] - s[0];
+  g[1] = s[2] - s[0];
+  g[2] = s[3] - s[0];
+}
+
+// y_i += r . grad_ref phi_i at the point with barycentric coordinates lam.
+template <typename T>
+__device__ __forceinline__ void p2_ref_test(const T r[3], const T lam[4], T* y) {
+  const T rho[4] = {-(r[0] + r[1] + r[2]), r[0], r[1], r[2]};   // r . grad lambda_a
+#pragma unroll
+  for (int a = 0; a < 4; ++a) y[a] += (T(4) * lam[a] - T(1)) * rho[a];
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const int a = edge_end(e, 0), b = edge_end(e, 1);
+    y[4 + e] += T(4) * (lam[a] * rho[b] + lam[b] * rho[a]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void metric(const T* M, const T g[3], T r[3]) {
+  r[0] = M[0] * g[0] + M[3] * g[1] + M[4] * g[2];
+  r[1] = M[3] * g[0] + M[1] * g[1] + M[5] * g[2];
+  r[2] = M[4] * g[0] + M[5] * g[1] + M[2] * g[2];
+}
+
+template <typename T>
+__device__ __forceinline__ void sincos2pi(T x, T* s, T* c);
+template <>
+__device__ __forceinline__ void sincos2pi<double>(double x, double* s, double* c) {
+  sincospi(2.0 * x, s, c);
+}
+template <>
+__device__ __forceinline__ void sincos2pi<float>(float x, float* s, float* c) {
+  sincospif(2.0f * x, s, c);
+}
+
+template <typename T, int R, int COEF, int MODE, bool DIR>
+__global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __restrict__ cst, int nkc,
+                                                            const T* __restrict__ x, const T* __restrict__ g,
+                                                            const T* __restrict__ kf, T* __restrict__ out) {
+  constexpr int P = R + 1;
+  constexpr int P3 = P * P * P;
+  constexpr int NL = R == 1 ? 4 : 10;
+  __shared__ OpConst<T> c;
+  __shared__ T xch[kWarps][P][R][32];
+  const int macro = blockIdx.z / nkc;
+  const int kc = blockIdx.z - macro * nkc;
+  {
+    const int4* src = reinterpret_cast<const int4*>(cst + macro);
+    int4* dst = reinterpret_cast<int4*>(&c);
+    for (int t = threadIdx.x; t < (int)(sizeof(OpConst<T>) / sizeof(int4)); t += blockDim.x) dst[t] = src[t];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n = c.n, N = c.N;
+  const int ti0 = 31 * blockIdx.x, tj0 = (kWarps - 1) * blockIdx.y, K0 = kChunk * kc;
+  if (ti0 + tj0 + K0 > n) return;   // lowest point owned by the CTA lies outside the macro (uniform)
+  const int ci = ti0 + lane - 1;
+  const int cj = tj0 + warp - 1;
+  const int ck_last = min(K0 + kChunk - 1, n - ti0 - tj0);
+  const int64_t base = c.base;
+  const uint32_t table = c.bnd_table;
+  // owned local index ranges in i (lanes) and j (warps)
+  const int a_lo = lane == 0 ? R : 1, a_hi = lane == 31 ? R - 1 : R;
+  const int b_lo = warp == 0 ? R : 1, b_hi = warp == kWarps - 1 ? R - 1 : R;
+
+  T carry[P * P];
+#pragma unroll
+  for (int t = 0; t < P * P; ++t) carry[t] = T(0);
+
+  for (int ck = K0 - 1; ck <= ck_last; ++ck) {
+    T acc[P3];
+#pragma unroll
+    for (int t = 0; t < P3; ++t) acc[t] = T(0);
+    const bool cube_ok = ci >= 0 && cj >= 0 && ck >= 0 && ci + cj + ck <= n - 1;
+    if (cube_ok) {
+      // gather the cube block (masked: outside the macro or Dirichlet boundary -> 0)
+      T xb[P3];
+      T gb[MODE == MODE_ADJ ? P3 : 1];
+      T kb[COEF == HHG_COEFF_FIELD_P1 || COEF == HHG_COEFF_FIELD_P2 ? P3 : 1];
+#pragma unroll
+      for (int cz = 0; cz < P; ++cz)
+#pragma unroll
+        for (int cy = 0; cy < P; ++cy)
+#pragma unroll
+          for (int cx = 0; cx < P; ++cx) {
+            const int s = cx + P * (cy + P * cz);
+            const int pi = R * ci + cx, pj = R * cj + cy, pk = R * ck + cz;
+            const bool in = pi + pj + pk <= N;
+            const int64_t idx = in ? packed_index(N, pi, pj, pk) : 0;
+            const bool live = in && !(DIR && on_dirichlet(table, N, pi, pj, pk));
+            if (MODE == MODE_APPLY || MODE == MODE_ADJ) xb[s] = live ? __ldg(x + base + idx) : T(0);
+            if (MODE == MODE_ADJ) gb[s] = live ? __ldg(g + base + idx) : T(0);
+            if (COEF == HHG_COEFF_FIELD_P1 || COEF == HHG_COEFF_FIELD_P2) kb[s] = in ? __ldg(kf + c.kbase + idx) : T(0);
+          }
+      // analytic coefficient: sin / cos of 2 pi x at the cube origin, per coordinate
+      T so[3], co[3];
+      if (COEF == HHG_COEFF_SIN3) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const T xd = c.X0[d] + T(ci) * c.H[0][d] + T(cj) * c.H[1][d] + T(ck) * c.H[2][d];
+          sincos2pi<T>(xd, &so[d], &co[d]);
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < 6; ++o) {
+        if (ci + cj + ck > n - 1 - class_shrink(o)) continue;
+        T ul[NL], yl[NL];
+#pragma unroll
+        for (int a = 0; a < NL; ++a) {
+          ul[a] = (MODE == MODE_APPLY || MODE == MODE_ADJ) ? xb[node_slot<R>(o, a)] : T(0);
+          yl[a] = T(0);
+        }
+        if (MODE == MODE_RHS) {
+          // b_a += sum_q w_q |det J| f(x_q) phi_a(xi_q), f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
+          for (int q = 0; q < c.nq; ++q) {
+            T xq[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+              xq[d] = c.X0[d] + T(ci) * c.H[0][d] + T(cj) * c.H[1][d] + T(ck) * c.H[2][d] + c.qoff[o][q][d];
+            const T f = T(3.0 * M_PI * M_PI) * sinpi(xq[0]) * sinpi(xq[1]) * sinpi(xq[2]);
+            const T s = c.w[q] * c.adet[o] * f;
+#pragma unroll
+            for (int a = 0; a < NL; ++a) yl[a] += s * (R == 1 ? c.lam[q][a] : c.psi[q][a]);
+          }
+        } else if (R == 1) {
+          // ---- P1: A_T = kbar_T A0_o with A0_o the hoisted constant matrix ----
+          T kbar = T(1);
+          if (COEF == HHG_COEFF_SIN3) {
+            kbar = T(0);
+            for (int q = 0; q < c.nq; ++q) {
+              T sv[3];
+#pragma unroll
+              for (int d = 0; d < 3; ++d) sv[d] = so[d] * c.cs[o][q][d][0] + co[d] * c.cs[o][q][d][1];
+              kbar += c.w[q] * (T(1) + T(0.5) * sv[0] * sv[1] * sv[2]);
+            }
+            kbar *= T(6);   // sum_q w_q = 1/6
+          } else if (COEF == HHG_COEFF_FIELD_P1) {
+            kbar = T(0.25) * (kb[node_slot<R>(o, 0)] + kb[node_slot<R>(o, 1)] + kb[node_slot<R>(o, 2)] +
+                              kb[node_slot<R>(o, 3)]);
+          }
+          if (MODE == MODE_APPLY) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              T s = T(0);
+#pragma unroll
+              for (int b = 0; b < 4; ++b) s += c.A[o][a][b] * ul[b];
+              yl[a] = kbar * s;
+            }
+          } else if (MODE == MODE_DIAG) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) yl[a] = kbar * c.A[o][a][a];
+          } else {
+            // dk_v += (1/4) g_T^T A0 u_T for each vertex v of T (P1 field, exact)
+            T t = T(0);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              T s = T(0);
+#pragma unroll
+              for (int b = 0; b < 4; ++b) s += c.A[o][a][b] * ul[b];
+              t += gb[node_slot<R>(o, a)] * s;
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) yl[a] = T(0.25) * t;
+          }
+        } else if (COEF == HHG_COEFF_CONST) {
+          // ---- P2 constant: hoisted 10x10 matrix ----
+          if (MODE == MODE_APPLY) {
+#pragma unroll
+            for (int a = 0; a < 10; ++a) {
+              T s = T(0);
+#pragma unroll
+              for (int b = 0; b < 10; ++b) s += c.A[o][a][b] * ul[b];
+              yl[a] = s;
+            }
+          } else {
+#pragma unroll
+            for (int a = 0; a < 10; ++a) yl[a] = c.A[o][a][a];
+          }
+        } else {
+          // ---- P2 variable coefficient: fused quadrature (Remark 4.1) ----
+          T gl[10];
+          if (MODE == MODE_ADJ) {
+#pragma unroll
+            for (int a = 0; a < 10; ++a) gl[a] = gb[node_slot<R>(o, a)];
+          }
+          const T* M = c.M[o];
+#pragma unroll 2
+          for (int q = 0; q < c.nq; ++q) {
+            const T lam[4] = {c.lam[q][0], c.lam[q][1], c.lam[q][2], c.lam[q][3]};
+            T kq;
+            if (COEF == HHG_COEFF_SIN3) {
+              T sv[3];
+#pragma unroll
+              for (int d = 0; d < 3; ++d) sv[d] = so[d] * c.cs[o][q][d][0] + co[d] * c.cs[o][q][d][1];
+              kq = T(1) + T(0.5) * sv[0] * sv[1] * sv[2];
+            } else {
+              kq = T(0);
+#pragma unroll
+              for (int m = 0; m < 10; ++m) kq += c.psi[q][m] * kb[node_slot<R>(o, m)];
+            }
+            if (MODE == MODE_APPLY) {
+              T gr[3], r[3];
+              p2_ref_grad<T>(ul, lam, gr);
+              metric<T>(M, gr, r);
+              const T s = kq * c.w[q];
+              r[0] *= s;
+              r[1] *= s;
+              r[2] *= s;
+              p2_ref_test<T>(r, lam, yl);
+            } else if (MODE == MODE_DIAG) {
+              // grad_ref phi_a . M grad_ref phi_a for every node a
+              const T s = kq * c.w[q];
+#pragma unroll
+              for (int a = 0; a < 10; ++a) {
+                T e[10];
+#pragma unroll
+                for (int b = 0; b < 10; ++b) e[b] = T(a == b ? 1 : 0);
+                T gr[3], r[3];
+                p2_ref_grad<T>(e, lam, gr);
+                metric<T>(M, gr, r);
+                yl[a] += s * (gr[0] * r[0] + gr[1] * r[1] + gr[2] * r[2]);
+              }
+            } else {
+              T gu[3], gg[3], r[3];
+              p2_ref_grad<T>(ul, lam, gu);
+              p2_ref_grad<T>(gl, lam, gg);
+              metric<T>(M, gu, r);
+              const T t = c.w[q] * (gg[0] * r[0] + gg[1] * r[1] + gg[2] * r[2]);
+#pragma unroll
+              for (int m = 0; m < 10; ++m) yl[m] += c.psi[q][m] * t;
+            }
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < NL; ++a) acc[node_slot<R>(o, a)] += yl[a];
+      }
+    }
+    // k: the bottom face receives the carried top face of the cube below; keep the new top face
+#pragma unroll
+    for (int t = 0; t < P * P; ++t) {
+      acc[t] += carry[t];
+      carry[t] = acc[t + R * P * P];
+    }
+    // i: add the low-i face of the right neighbour (planes 0..R-1)
+#pragma unroll
+    for (int cz = 0; cz < R; ++cz)
+#pragma unroll
+      for (int cy = 0; cy < P; ++cy) {
+        const T v = shfl_down<T>(acc[0 + P * (cy + P * cz)]);
+        acc[R + P * (cy + P * cz)] += v;
+      }
+    // j: add the low-j face of the warp above
+#pragma unroll
+    for (int cz = 0; cz < R; ++cz)
+#pragma unroll
+      for (int cx = 0; cx < P; ++cx) xch[warp][cx][cz][lane] = acc[cx + P * (0 + P * cz)];
+    __syncthreads();
+    if (warp < kWarps - 1) {
+#pragma unroll
+      for (int cz = 0; cz < R; ++cz)
+#pragma unroll
+        for (int cx = 0; cx < P; ++cx) acc[cx + P * (R + P * cz)] += xch[warp + 1][cx][cz][lane];
+    }
+    __syncthreads();
+    // write the owned points of planes R*ck .. R*ck + R-1
+    if (ck >= K0) {
+#pragma unroll
+      for (int cz = 0; cz < R; ++cz)
+#pragma unroll
+        for (int cy = 0; cy < P; ++cy)
+#pragma unroll
+          for (int cx = 0; cx < P; ++cx) {
+            if (cx < a_lo || cx > a_hi || cy < b_lo || cy > b_hi) continue;
+            const int pi = R * ci + cx, pj = R * cj + cy, pk = R * ck + cz;
+            if (pi < 0 || pj < 0 || pi + pj + pk > N) continue;
+            const int64_t idx = base + packed_index(N, pi, pj, pk);
+            T v = acc[cx + P * (cy + P * cz)];
+            if (DIR && MODE != MODE_ADJ && on_dirichlet(table, N, pi, pj, pk))
+              v = MODE == MODE_APPLY ? x[idx] : (MODE == MODE_DIAG ? T(1) : T(0));
+            out[idx] = v;
+          }
+    }
+  }
+}
+
+template <typename T, int R, int COEF, int MODE>
+static int launch_march_t(const hhg_op* op, const OpConst<T>* cst, const T* x, const T* g, const T* kf, T* out,
+                          cudaStream_t s) {
+  const int N = op->N;
+  const int n = op->n;
+  dim3 grid((unsigned)((n + 31) / 31 + 1), (unsigned)((n + kWarps - 1) / (kWarps - 1) + 1), 1);
+  const int nkc = (n + 1 + kChunk - 1) / kChunk;
+  grid.z = (unsigned)(nkc * op->mesh->nmacro());
+  (void)N;
+  if (op->bc == HHG_DIRICHLET)
+    march_kernel<T, R, COEF, MODE, true><<<grid, 32 * kWarps, 0, s>>>(cst, nkc, x, g, kf, out);
+  else
+    march_kernel<T, R, COEF, MODE, false><<<grid, 32 * kWarps, 0, s>>>(cst, nkc, x, g, kf, out);
+  HHG_CUDA_TRY(cudaGetLastError());
+  return HHG_OK;
+}
+
+// Dispatch on (degree, coefficient, mode).  Returns HHG_E_UNSUPPORTED for other combinations.
+template <typename T>
+int launch_march(const hhg_op* op, const OpConst<T>* cst, int mode, const T* x, const T* g, const T* kf, T* out,
+                 cudaStream_t s) {
+  const int ct = op->coeff.type;
+#define HHG_MARCH_CASE(RR, CC, MM) \
+  if (op->degree == RR && ct == CC && mode == MM) return launch_march_t<T, RR, CC, MM>(op, cst, x, g, kf, out, s);
+  HHG_MARCH_CASE(1, HHG_COEFF_SIN3, MODE_APPLY)
+  HHG_MARCH_CASE(1, HHG_COEFF_FIELD_P1, MODE_APPLY)
+  HHG_MARCH_CASE(1, HHG_COEFF_SIN3, MODE_DIAG)
+  HHG_MARCH_CASE(1, HHG_COEFF_FIELD_P1, MODE_DIAG)
+  HHG_MARCH_CASE(1, HHG_COEFF_FIELD_P1, MODE_ADJ)
+  HHG_MARCH_CASE(2, HHG_COEFF_CONST, MODE_APPLY)
+  HHG_MARCH_CASE(2, HHG_COEFF_SIN3, MODE_APPLY)
+  HHG_MARCH_CASE(2, HHG_COEFF_FIELD_P2, MODE_APPLY)
+  HHG_MARCH_CASE(2, HHG_COEFF_SIN3, MODE_DIAG)
+  HHG_MARCH_CASE(2, HHG_COEFF_FIELD_P2, MODE_DIAG)
+  HHG_MARCH_CASE(2, HHG_COEFF_FIELD_P2, MODE_ADJ)
+  if (sizeof(T) == 8) {
+    HHG_MARCH_CASE(1, HHG_COEFF_CONST, MODE_RHS)
+    HHG_MARCH_CASE(2, HHG_COEFF_CONST, MODE_RHS)
+  }
+#undef HHG_MARCH_CASE
+  return fail(HHG_E_UNSUPPORTED, "no kernel for degree %d, coefficient %d, mode %d", op->degree, ct, mode);
+}
+
+// Squared L2 error of u_h against u = sin(pi x) sin(pi y) sin(pi z): one thread per cube,
+// the six micro-tets with the op's quadrature rule; per-CTA partial sums (no atomics).
+template <int R>
+__global__ void __launch_bounds__(256) l2_error_kernel(const OpConst<double>* __restrict__ cst,
+                                                        const double* __restrict__ uh, double* __restrict__ partial) {
+  constexpr int NL = R == 1 ? 4 : 10;
+  const OpConst<double>& c = cst[blockIdx.y];
+  const int n = c.n, N = c.N;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (p < dV(n - 1)) {
+    int ci, cj, ck;
+    decode_point(p, n - 1, ci, cj, ck);   // cube origins: i + j + k <= n - 1
+    for (int o = 0; o < 6; ++o) {
+      if (ci + cj + ck > n - 1 - class_shrink(o)) continue;
+      double ul[NL];
+      for (int a = 0; a < NL; ++a) {
+        int q[3];
+        for (int d = 0; d < 3; ++d) {
+          if (R == 1 || a < 4)
+            q[d] = R * kClassOffsetsD[o][a][d];
+          else
+            q[d] = kClassOffsetsD[o][kP2EdgesD[a - 4][0]][d] + kClassOffsetsD[o][kP2EdgesD[a - 4][1]][d];
+        }
+        ul[a] = uh[c.base + packed_index(N, R * ci + q[0], R * cj + q[1], R * ck + q[2])];
+      }
+      for (int q = 0; q < c.nq; ++q) {
+        double xq[3];
+        for (int d = 0; d < 3; ++d)
+          xq[d] = c.X0[d] + ci * c.H[0][d] + cj * c.H[1][d] + ck * c.H[2][d] + c.qoff[o][q][d];
+        double uhq = 0.0;
+        for (int a = 0; a < NL; ++a) uhq += ul[a] * (R == 1 ? c.lam[q][a] : c.psi[q][a]);
+        const double e = uhq - sinpi(xq[0]) * sinpi(xq[1]) * sinpi(xq[2]);
+        acc += c.w[q] * c.adet[o] * e * e;
+      }
+    }
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = red[0];
+}
+
+int64_t launch_l2_blocks(const hhg_op* op) {
+  return ((lattice_size(op->n - 1) + 255) / 256) * op->mesh->nmacro();
+}
+
+int launch_l2_error(const hhg_op* op, const double* uh, double* partial, cudaStream_t s) {
+  const unsigned gx = (unsigned)((lattice_size(op->n - 1) + 255) / 256);
+  dim3 grid(gx, op->mesh->nmacro());
+  if (op->degree == 1)
+    l2_error_kernel<1><<<grid, 256, 0, s>>>((const OpConst<double>*)op->d_const64, uh, partial);
+  else
+    l2_error_kernel<2><<<grid, 256, 0, s>>>((const OpConst<double>*)op->d_const64, uh, partial);
+  HHG_CUDA_TRY(cudaGetLastError());
+  return HHG_OK;
+}
+
+template int launch_march<double>(const hhg_op*, const OpConst<double>*, int, const double*, const double*,
+                                  const double*, double*, cudaStream_t);
+template int launch_march<float>(const hhg_op*, const OpConst<float>*, int, const float*, const float*, const float*,
+                                 float*, cudaStream_t);
+
+}  // namespace hhg

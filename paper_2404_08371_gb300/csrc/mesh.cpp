@@ -50,6 +50,9 @@ Interface::~Interface() {
   cudaFree(d_ptr);
   cudaFree(d_idx);
   cudaFree(d_bnd);
+  cudaFree(d_cta_plane);
+  cudaFree(d_cta_start);
+  cudaFree(d_pstart);
 }
 
 // ---------------------------------------------------------------------------
@@ -290,6 +293,17 @@ extern "C" int hhg_mesh_create(const double* vx, int64_t nv, const int32_t* tx, 
         for (int b = a + 1; b < 3; ++b) bnd_edges.insert(Edge{std::min(f[a], f[b]), std::max(f[a], f[b])});
       }
     }
+  // macros around every vertex, edge and face (for the owner tables)
+  std::map<std::vector<int32_t>, int> lowest;
+  for (int64_t t = 0; t < nt; ++t)
+    for (int z = 1; z < 15; ++z) {
+      std::vector<int32_t> key;
+      for (int a = 0; a < 4; ++a)
+        if (!(z & (1 << a))) key.push_back(tx[4 * t + a]);
+      std::sort(key.begin(), key.end());
+      auto it = lowest.find(key);
+      if (it == lowest.end() || it->second > (int)t) lowest[key] = (int)t;
+    }
   // boundary table per macro, indexed by the zero set z of the weights (w0, w1, w2, w3)
   for (int64_t t = 0; t < nt; ++t) {
     MacroGeom& g = m->macros[t];
@@ -313,6 +327,15 @@ extern "C" int hhg_mesh_create(const double* vx, int64_t nv, const int32_t* tx, 
       if (b) table |= 1u << z;
     }
     g.bnd_table = table;
+    uint32_t own = 1u;   // z = 0: interior points belong to this macro only
+    for (int z = 1; z < 15; ++z) {
+      std::vector<int32_t> key;
+      for (int a = 0; a < 4; ++a)
+        if (!(z & (1 << a))) key.push_back(g.vid[a]);
+      std::sort(key.begin(), key.end());
+      if (lowest[key] == (int)t) own |= 1u << z;
+    }
+    g.own_table = own;
   }
   HHG_CUDA_TRY(cudaMalloc(&m->d_macros, sizeof(MacroGeom) * nt));
   HHG_CUDA_TRY(cudaMemcpy(m->d_macros, m->macros.data(), sizeof(MacroGeom) * nt, cudaMemcpyHostToDevice));
@@ -401,6 +424,32 @@ int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
   I->ndof_total = nmacro() * V - dup;
   int64_t nb_unique = nbnd_points - dup_bnd;
   I->ndof_interior = I->ndof_total - nb_unique;
+  // plane launch tables (32-bit in-macro indexing)
+  if (V >= ((int64_t)1 << 31)) return fail(HHG_E_UNSUPPORTED, "level too fine for 32-bit in-macro indexing");
+  {
+    std::vector<int> cta_start(N + 2), pstart(N + 2), cta_plane;
+    int64_t ncta = 0, p = 0;
+    for (int64_t k = 0; k <= N + 1; ++k) {
+      cta_start[k] = (int)ncta;
+      pstart[k] = (int)p;
+      if (k <= N) {
+        const int64_t s = N - k, cnt = (s + 1) * (s + 2) / 2, nb = (cnt + 255) / 256;
+        for (int64_t b = 0; b < nb; ++b) cta_plane.push_back((int)k);
+        ncta += nb;
+        p += cnt;
+      }
+    }
+    I->ncta = ncta;
+    HHG_CUDA_TRY(cudaMalloc(&I->d_cta_plane, sizeof(int) * cta_plane.size()));
+    HHG_CUDA_TRY(cudaMalloc(&I->d_cta_start, sizeof(int) * cta_start.size()));
+    HHG_CUDA_TRY(cudaMalloc(&I->d_pstart, sizeof(int) * pstart.size()));
+    HHG_CUDA_TRY(cudaMemcpy(I->d_cta_plane, cta_plane.data(), sizeof(int) * cta_plane.size(), cudaMemcpyHostToDevice));
+    HHG_CUDA_TRY(cudaMemcpy(I->d_cta_start, cta_start.data(), sizeof(int) * cta_start.size(), cudaMemcpyHostToDevice));
+    HHG_CUDA_TRY(cudaMemcpy(I->d_pstart, pstart.data(), sizeof(int) * pstart.size(), cudaMemcpyHostToDevice));
+  }
+  I->h_ptr = ptr;
+  I->h_idx = idx;
+  I->h_bnd = bnd;
   if (I->ngroups > 0) {
     HHG_CUDA_TRY(cudaMalloc(&I->d_ptr, sizeof(int64_t) * ptr.size()));
     HHG_CUDA_TRY(cudaMalloc(&I->d_idx, sizeof(int64_t) * idx.size()));

@@ -69,6 +69,7 @@ static void build_const(hhg_op* op) {
     c.base = (int64_t)m * lattice_size(op->N);
     c.kbase = (int64_t)m * lattice_size(Nk);
     c.bnd_table = g.bnd_table;
+    c.own_table = g.own_table;
     c.N = op->N;
     c.n = n;
     for (int d = 0; d < 3; ++d) c.x0[d] = g.p0[d];
@@ -112,6 +113,37 @@ static void build_const(hhg_op* op) {
           }
       }
     }
+    // quadrature tables for variable coefficients (the op's rule)
+    const QuadRule& rq = op->rule;
+    c.nq = rq.nq();
+    for (int d = 0; d < 3; ++d) c.X0[d] = c.x0[d];
+    for (int a = 0; a < 3; ++a)
+      for (int d = 0; d < 3; ++d) c.H[a][d] = c.h[a][d];
+    for (int q = 0; q < rq.nq() && q < kMaxQ; ++q) {
+      const double* xi = &rq.xi[3 * q];
+      const double lam[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
+      c.w[q] = rq.w[q];
+      for (int a = 0; a < 4; ++a) {
+        c.lam[q][a] = lam[a];
+        c.psi[q][a] = lam[a] * (2.0 * lam[a] - 1.0);
+      }
+      for (int e = 0; e < 6; ++e) c.psi[q][4 + e] = 4.0 * lam[kP2Edges[e][0]] * lam[kP2Edges[e][1]];
+      for (int o = 0; o < 6; ++o) {
+        // index-space offset of the point from the cube origin: off_o[0] + D_o xi
+        double ref[3];
+        for (int a = 0; a < 3; ++a) {
+          ref[a] = kClassOffsets[o][0][a];
+          for (int b = 0; b < 3; ++b) ref[a] += (kClassOffsets[o][b + 1][a] - kClassOffsets[o][0][a]) * xi[b];
+        }
+        for (int d = 0; d < 3; ++d) {
+          double delta = 0;
+          for (int a = 0; a < 3; ++a) delta += c.h[a][d] * ref[a];
+          c.cs[o][q][d][0] = std::cos(2.0 * M_PI * delta);
+          c.cs[o][q][d][1] = std::sin(2.0 * M_PI * delta);
+          c.qoff[o][q][d] = delta;
+        }
+      }
+    }
     if (op->degree == 1) {
       // fold the six per-class matrices into the 15-point stencil of a point whose incident tets all exist
       for (int o = 0; o < 6; ++o)
@@ -133,6 +165,7 @@ static OpConst<T> convert_const(const OpConst<double>& c) {
   o.base = c.base;
   o.kbase = c.kbase;
   o.bnd_table = c.bnd_table;
+  o.own_table = c.own_table;
   o.N = c.N;
   o.n = c.n;
   for (int a = 0; a < 6; ++a)
@@ -145,61 +178,101 @@ static OpConst<T> convert_const(const OpConst<double>& c) {
   }
   std::memcpy(o.x0, c.x0, sizeof(c.x0));
   std::memcpy(o.h, c.h, sizeof(c.h));
+  o.nq = c.nq;
+  for (int q = 0; q < kMaxQ; ++q) {
+    o.w[q] = (T)c.w[q];
+    for (int a = 0; a < 4; ++a) o.lam[q][a] = (T)c.lam[q][a];
+    for (int m = 0; m < 10; ++m) o.psi[q][m] = (T)c.psi[q][m];
+    for (int cl = 0; cl < 6; ++cl)
+      for (int d = 0; d < 3; ++d) {
+        o.qoff[cl][q][d] = (T)c.qoff[cl][q][d];
+        for (int t = 0; t < 2; ++t) o.cs[cl][q][d][t] = (T)c.cs[cl][q][d][t];
+      }
+  }
+  for (int d = 0; d < 3; ++d) {
+    o.X0[d] = (T)c.X0[d];
+    for (int a = 0; a < 3; ++a) o.H[a][d] = (T)c.H[a][d];
+  }
   return o;
 }
 
 // ---------------------------------------------------------------------------
 // Device: P1 constant-coefficient apply (gather; one thread per output point).
+// A CTA covers 256 consecutive points of one plane k; the plane of each CTA and
+// the first packed position of each plane come from small per-level tables, so
+// the index arithmetic is 32-bit and free of divisions.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int tri(int s) { return ((s + 1) * (s + 2)) >> 1; }          // points of a plane
+__device__ __forceinline__ int row32(int s, int j) { return (j * (2 * s + 3 - j)) >> 1; }  // row start in plane
+
 template <typename T, bool DIRICHLET>
 __global__ void __launch_bounds__(256) p1_const_apply_kernel(const OpConst<T>* __restrict__ cst,
+                                                              const int* __restrict__ cta_plane,
+                                                              const int* __restrict__ cta_start,
+                                                              const int* __restrict__ pstart,
                                                               const T* __restrict__ x, T* __restrict__ y) {
   const OpConst<T>& c = cst[blockIdx.y];
   const int N = c.N;
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= dV(N)) return;
-  int i, j, k;
-  decode_point(p, N, i, j, k);
+  const int k = __ldg(cta_plane + blockIdx.x);
+  const int s = N - k;
+  const int q = (blockIdx.x - __ldg(cta_start + k)) * 256 + threadIdx.x;
+  if (q >= tri(s)) return;
+  // row j: largest j with row32(s, j) <= q
+  const float b = 2.0f * s + 3.0f;
+  int j = (int)(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)q, 0.0f))));
+  j = max(0, min(j, s));
+  if (j < s && row32(s, j + 1) <= q) ++j;
+  if (j > 0 && row32(s, j) > q) --j;
+  const int i = q - row32(s, j);
+  const int pk = __ldg(pstart + k);
+  const int p = pk + q;
   const T* __restrict__ xm = x + c.base;
   T* __restrict__ ym = y + c.base;
   const uint32_t table = c.bnd_table;
-  if (DIRICHLET && on_dirichlet(table, N, i, j, k)) {
-    ym[p] = xm[p];
-    return;
-  }
-  const int s = N - k;
-  const bool fast = DIRICHLET ? (i >= 2 && j >= 2 && k >= 2 && i + j + k <= N - 2)
-                              : (i >= 1 && j >= 1 && k >= 1 && i + j + k <= N - 1);
-  T acc;
-  if (fast) {
-    // rows of the 15-point stencil
-    const int64_t r00 = p - i;                                     // (j, k)
-    const int64_t rp0 = r00 + (s + 1 - j);                         // (j+1, k)
-    const int64_t rm0 = r00 - (s + 2 - j);                         // (j-1, k)
-    const int64_t pk1 = plane_start(N, k + 1);
-    const int64_t r01 = pk1 + row_start(s - 1, j);                 // (j, k+1)
-    const int64_t rm1 = pk1 + row_start(s - 1, j - 1);             // (j-1, k+1)
-    const int64_t pkm = plane_start(N, k - 1);
-    const int64_t r0m = pkm + row_start(s + 1, j);                 // (j, k-1)
-    const int64_t rpm = pkm + row_start(s + 1, j + 1);             // (j+1, k-1)
-    acc = c.S[0] * __ldg(xm + r00 + i);
-    acc += c.S[1] * __ldg(xm + r00 + i + 1);
-    acc += c.S[2] * __ldg(xm + r00 + i - 1);
-    acc += c.S[3] * __ldg(xm + rp0 + i);
-    acc += c.S[4] * __ldg(xm + rm0 + i);
-    acc += c.S[5] * __ldg(xm + r01 + i);
-    acc += c.S[6] * __ldg(xm + r0m + i);
-    acc += c.S[7] * __ldg(xm + rm0 + i + 1);
-    acc += c.S[8] * __ldg(xm + rp0 + i - 1);
-    acc += c.S[9] * __ldg(xm + r0m + i + 1);
-    acc += c.S[10] * __ldg(xm + r01 + i - 1);
-    acc += c.S[11] * __ldg(xm + rpm + i);
-    acc += c.S[12] * __ldg(xm + rm1 + i);
-    acc += c.S[13] * __ldg(xm + rm1 + i + 1);
-    acc += c.S[14] * __ldg(xm + rpm + i - 1);
+  const bool on_face = (i == 0) | (j == 0) | (k == 0) | (i + j + k == N);
+  T acc = T(0);
+  if (!on_face) {
+    // all 24 incident micro-tets exist: 15-point stencil
+    const int r00 = p - i;                                 // (j, k)
+    const int rp0 = r00 + (s + 1 - j);                     // (j+1, k)
+    const int rm0 = r00 - (s + 2 - j);                     // (j-1, k)
+    const int pk1 = pk + tri(s);
+    const int r01 = pk1 + row32(s - 1, j);                 // (j, k+1)
+    const int rm1 = pk1 + row32(s - 1, j - 1);             // (j-1, k+1)
+    const int pkm = pk - tri(s + 1);
+    const int r0m = pkm + row32(s + 1, j);                 // (j, k-1)
+    const int rpm = pkm + row32(s + 1, j + 1);             // (j+1, k-1)
+    T v[15];
+    v[0] = __ldg(xm + r00 + i);
+    v[1] = __ldg(xm + r00 + i + 1);
+    v[2] = __ldg(xm + r00 + i - 1);
+    v[3] = __ldg(xm + rp0 + i);
+    v[4] = __ldg(xm + rm0 + i);
+    v[5] = __ldg(xm + r01 + i);
+    v[6] = __ldg(xm + r0m + i);
+    v[7] = __ldg(xm + rm0 + i + 1);
+    v[8] = __ldg(xm + rp0 + i - 1);
+    v[9] = __ldg(xm + r0m + i + 1);
+    v[10] = __ldg(xm + r01 + i - 1);
+    v[11] = __ldg(xm + rpm + i);
+    v[12] = __ldg(xm + rm1 + i);
+    v[13] = __ldg(xm + rm1 + i + 1);
+    v[14] = __ldg(xm + rpm + i - 1);
+    if (DIRICHLET && !(i >= 2 && j >= 2 && k >= 2 && i + j + k <= N - 2)) {
+      // a neighbour may lie on a Dirichlet face: its column is dropped
+#pragma unroll
+      for (int d = 0; d < 15; ++d)
+        if (on_dirichlet(table, N, i + kStencilD[d][0], j + kStencilD[d][1], k + kStencilD[d][2])) v[d] = T(0);
+    }
+#pragma unroll
+    for (int d = 0; d < 15; ++d) acc += c.S[d] * v[d];
   } else {
-    // near the macro boundary: sum the incident micro-tets that exist (Algorithm 1 per tet)
-    acc = T(0);
+    if (DIRICHLET && on_dirichlet(table, N, i, j, k)) {
+      ym[p] = xm[p];
+      return;
+    }
+    // point on a macro face that is not a Dirichlet point (Neumann, or an interface
+    // between macros): sum the incident micro-tets that exist (Algorithm 1 per tet)
     const int n = N;   // P1: one lattice step per cube
 #pragma unroll 1
     for (int o = 0; o < 6; ++o) {
@@ -208,10 +281,11 @@ __global__ void __launch_bounds__(256) p1_const_apply_kernel(const OpConst<T>* _
       for (int a = 0; a < 4; ++a) {
         const int ci = i - kClassOffsetsD[o][a][0], cj = j - kClassOffsetsD[o][a][1], ck = k - kClassOffsetsD[o][a][2];
         if (ci < 0 || cj < 0 || ck < 0 || ci + cj + ck > lim) continue;
-        for (int b = 0; b < 4; ++b) {
-          const int pi = ci + kClassOffsetsD[o][b][0], pj = cj + kClassOffsetsD[o][b][1], pk = ck + kClassOffsetsD[o][b][2];
-          if (DIRICHLET && on_dirichlet(table, N, pi, pj, pk)) continue;
-          acc += c.A[o][a][b] * __ldg(xm + packed_index(N, pi, pj, pk));
+        for (int b2 = 0; b2 < 4; ++b2) {
+          const int pi = ci + kClassOffsetsD[o][b2][0], pj = cj + kClassOffsetsD[o][b2][1],
+                    pkk = ck + kClassOffsetsD[o][b2][2];
+          if (DIRICHLET && on_dirichlet(table, N, pi, pj, pkk)) continue;
+          acc += c.A[o][a][b2] * __ldg(xm + __ldg(pstart + pkk) + row32(N - pkk, pj) + pi);
         }
       }
     }
@@ -344,6 +418,11 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int nb, 
   if (threadIdx.x == 0) out[0] = red[0];
 }
 
+template int launch_interface_sum<double>(const Interface*, double*, int, bool, cudaStream_t);
+template int launch_interface_sum<float>(const Interface*, float*, int, bool, cudaStream_t);
+template int launch_make_consistent<double>(const Interface*, double*, int, cudaStream_t);
+template int launch_make_consistent<float>(const Interface*, float*, int, cudaStream_t);
+
 constexpr int kDotBlocks = 304;   // 2 x 152 SMs
 
 template <typename T>
@@ -371,18 +450,29 @@ const OpConst<float>* dconst<float>(const hhg_op* op) {
 }
 
 template <typename T>
+const T* field_ptr(const hhg_op* op) {
+  return (op->coeff.type == HHG_COEFF_FIELD_P1 || op->coeff.type == HHG_COEFF_FIELD_P2) ? (const T*)op->coeff.field
+                                                                                          : nullptr;
+}
+
+template <typename T>
 int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
   const int64_t V = lattice_size(op->N);
   const int nm = op->mesh->nmacro();
   if (op->kind == HHG_DIFFUSION && op->degree == 1 && op->coeff.type == HHG_COEFF_CONST) {
-    dim3 grid((unsigned)((V + 255) / 256), nm);
+    (void)V;
+    const Interface* I = op->itf;
+    dim3 grid((unsigned)I->ncta, nm);
     if (op->bc == HHG_DIRICHLET)
-      p1_const_apply_kernel<T, true><<<grid, 256, 0, s>>>(dconst<T>(op), x, y);
+      p1_const_apply_kernel<T, true><<<grid, 256, 0, s>>>(dconst<T>(op), I->d_cta_plane, I->d_cta_start,
+                                                          I->d_pstart, x, y);
     else
-      p1_const_apply_kernel<T, false><<<grid, 256, 0, s>>>(dconst<T>(op), x, y);
+      p1_const_apply_kernel<T, false><<<grid, 256, 0, s>>>(dconst<T>(op), I->d_cta_plane, I->d_cta_start,
+                                                           I->d_pstart, x, y);
     HHG_CUDA_TRY(cudaGetLastError());
     return HHG_OK;
   }
+  if (op->kind == HHG_DIFFUSION) return launch_march<T>(op, dconst<T>(op), 0, x, nullptr, field_ptr<T>(op), y, s);
   return fail(HHG_E_UNSUPPORTED, "apply: operator kind %d degree %d coefficient %d not implemented", op->kind,
               op->degree, op->coeff.type);
 }
@@ -396,6 +486,7 @@ int launch_diag(const hhg_op* op, T* d, cudaStream_t s) {
     HHG_CUDA_TRY(cudaGetLastError());
     return HHG_OK;
   }
+  if (op->kind == HHG_DIFFUSION) return launch_march<T>(op, dconst<T>(op), 1, nullptr, nullptr, field_ptr<T>(op), d, s);
   return fail(HHG_E_UNSUPPORTED, "diagonal: operator not implemented");
 }
 
@@ -404,12 +495,22 @@ int launch_diag(const hhg_op* op, T* d, cudaStream_t s) {
 using namespace hhg;
 
 hhg_op::~hhg_op() {
+  if (mg) hhg::destroy_mg(mg);
+  if (work) hhg::destroy_work(work);
   cudaFree(d_const64);
   cudaFree(d_const32);
 }
 
 static int check_dtype(int dtype) {
   if (dtype != HHG_F32 && dtype != HHG_F64) return fail(HHG_E_ARG, "dtype must be HHG_F32 or HHG_F64");
+  return HHG_OK;
+}
+
+static int check_field(const hhg_op* op, int dtype) {
+  if (op->coeff.type != HHG_COEFF_FIELD_P1 && op->coeff.type != HHG_COEFF_FIELD_P2) return HHG_OK;
+  if (!op->coeff.field) return fail(HHG_E_ARG, "coefficient field pointer is null");
+  if (op->coeff.field_dtype != dtype)
+    return fail(HHG_E_ARG, "coefficient field dtype %d differs from the apply dtype %d", op->coeff.field_dtype, dtype);
   return HHG_OK;
 }
 
@@ -426,6 +527,10 @@ extern "C" int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, 
   if (bc != HHG_DIRICHLET && bc != HHG_NEUMANN) return fail(HHG_E_ARG, "op_create: unknown boundary mode %d", bc);
   if (coeff->type < HHG_COEFF_CONST || coeff->type > HHG_COEFF_FIELD_P2)
     return fail(HHG_E_ARG, "op_create: unknown coefficient type %d", coeff->type);
+  if ((coeff->type == HHG_COEFF_FIELD_P1 && degree != 1) || (coeff->type == HHG_COEFF_FIELD_P2 && degree != 2))
+    return fail(HHG_E_UNSUPPORTED, "op_create: the coefficient field must have the operator's degree");
+  if ((coeff->type == HHG_COEFF_SIN3 || coeff->type == HHG_COEFF_FIELD_P2) && quad_degree > 5)
+    return fail(HHG_E_UNSUPPORTED, "op_create: quadrature degree above 5");
   std::unique_ptr<hhg_op> op(new hhg_op());
   op->mesh = mesh;
   op->level = level;
@@ -443,6 +548,7 @@ extern "C" int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, 
   if (coeff->type == HHG_COEFF_FIELD_P1 || coeff->type == HHG_COEFF_FIELD_P2)
     HHG_TRY(mesh->interface(level, coeff->type == HHG_COEFF_FIELD_P1 ? 1 : 2, &itf));
   build_const(op.get());
+  HHG_TRY(mesh->interface(level, degree, &op->itf));
   const int nm = mesh->nmacro();
   std::vector<OpConst<float>> c32(nm);
   for (int m = 0; m < nm; ++m) c32[m] = convert_const<float>(op->h_const[m]);
@@ -476,6 +582,7 @@ extern "C" int hhg_op_apply(hhg_op_t* op, const void* x, void* y, int dtype, int
   HHG_TRY(check_dtype(dtype));
   if (nrhs < 1 || (nrhs > 1 && op->kind != HHG_EPSILON)) return fail(HHG_E_ARG, "op_apply: bad nrhs %d", nrhs);
   if (x == y) return fail(HHG_E_ARG, "op_apply: x and y must not overlap");
+  HHG_TRY(check_field(op, dtype));
   cudaStream_t s = (cudaStream_t)stream;
   const Interface* itf = nullptr;
   HHG_TRY(op->mesh->interface(op->level, op->degree, &itf));
@@ -494,6 +601,7 @@ extern "C" int hhg_op_diagonal(hhg_op_t* op, void* d, int dtype, void* stream) {
   if (!op || !d) return fail(HHG_E_ARG, "op_diagonal: null pointer");
   HHG_TRY(check_dtype(dtype));
   if (op->kind != HHG_DIFFUSION) return fail(HHG_E_UNSUPPORTED, "op_diagonal: scalar operators only");
+  HHG_TRY(check_field(op, dtype));
   cudaStream_t s = (cudaStream_t)stream;
   const Interface* itf = nullptr;
   HHG_TRY(op->mesh->interface(op->level, op->degree, &itf));
@@ -536,5 +644,30 @@ extern "C" int hhg_vec_dot(const hhg_mesh_t* mesh, int level, int degree, const 
     HHG_TRY(launch_dot<float>(itf, (const float*)x, (const float*)y, n, n_per_point, d, s));
   HHG_CUDA_TRY(cudaMemcpyAsync(result, d, sizeof(double), cudaMemcpyDeviceToHost, s));
   HHG_CUDA_TRY(cudaStreamSynchronize(s));
+  return HHG_OK;
+}
+
+extern "C" int hhg_op_apply_adjoint_coeff(hhg_op_t* op, const void* u, const void* g, void* dk, int dtype, int nrhs,
+                                          void* stream) {
+  clear_error();
+  if (!op || !u || !g || !dk) return fail(HHG_E_ARG, "op_apply_adjoint_coeff: null pointer");
+  HHG_TRY(check_dtype(dtype));
+  if (op->coeff.type != HHG_COEFF_FIELD_P1 && op->coeff.type != HHG_COEFF_FIELD_P2)
+    return fail(HHG_E_UNSUPPORTED, "op_apply_adjoint_coeff: the coefficient is not a field");
+  if (op->kind != HHG_DIFFUSION) return fail(HHG_E_UNSUPPORTED, "op_apply_adjoint_coeff: diffusion operators only");
+  if (nrhs != 1) return fail(HHG_E_ARG, "op_apply_adjoint_coeff: nrhs must be 1 for scalar operators");
+  HHG_TRY(check_field(op, dtype));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Interface* itf = nullptr;
+  HHG_TRY(op->mesh->interface(op->level, op->degree, &itf));
+  if (dtype == HHG_F64) {
+    HHG_TRY(launch_march<double>(op, dconst<double>(op), 2, (const double*)u, (const double*)g,
+                                 field_ptr<double>(op), (double*)dk, s));
+    HHG_TRY(launch_interface_sum<double>(itf, (double*)dk, 1, false, s));
+  } else {
+    HHG_TRY(launch_march<float>(op, dconst<float>(op), 2, (const float*)u, (const float*)g, field_ptr<float>(op),
+                                (float*)dk, s));
+    HHG_TRY(launch_interface_sum<float>(itf, (float*)dk, 1, false, s));
+  }
   return HHG_OK;
 }

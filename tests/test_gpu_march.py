@@ -1,0 +1,128 @@
+"""Variable-coefficient and P2 operators through the C-ABI against the oracle (Eq. P2V, Eq. 6.1, Algorithm 1)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import assemble as OA, layout as OL
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+QD = {1: 2, 2: 4}
+
+
+def _coeff(case, kind, dtype):
+    """(library coefficient, oracle coefficient, rounded-input flag)."""
+    if kind == "const":
+        return ("const", 1.3), ("const", 1.3)
+    if kind == "sin3":
+        return ("sin3",), ("sin3",)
+    kg = np.exp(W.fourier_field(case.S.coords, seed=0))
+    if dtype == torch.float32:
+        kg = kg.astype(np.float32).astype(np.float64)
+    field = case.packed(kg, dtype)
+    return ("field_p%d" % case.degree, field), ("field", case.S, kg)
+
+
+CASES = [("reference_tet", 0), ("reference_tet", 1), ("reference_tet", 3), ("cube6", 2), ("cube48", 1), ("cuboid36", 1)]
+
+
+@pytest.mark.parametrize("meshname,level", CASES)
+@pytest.mark.parametrize("degree,kind", [(1, "sin3"), (1, "field"), (2, "const"), (2, "sin3"), (2, "field")])
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_apply_parity(meshname, level, degree, kind, bc, dtype):
+    from gpu_helpers import Case, rel_err
+    import paper_2404_08371_gb300 as hhg
+    c = Case(meshname, level, degree)
+    lc, oc = _coeff(c, kind, dtype)
+    op = hhg.Operator(c.mesh, degree=degree, coeff=lc, bc=bc, quad_degree=QD[degree])
+    xg = W.uniform(c.S.ndof, seed=0)
+    if dtype == torch.float32:
+        xg = xg.astype(np.float32).astype(np.float64)
+    y = op.apply(c.packed(xg, dtype))
+    ref = OA.diffusion_matrix(c.S, oc, QD[degree], bc) @ xg
+    got, spread = c.unpack(y)
+    assert rel_err(got, ref) <= TOL[dtype], rel_err(got, ref)
+    assert spread == 0.0
+
+
+@pytest.mark.parametrize("meshname,level", [("reference_tet", 2), ("cube6", 1), ("cube48", 1)])
+@pytest.mark.parametrize("degree,kind", [(1, "sin3"), (1, "field"), (2, "const"), (2, "sin3"), (2, "field")])
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_diagonal_parity(meshname, level, degree, kind, bc):
+    from gpu_helpers import Case, rel_err
+    import paper_2404_08371_gb300 as hhg
+    c = Case(meshname, level, degree)
+    lc, oc = _coeff(c, kind, torch.float64)
+    op = hhg.Operator(c.mesh, degree=degree, coeff=lc, bc=bc, quad_degree=QD[degree])
+    d = op.diagonal(torch.float64)
+    ref = OA.diffusion_matrix(c.S, oc, QD[degree], bc).diagonal()
+    got, spread = c.unpack(d)
+    assert rel_err(got, ref) <= 1e-12 and spread == 0.0
+
+
+@pytest.mark.parametrize("meshname,level", [("reference_tet", 0), ("reference_tet", 3), ("cube6", 2), ("cube48", 1)])
+@pytest.mark.parametrize("degree", [1, 2])
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_adjoint_parity(meshname, level, degree, bc, dtype):
+    from gpu_helpers import Case, rel_err
+    import paper_2404_08371_gb300 as hhg
+    c = Case(meshname, level, degree)
+    lc, oc = _coeff(c, "field", dtype)
+    op = hhg.Operator(c.mesh, degree=degree, coeff=lc, bc=bc, quad_degree=QD[degree])
+    u = W.uniform(c.S.ndof, seed=1)
+    g = W.uniform(c.S.ndof, seed=2)
+    if dtype == torch.float32:
+        u = u.astype(np.float32).astype(np.float64)
+        g = g.astype(np.float32).astype(np.float64)
+    dk = op.adjoint_coeff(c.packed(u, dtype), c.packed(g, dtype))
+    ref = OA.diffusion_coeff_adjoint(c.S, c.S, u, g, QD[degree], bc)
+    got, spread = c.unpack(dk)
+    assert rel_err(got, ref) <= (1e-12 if dtype == torch.float64 else 2e-5), rel_err(got, ref)
+    assert spread == 0.0
+
+
+def test_field_dtype_mismatch_rejected():
+    from gpu_helpers import Case
+    import paper_2404_08371_gb300 as hhg
+    c = Case("reference_tet", 1, 1)
+    lc, _ = _coeff(c, "field", torch.float64)
+    op = hhg.Operator(c.mesh, degree=1, coeff=lc)
+    with pytest.raises(hhg.HHGError):
+        op.apply(torch.zeros(c.mesh.vec_size(1), dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+def test_level8_sampled_sin3(degree):
+    """The level-8 workload: sampled rows of the analytic-coefficient apply against the oracle's per-point sums."""
+    import paper_2404_08371_gb300 as hhg
+    from oracle import mesh as OM
+    v, t = W.reference_tet()
+    level = 8
+    mesh = hhg.Mesh(v, t, level)
+    op = hhg.Operator(mesh, degree=degree, coeff=("sin3",), bc="dirichlet", quad_degree=QD[degree])
+    N = degree * 2 ** level
+    n = mesh.vec_size(degree)
+    xp = W.uniform(n, seed=0)
+    y = op.apply(torch.tensor(xp, device="cuda")).cpu().numpy()
+    rng = np.random.default_rng(2)
+    sample = rng.choice(n, 200, replace=False)
+    pts = np.empty((len(sample), 3), dtype=np.int64)
+    # lattice points of the sampled packed positions (from the layout definition)
+    allpos = OM.packed_position
+    planes = np.array([OM.lattice_size(N) - OM.lattice_size(N - k) for k in range(N + 2)])
+    for e, p in enumerate(sample):
+        k = np.searchsorted(planes, p, side="right") - 1
+        q = p - planes[k]
+        s = N - k
+        j = 0
+        while (j + 1) * (s + 1) - (j + 1) * j // 2 <= q:
+            j += 1
+        i = q - (j * (s + 1) - j * (j - 1) // 2)
+        pts[e] = (i, j, k)
+        assert allpos(pts[e:e + 1], N)[0] == p
+    ref = OA.sampled_diffusion_rows(v[t[0]], level, degree, ("sin3",), QD[degree], "dirichlet", xp, pts)
+    assert np.abs(y[sample] - ref).max() <= 1e-12 * np.abs(y).max()
