@@ -272,7 +272,8 @@ __global__ void cheb_update_kernel(int64_t n, const T* __restrict__ b, const T* 
                                    const T* __restrict__ dinv, T* __restrict__ x, T* __restrict__ d, T alpha, T beta) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
-    const T dv = alpha * d[t] + beta * dinv[t] * (b[t] - y[t]);
+    // the first step of a smoothing call (alpha = 0) must not read d: it holds the previous call's values
+    const T dv = (alpha == T(0) ? T(0) : alpha * d[t]) + beta * dinv[t] * (b[t] - y[t]);
     d[t] = dv;
     x[t] += dv;
   }
