@@ -63,8 +63,16 @@ struct Interface {
   int* d_cta_plane = nullptr;   // plane of each CTA
   int* d_cta_start = nullptr;   // first CTA of each plane (N + 2 entries)
   int* d_pstart = nullptr;      // first packed position of each plane (N + 2 entries)
+  // task list of the marching kernels: (i-tile, j-tile, k-chunk, macro), heaviest first
+  int4* d_march_tasks = nullptr;
+  int64_t n_march_tasks = 0;
+  int march_kchunk = 32;
   ~Interface();
 };
+
+// Tile shape of the marching kernels (march.cu): 32 lanes along i (31 owned), kMarchWarps warps
+// along j (kMarchWarps - 1 owned), march_kchunk cube layers along k.
+constexpr int kMarchWarps = 8;
 
 // Quadrature rule on the reference tetrahedron (volume 1/6).
 struct QuadRule {

@@ -24,8 +24,7 @@
 
 namespace hhg {
 
-constexpr int kWarps = 8;     // warps per CTA along j
-constexpr int kChunk = 32;    // cube layers per CTA along k
+constexpr int kWarps = kMarchWarps;   // warps per CTA along j
 
 enum { MODE_APPLY = 0, MODE_DIAG = 1, MODE_ADJ = 2, MODE_RHS = 3 };
 
@@ -108,7 +107,8 @@ __device__ __forceinline__ void sincos2pi<float>(float x, float* s, float* c) {
 }
 
 template <typename T, int R, int COEF, int MODE, bool DIR>
-__global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __restrict__ cst, int nkc,
+__global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __restrict__ cst,
+                                                            const int4* __restrict__ tasks, int kChunk,
                                                             const T* __restrict__ x, const T* __restrict__ g,
                                                             const T* __restrict__ kf, T* __restrict__ out) {
   constexpr int P = R + 1;
@@ -116,8 +116,9 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
   constexpr int NL = R == 1 ? 4 : 10;
   __shared__ OpConst<T> c;
   __shared__ T xch[kWarps][P][R][32];
-  const int macro = blockIdx.z / nkc;
-  const int kc = blockIdx.z - macro * nkc;
+  const int4 task = tasks[blockIdx.x];   // (i-tile, j-tile, k-chunk, macro), heaviest first
+  const int macro = task.w;
+  const int kc = task.z;
   {
     const int4* src = reinterpret_cast<const int4*>(cst + macro);
     int4* dst = reinterpret_cast<int4*>(&c);
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n = c.n, N = c.N;
-  const int ti0 = 31 * blockIdx.x, tj0 = (kWarps - 1) * blockIdx.y, K0 = kChunk * kc;
+  const int ti0 = 31 * task.x, tj0 = (kWarps - 1) * task.y, K0 = kChunk * kc;
   if (ti0 + tj0 + K0 > n) return;   // lowest point owned by the CTA lies outside the macro (uniform)
   const int ci = ti0 + lane - 1;
   const int cj = tj0 + warp - 1;
@@ -360,16 +361,14 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
 template <typename T, int R, int COEF, int MODE>
 static int launch_march_t(const hhg_op* op, const OpConst<T>* cst, const T* x, const T* g, const T* kf, T* out,
                           cudaStream_t s) {
-  const int N = op->N;
-  const int n = op->n;
-  dim3 grid((unsigned)((n + 31) / 31 + 1), (unsigned)((n + kWarps - 1) / (kWarps - 1) + 1), 1);
-  const int nkc = (n + 1 + kChunk - 1) / kChunk;
-  grid.z = (unsigned)(nkc * op->mesh->nmacro());
-  (void)N;
+  const Interface* I = op->itf;
+  const unsigned grid = (unsigned)I->n_march_tasks;
   if (op->bc == HHG_DIRICHLET)
-    march_kernel<T, R, COEF, MODE, true><<<grid, 32 * kWarps, 0, s>>>(cst, nkc, x, g, kf, out);
+    march_kernel<T, R, COEF, MODE, true><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x, g, kf,
+                                                                       out);
   else
-    march_kernel<T, R, COEF, MODE, false><<<grid, 32 * kWarps, 0, s>>>(cst, nkc, x, g, kf, out);
+    march_kernel<T, R, COEF, MODE, false><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x, g,
+                                                                        kf, out);
   HHG_CUDA_TRY(cudaGetLastError());
   return HHG_OK;
 }

@@ -53,6 +53,7 @@ Interface::~Interface() {
   cudaFree(d_cta_plane);
   cudaFree(d_cta_start);
   cudaFree(d_pstart);
+  cudaFree(d_march_tasks);
 }
 
 // ---------------------------------------------------------------------------
@@ -446,6 +447,42 @@ int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
     HHG_CUDA_TRY(cudaMemcpy(I->d_cta_plane, cta_plane.data(), sizeof(int) * cta_plane.size(), cudaMemcpyHostToDevice));
     HHG_CUDA_TRY(cudaMemcpy(I->d_cta_start, cta_start.data(), sizeof(int) * cta_start.size(), cudaMemcpyHostToDevice));
     HHG_CUDA_TRY(cudaMemcpy(I->d_pstart, pstart.data(), sizeof(int) * pstart.size(), cudaMemcpyHostToDevice));
+  }
+  // marching-kernel tasks: every tile with owned points, sorted by its number of cubes (longest
+  // first), with the k-chunk shortened until there are enough tasks to fill the GPU
+  {
+    const int64_t n = (int64_t)1 << lvl;
+    const int jw = kMarchWarps - 1;
+    int kch = 32;
+    std::vector<std::pair<int64_t, int4>> tasks;
+    for (;;) {
+      tasks.clear();
+      for (int64_t kc = 0; kc * kch <= n; ++kc)
+        for (int64_t ty = 0; ty * jw + kc * kch <= n; ++ty)
+          for (int64_t tx = 0; tx * 31 + ty * jw + kc * kch <= n; ++tx) {
+            int64_t work = 1;   // the top layer still writes carried points
+            for (int64_t ck = std::max<int64_t>(kc * kch - 1, 0); ck <= kc * kch + kch - 1; ++ck)
+              for (int64_t cj = std::max<int64_t>(ty * jw - 1, 0); cj <= ty * jw + jw - 1; ++cj) {
+                const int64_t hi = std::min<int64_t>(tx * 31 + 30, n - 1 - cj - ck), lo = std::max<int64_t>(tx * 31 - 1, 0);
+                if (hi >= lo) work += hi - lo + 1;
+              }
+            tasks.push_back({work, int4{(int)tx, (int)ty, (int)kc, 0}});
+          }
+      if (kch <= 4 || (int64_t)tasks.size() * nmacro() >= 4 * 152) break;
+      kch /= 2;
+    }
+    std::vector<std::pair<int64_t, int4>> all;
+    for (int mac = 0; mac < nmacro(); ++mac)
+      for (auto& t : tasks) all.push_back({t.first, int4{t.second.x, t.second.y, t.second.z, mac}});
+    std::stable_sort(all.begin(), all.end(), [](const std::pair<int64_t, int4>& a, const std::pair<int64_t, int4>& b) {
+      return a.first > b.first;
+    });
+    std::vector<int4> tv(all.size());
+    for (size_t t = 0; t < all.size(); ++t) tv[t] = all[t].second;
+    I->march_kchunk = kch;
+    I->n_march_tasks = (int64_t)tv.size();
+    HHG_CUDA_TRY(cudaMalloc(&I->d_march_tasks, sizeof(int4) * tv.size()));
+    HHG_CUDA_TRY(cudaMemcpy(I->d_march_tasks, tv.data(), sizeof(int4) * tv.size(), cudaMemcpyHostToDevice));
   }
   I->h_ptr = ptr;
   I->h_idx = idx;
