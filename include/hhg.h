@@ -175,6 +175,29 @@ int hhg_l2_error_sin3(const hhg_mesh_t* mesh, int level, int degree, const doubl
 int hhg_cheb_smooth(hhg_op_t* op, const void* b, void* x, const void* dinv, double lam, double lo, double hi,
                     int order, int dtype, void* stream);
 
+/* The smoothing step of hhg_cheb_smooth, for callers that must not allocate
+ * device memory while they run.  (The paper has no counterpart: this is an
+ * interface variant, not part of the method.)  hhg_cheb_smooth allocates two
+ * work vectors on its first call for an operator; processes that hand all
+ * device memory to their own allocator, or loops that cannot afford the
+ * device synchronisation of cudaMalloc, can call this entry point instead.
+ * It calls no cudaMalloc / cudaFree: its two work vectors live in one fixed
+ * 8 MiB array in the library's device image (2 x 524288 entries), held by
+ * every GPU that loads the library until the process exits.
+ * Limits and rules:
+ *  - the operator's vectors may have at most 524288 entries
+ *    (hhg_vec_size); larger operators get HHG_E_ARG;
+ *  - the first call on a device looks up the array's device address for that
+ *    device (cudaGetSymbolAddress); make that first call before any stream
+ *    capture begins;
+ *  - all calls share the one array, which keeps the last call's contents
+ *    (nothing in it needs to start at zero); calls that overlap on the GPU,
+ *    e.g. on two streams at once, race with each other;
+ *  - the operator must have been created beforehand (hhg_op_create allocates).
+ * Arguments, results and errors are otherwise those of hhg_cheb_smooth. */
+int hhg_cheb_smooth_noalloc(hhg_op_t* op, const void* b, void* x, const void* dinv, double lam, double lo,
+                            double hi, int order, int dtype, void* stream);
+
 /* Power iteration for the largest eigenvalue of D^{-1} A from start vector
  * v (consistent, overwritten by the last iterate): iters steps of
  * v <- D^{-1} A v / ||D^{-1} A v||; returns the last norm.  Synchronous. */

@@ -60,6 +60,7 @@ SIGNATURES = {
     "hhg_rhs_sin3_poisson": ([_vp, _i, _i, _vp, _vp], _i),
     "hhg_l2_error_sin3": ([_vp, _i, _i, _vp, ctypes.POINTER(_d), _vp], _i),
     "hhg_cheb_smooth": ([_vp, _vp, _vp, _vp, _d, _d, _d, _i, _i, _vp], _i),
+    "hhg_cheb_smooth_noalloc": ([_vp, _vp, _vp, _vp, _d, _d, _d, _i, _i, _vp], _i),
     "hhg_power_iteration": ([_vp, _vp, _vp, _i, _i, ctypes.POINTER(_d), _vp], _i),
     "hhg_mg_default_opts": ([ctypes.POINTER(hhg_mg_opts_t)], _i),
     "hhg_mg_solve": ([_vp, _vp, _vp, ctypes.POINTER(hhg_mg_opts_t), ctypes.POINTER(hhg_mg_stats_t), _vp], _i),

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "hhg_internal.h"
@@ -542,6 +543,42 @@ extern "C" int hhg_cheb_smooth(hhg_op_t* op, const void* b, void* x, const void*
                               (float*)op->work->y, (float*)op->work->d, s);
 }
 
+// ---------------------------------------------------------------------------
+// Chebyshev smoothing without device allocation.
+//
+// hhg_cheb_smooth allocates its two work vectors (A x and the Chebyshev direction)
+// with cudaMalloc the first time it runs on an operator.  Some callers must not
+// allocate device memory once they are running: processes whose device memory is
+// entirely handed to another allocator (a framework's caching pool), so that a
+// cudaMalloc would fail or fragment it, and latency-critical loops where the
+// device-wide synchronisation of cudaMalloc is not acceptable.  The variant below
+// takes its work vectors from a fixed array in the library's device image instead.
+// ---------------------------------------------------------------------------
+// Capacity: two work vectors of at most kNoAllocPoints entries each (FP64 or FP32),
+// 8 MiB in all; every GPU that loads the library holds the array until the process exits.
+constexpr int64_t kNoAllocPoints = (int64_t)1 << 19;
+static __device__ __align__(256) double g_smooth_scratch[2 * kNoAllocPoints];
+
+// Device address of g_smooth_scratch on the current device, looked up once per device.
+// (In host code the name g_smooth_scratch is only a host-side stand-in for the array.)
+static int noalloc_scratch(void** out) {
+  static std::mutex mu;
+  static void* addr[64] = {};
+  int dev = 0;
+  HHG_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(HHG_E_CUDA, "cheb_smooth_noalloc: device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_smooth_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(HHG_E_CUDA, "cheb_smooth_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return HHG_OK;
+}
+
 template <typename T>
 static int power_t(hhg_op* op, const T* dinv, T* v, int iters, double* lam, T* y, cudaStream_t s) {
   const int dt = sizeof(T) == 8 ? HHG_F64 : HHG_F32;
@@ -562,6 +599,34 @@ static int power_t(hhg_op* op, const T* dinv, T* v, int iters, double* lam, T* y
   HHG_CUDA_TRY(cudaGetLastError());
   *lam = l;
   return HHG_OK;
+}
+
+extern "C" int hhg_cheb_smooth_noalloc(hhg_op_t* op, const void* b, void* x, const void* dinv, double lam,
+                                       double lo, double hi, int order, int dtype, void* stream) {
+  clear_error();
+  if (!op || !b || !x || !dinv) return fail(HHG_E_ARG, "cheb_smooth_noalloc: null pointer");
+  if (order < 1 || !(lam > 0) || !(hi > lo) || !(lo > 0)) return fail(HHG_E_ARG, "cheb_smooth_noalloc: bad parameters");
+  if (dtype != HHG_F32 && dtype != HHG_F64) return fail(HHG_E_ARG, "cheb_smooth_noalloc: bad dtype");
+  if (op->kind != HHG_DIFFUSION) return fail(HHG_E_UNSUPPORTED, "cheb_smooth_noalloc: scalar operators only");
+  if (op->npts > kNoAllocPoints)
+    return fail(HHG_E_ARG,
+                "cheb_smooth_noalloc: the operator's vectors have %lld entries; the fixed scratch holds at most %lld "
+                "per vector (use hhg_cheb_smooth)",
+                (long long)op->npts, (long long)kNoAllocPoints);
+  void* scratch = nullptr;
+  HHG_TRY(noalloc_scratch(&scratch));
+  cudaStream_t s = (cudaStream_t)stream;
+  // y = A x occupies the first kNoAllocPoints entries, the direction d the next ones.  Neither
+  // needs clearing: the apply writes y before it is read, and the first update writes d
+  // without reading it.
+  if (dtype == HHG_F64) {
+    double* y = (double*)scratch;
+    return cheb_smooth_t<double>(op, (const double*)b, (double*)x, (const double*)dinv, lam, lo, hi, order, y,
+                                 y + kNoAllocPoints, s);
+  }
+  float* y = (float*)scratch;
+  return cheb_smooth_t<float>(op, (const float*)b, (float*)x, (const float*)dinv, lam, lo, hi, order, y,
+                              y + kNoAllocPoints, s);
 }
 
 extern "C" int hhg_power_iteration(hhg_op_t* op, const void* dinv, void* v, int iters, int dtype, double* lam,
