@@ -139,6 +139,12 @@ int hhg_op_apply_adjoint_coeff(hhg_op_t* op, const void* u, const void* g, void*
 /* d = diag(A) (Dirichlet rows: 1), packed, overwritten (scalar ops). */
 int hhg_op_diagonal(hhg_op_t* op, void* d, int dtype, void* stream);
 
+/* Physical coordinates of every packed point of a degree-p space at `level`:
+ * xyz (device, FP64) receives 3 values per point, (x, y, z), in the packed
+ * order (nmacro * V(p * 2^level) points), overwritten.  Use it to sample
+ * coefficient fields or initial data. */
+int hhg_vec_coordinates(const hhg_mesh_t* mesh, int level, int degree, double* xyz, void* stream);
+
 /* Make a packed vector consistent: every copy of a shared point takes the
  * value of its copy in the lowest-numbered macro.  n_per_point = ncomp*nrhs. */
 int hhg_vec_make_consistent(const hhg_mesh_t* mesh, int level, int degree, void* x, int dtype,

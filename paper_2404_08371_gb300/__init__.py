@@ -78,6 +78,13 @@ class Mesh:
     def empty(self, degree: int, dtype=torch.float64, level: int | None = None, per_point: int = 1):
         return torch.empty(self.vec_size(degree, level) * per_point, dtype=dtype, device=self.device)
 
+    def coordinates(self, degree: int, level: int | None = None) -> torch.Tensor:
+        """Physical coordinates (npoints, 3) of the packed points of a degree-p space."""
+        lvl = self.level if level is None else level
+        xyz = torch.empty(self.vec_size(degree, lvl) * 3, dtype=torch.float64, device=self.device)
+        check(lib.hhg_vec_coordinates(self.handle, lvl, degree, _dev_ptr(xyz), _stream()), "hhg_vec_coordinates")
+        return xyz.view(-1, 3)
+
     def make_consistent(self, x: torch.Tensor, degree: int, level: int | None = None, per_point: int = 1):
         check(lib.hhg_vec_make_consistent(self.handle, self.level if level is None else level, degree, _dev_ptr(x),
                                           dtype_code(x), per_point, _stream()), "hhg_vec_make_consistent")

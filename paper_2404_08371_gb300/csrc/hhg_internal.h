@@ -67,12 +67,19 @@ struct Interface {
   int4* d_march_tasks = nullptr;
   int64_t n_march_tasks = 0;
   int march_kchunk = 32;
+  // task list of the P1 stencil kernel: (i-chunk, row group, k-chunk, macro), heaviest first
+  int4* d_stencil_tasks = nullptr;
+  int64_t n_stencil_tasks = 0;
+  int stencil_kchunk = 32;
   ~Interface();
 };
 
 // Tile shape of the marching kernels (march.cu): 32 lanes along i (31 owned), kMarchWarps warps
 // along j (kMarchWarps - 1 owned), march_kchunk cube layers along k.
 constexpr int kMarchWarps = 8;
+// Tile of the P1 stencil kernel (ops.cu): 8 warps = 8 rows j, 32 lanes x kStencilV points along i.
+constexpr int kStencilWarps = 8;
+constexpr int kStencilV = 4;
 
 // Quadrature rule on the reference tetrahedron (volume 1/6).
 struct QuadRule {
@@ -118,8 +125,10 @@ struct alignas(16) OpConst {
   int n;                 // cubes per edge (2^level)
   T A[6][10][10];        // hoisted constant-coefficient local matrices per class (P1 uses [4][4])
   T S[15];               // P1 interior 15-point stencil (offset order kStencil)
+  T Sface[4][15];        // P1 stencil of a point inside macro face a (the face with weight a = 0)
   T M[6][6];             // per class |det J| J^{-1} J^{-T} (xx, yy, zz, xy, xz, yz)
   T adet[6];             // per class |det J| of the micro-tet map
+  T Jinv[6][9];          // per class J^{-1}, row-major
   uint32_t own_table;    // see MacroGeom
   double x0[3];          // physical position of lattice point (0,0,0)
   double h[3][3];        // h[a] = e[a] / n: physical step of one cube along index axis a
@@ -150,6 +159,10 @@ int launch_make_consistent(const Interface* itf, T* x, int per_point, cudaStream
 template <typename T>
 int launch_march(const struct ::hhg_op* op, const OpConst<T>* cst, int mode, const T* x, const T* g, const T* kf,
                  T* out, cudaStream_t s);
+// P2 vector epsilon operator (eps.cu): mode 0 apply to nrhs right-hand sides, 2 adjoint in mu.
+template <typename T>
+int launch_eps(const struct ::hhg_op* op, const OpConst<T>* cst, int mode, int nrhs, const T* x, const T* g,
+               const T* mu, T* out, cudaStream_t s);
 // Squared L2 error of u_h against sin(pi x) sin(pi y) sin(pi z): per-CTA partial sums.
 int64_t launch_l2_blocks(const struct ::hhg_op* op);
 int launch_l2_error(const struct ::hhg_op* op, const double* uh, double* partial, cudaStream_t s);

@@ -54,6 +54,7 @@ Interface::~Interface() {
   cudaFree(d_cta_start);
   cudaFree(d_pstart);
   cudaFree(d_march_tasks);
+  cudaFree(d_stencil_tasks);
 }
 
 // ---------------------------------------------------------------------------
@@ -483,6 +484,40 @@ int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
     I->n_march_tasks = (int64_t)tv.size();
     HHG_CUDA_TRY(cudaMalloc(&I->d_march_tasks, sizeof(int4) * tv.size()));
     HHG_CUDA_TRY(cudaMemcpy(I->d_march_tasks, tv.data(), sizeof(int4) * tv.size(), cudaMemcpyHostToDevice));
+  }
+  // P1 stencil-kernel tasks: (i-chunk, row group, k-chunk), sorted by their number of points
+  if (degree == 1) {
+    const int64_t iw = 32 * kStencilV, jw = kStencilWarps;
+    int kch = 32;
+    std::vector<std::pair<int64_t, int4>> tasks;
+    for (;;) {
+      tasks.clear();
+      for (int64_t kc = 0; kc * kch <= N; ++kc)
+        for (int64_t ty = 0; ty * jw + kc * kch <= N; ++ty)
+          for (int64_t tx = 0; tx * iw + ty * jw + kc * kch <= N; ++tx) {
+            int64_t work = 0;
+            for (int64_t k = kc * kch; k < std::min<int64_t>(kc * kch + kch, N + 1); ++k)
+              for (int64_t j = ty * jw; j < ty * jw + jw; ++j) {
+                const int64_t len = N - j - k + 1 - tx * iw;   // points of the row from the chunk start
+                if (len > 0) work += std::min<int64_t>(len, iw);
+              }
+            tasks.push_back({work, int4{(int)tx, (int)ty, (int)kc, 0}});
+          }
+      if (kch <= 4 || (int64_t)tasks.size() * nmacro() >= 8 * 152) break;
+      kch /= 2;
+    }
+    std::vector<std::pair<int64_t, int4>> all;
+    for (int mac = 0; mac < nmacro(); ++mac)
+      for (auto& t : tasks) all.push_back({t.first, int4{t.second.x, t.second.y, t.second.z, mac}});
+    std::stable_sort(all.begin(), all.end(), [](const std::pair<int64_t, int4>& a, const std::pair<int64_t, int4>& b) {
+      return a.first > b.first;
+    });
+    std::vector<int4> tv(all.size());
+    for (size_t t = 0; t < all.size(); ++t) tv[t] = all[t].second;
+    I->stencil_kchunk = kch;
+    I->n_stencil_tasks = (int64_t)tv.size();
+    HHG_CUDA_TRY(cudaMalloc(&I->d_stencil_tasks, sizeof(int4) * tv.size()));
+    HHG_CUDA_TRY(cudaMemcpy(I->d_stencil_tasks, tv.data(), sizeof(int4) * tv.size(), cudaMemcpyHostToDevice));
   }
   I->h_ptr = ptr;
   I->h_idx = idx;

@@ -94,6 +94,8 @@ static void build_const(hhg_op* op) {
           Mm[a][b] = adet * s;
         }
       c.adet[o] = adet;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) c.Jinv[o][a * 3 + b] = Ji[a][b];
       c.M[o][0] = Mm[0][0];
       c.M[o][1] = Mm[1][1];
       c.M[o][2] = Mm[2][2];
@@ -145,6 +147,36 @@ static void build_const(hhg_op* op) {
       }
     }
     if (op->degree == 1) {
+      // stencils of a point inside each macro face: the incident micro-tets that lie in the
+      // macro are the same for every such point; found on a probe point of a level-3 macro
+      for (int a = 0; a < 4; ++a) {
+        const int M = 8;
+        const int probe[4][3] = {{3, 3, 2}, {0, 3, 3}, {3, 0, 3}, {3, 3, 0}};
+        const int* v = probe[a];
+        for (int o = 0; o < 6; ++o)
+          for (int la = 0; la < 4; ++la) {
+            int cc[3];
+            for (int t = 0; t < 3; ++t) cc[t] = v[t] - kClassOffsets[o][la][t];
+            bool ok = true;
+            for (int lb = 0; lb < 4 && ok; ++lb) {
+              int q[3], sum = 0;
+              for (int t = 0; t < 3; ++t) {
+                q[t] = cc[t] + kClassOffsets[o][lb][t];
+                sum += q[t];
+                if (q[t] < 0) ok = false;
+              }
+              if (sum > M) ok = false;
+            }
+            if (!ok) continue;
+            for (int lb = 0; lb < 4; ++lb) {
+              int d[3];
+              for (int t = 0; t < 3; ++t) d[t] = kClassOffsets[o][lb][t] - kClassOffsets[o][la][t];
+              for (int st = 0; st < 15; ++st)
+                if (d[0] == kStencil[st][0] && d[1] == kStencil[st][1] && d[2] == kStencil[st][2])
+                  c.Sface[a][st] += c.A[o][la][lb];
+            }
+          }
+      }
       // fold the six per-class matrices into the 15-point stencil of a point whose incident tets all exist
       for (int o = 0; o < 6; ++o)
         for (int a = 0; a < 4; ++a)
@@ -171,9 +203,13 @@ static OpConst<T> convert_const(const OpConst<double>& c) {
   for (int a = 0; a < 6; ++a)
     for (int b = 0; b < 10; ++b)
       for (int d = 0; d < 10; ++d) o.A[a][b][d] = (T)c.A[a][b][d];
-  for (int s = 0; s < 15; ++s) o.S[s] = (T)c.S[s];
+  for (int s = 0; s < 15; ++s) {
+    o.S[s] = (T)c.S[s];
+    for (int a = 0; a < 4; ++a) o.Sface[a][s] = (T)c.Sface[a][s];
+  }
   for (int a = 0; a < 6; ++a) {
     o.adet[a] = (T)c.adet[a];
+    for (int b = 0; b < 9; ++b) o.Jinv[a][b] = (T)c.Jinv[a][b];
     for (int b = 0; b < 6; ++b) o.M[a][b] = (T)c.M[a][b];
   }
   std::memcpy(o.x0, c.x0, sizeof(c.x0));
@@ -205,8 +241,37 @@ static OpConst<T> convert_const(const OpConst<double>& c) {
 __device__ __forceinline__ int tri(int s) { return ((s + 1) * (s + 2)) >> 1; }          // points of a plane
 __device__ __forceinline__ int row32(int s, int j) { return (j * (2 * s + 3 - j)) >> 1; }  // row start in plane
 
+// Point on a macro face that is not a Dirichlet point (Neumann, or an interface between
+// macros): sum the incident micro-tets that exist (Algorithm 1 per tet).
 template <typename T, bool DIRICHLET>
-__global__ void __launch_bounds__(256) p1_const_apply_kernel(const OpConst<T>* __restrict__ cst,
+__device__ __noinline__ T p1_face_point(const OpConst<T>& c, const int* __restrict__ pstart, const T* __restrict__ xm,
+                                        int i, int j, int k) {
+  const int N = c.N;
+  const uint32_t table = c.bnd_table;
+  T acc = T(0);
+  for (int o = 0; o < 6; ++o) {
+    const int lim = N - 1 - (o == 0 ? 0 : (o == 5 ? 2 : 1));
+    for (int a = 0; a < 4; ++a) {
+      const int ci = i - kClassOffsetsD[o][a][0], cj = j - kClassOffsetsD[o][a][1], ck = k - kClassOffsetsD[o][a][2];
+      if (ci < 0 || cj < 0 || ck < 0 || ci + cj + ck > lim) continue;
+      for (int b2 = 0; b2 < 4; ++b2) {
+        const int pi = ci + kClassOffsetsD[o][b2][0], pj = cj + kClassOffsetsD[o][b2][1],
+                  pkk = ck + kClassOffsetsD[o][b2][2];
+        if (DIRICHLET && on_dirichlet(table, N, pi, pj, pkk)) continue;
+        acc += c.A[o][a][b2] * __ldg(xm + __ldg(pstart + pkk) + row32(N - pkk, pj) + pi);
+      }
+    }
+  }
+  return acc;
+}
+
+// P1 constant-coefficient apply, one thread per output point (gather).  A CTA covers 256
+// consecutive points of one plane k; the plane of each CTA and the first packed position of each
+// plane come from per-level tables, so the index arithmetic is 32-bit and free of divisions.
+// Points off the macro faces use the 15-point stencil (Dirichlet columns dropped near Dirichlet
+// faces), points inside a face the face's stencil, points on macro edges/vertices the per-tet sum.
+template <typename T, bool DIRICHLET>
+__global__ void __launch_bounds__(256) p1_gather_kernel(const OpConst<T>* __restrict__ cst,
                                                               const int* __restrict__ cta_plane,
                                                               const int* __restrict__ cta_start,
                                                               const int* __restrict__ pstart,
@@ -271,26 +336,148 @@ __global__ void __launch_bounds__(256) p1_const_apply_kernel(const OpConst<T>* _
       ym[p] = xm[p];
       return;
     }
-    // point on a macro face that is not a Dirichlet point (Neumann, or an interface
-    // between macros): sum the incident micro-tets that exist (Algorithm 1 per tet)
-    const int n = N;   // P1: one lattice step per cube
-#pragma unroll 1
-    for (int o = 0; o < 6; ++o) {
-      const int lim = n - 1 - (o == 0 ? 0 : (o == 5 ? 2 : 1));
-#pragma unroll 1
-      for (int a = 0; a < 4; ++a) {
-        const int ci = i - kClassOffsetsD[o][a][0], cj = j - kClassOffsetsD[o][a][1], ck = k - kClassOffsetsD[o][a][2];
-        if (ci < 0 || cj < 0 || ck < 0 || ci + cj + ck > lim) continue;
-        for (int b2 = 0; b2 < 4; ++b2) {
-          const int pi = ci + kClassOffsetsD[o][b2][0], pj = cj + kClassOffsetsD[o][b2][1],
-                    pkk = ck + kClassOffsetsD[o][b2][2];
-          if (DIRICHLET && on_dirichlet(table, N, pi, pj, pkk)) continue;
-          acc += c.A[o][a][b2] * __ldg(xm + __ldg(pstart + pkk) + row32(N - pkk, pj) + pi);
-        }
+    const int z = zero_mask(N, i, j, k);
+    if (__popc(z) == 1) {
+      // inside one macro face: the face's own stencil; neighbours outside the macro drop out
+      const T* Sf = c.Sface[__ffs(z) - 1];
+#pragma unroll
+      for (int d = 0; d < 15; ++d) {
+        const int pi = i + kStencilD[d][0], pj = j + kStencilD[d][1], pkk = k + kStencilD[d][2];
+        if (!inside(N, pi, pj, pkk)) continue;
+        if (DIRICHLET && on_dirichlet(table, N, pi, pj, pkk)) continue;
+        acc += Sf[d] * __ldg(xm + __ldg(pstart + pkk) + row32(N - pkk, pj) + pi);
       }
+    } else {
+      // on a macro edge or vertex: sum the incident micro-tets that exist
+      acc = p1_face_point<T, DIRICHLET>(c, pstart, xm, i, j, k);
     }
   }
   ym[p] = acc;
+}
+
+
+// Window of row (jr, kr): x at i = i0 - 1 .. i0 + V, zero outside the row and (DIRICHLET) at
+// Dirichlet points.
+template <typename T, int V, bool DIRICHLET>
+__device__ __forceinline__ void p1_window(const T* __restrict__ xm, const int* __restrict__ pstart, int N,
+                                          uint32_t table, int i0, int jr, int kr, T w[V + 2]) {
+  const int len = N - jr - kr + 1;   // points of the row (none if <= 0)
+  if (jr < 0 || kr < 0 || kr > N || len <= 0) {
+#pragma unroll
+    for (int t = 0; t < V + 2; ++t) w[t] = T(0);
+    return;
+  }
+  const T* __restrict__ row = xm + __ldg(pstart + kr) + row32(N - kr, jr);
+  const bool rowface = (jr == 0) | (kr == 0);
+  if (!rowface && i0 >= 2 && i0 + V < len - 1) {
+    // the window lies inside the row, away from its end points: no bounds, no Dirichlet points
+#pragma unroll
+    for (int t = 0; t < V + 2; ++t) w[t] = __ldg(row + i0 - 1 + t);
+    return;
+  }
+#pragma unroll
+  for (int t = 0; t < V + 2; ++t) {
+    const int ii = i0 - 1 + t;
+    T v = (ii >= 0 && ii < len) ? __ldg(row + ii) : T(0);
+    if (DIRICHLET && (rowface || ii == 0 || ii == len - 1) && ii >= 0 && ii < len &&
+        on_dirichlet(table, N, ii, jr, kr))
+      v = T(0);
+    w[t] = v;
+  }
+}
+
+// P1 constant-coefficient apply.  A CTA of 8 warps owns 8 rows j (one per warp) of an i-chunk of
+// 32*V points (V consecutive points per lane) and climbs the planes k of a k-chunk.  Each lane
+// keeps the seven row windows of the 15-point stencil -- rows (j,k), (j+-1,k), (j,k+1),
+// (j-1,k+1), (j,k-1), (j+1,k-1) -- in registers and rotates them when k advances, so a step
+// loads three new windows.  All 24 micro-tets around a point off the macro faces exist, so its
+// row of A is the 15-point stencil folded from the six hoisted class matrices; Dirichlet
+// columns were zeroed when the windows were loaded.
+template <typename T, int V, bool DIRICHLET>
+__global__ void __launch_bounds__(256) p1_stencil_kernel(const OpConst<T>* __restrict__ cst,
+                                                          const int4* __restrict__ tasks, int kch,
+                                                          const int* __restrict__ pstart, const T* __restrict__ x,
+                                                          T* __restrict__ y) {
+  const int4 task = tasks[blockIdx.x];
+  const OpConst<T>& c = cst[task.w];
+  const int N = c.N;
+  const uint32_t table = c.bnd_table;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = task.x * 32 * V + V * lane;
+  const int j = task.y * kStencilWarps + warp;
+  const int k0 = task.z * kch;
+  // last plane with a point of this warp's row segment
+  const int k_end = min(k0 + kch - 1, N - j - task.x * 32 * V);
+  if (k_end < k0) return;
+  const T* __restrict__ xm = x + c.base;
+  T* __restrict__ ym = y + c.base;
+  T S[15];
+#pragma unroll
+  for (int d = 0; d < 15; ++d) S[d] = c.S[d];
+  T w00[V + 2], wp0[V + 2], wm0[V + 2], w01[V + 2], wm1[V + 2], w0m[V + 2], wpm[V + 2];
+  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j, k0, w00);
+  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j + 1, k0, wp0);
+  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j - 1, k0, wm0);
+  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j, k0 + 1, w01);
+  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j - 1, k0 + 1, wm1);
+  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j, k0 - 1, w0m);
+  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j + 1, k0 - 1, wpm);
+  for (int k = k0; k <= k_end; ++k) {
+    const int len = N - j - k + 1;
+    if (i0 < len) {
+      const int rowbase = __ldg(pstart + k) + row32(N - k, j);
+      if (j >= 1 && k >= 1 && i0 >= 1 && i0 + V <= len - 2) {
+        // all V points lie off the macro faces: the interior stencil
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          ym[rowbase + i0 + v] = S[0] * w00[v + 1] + S[1] * w00[v + 2] + S[2] * w00[v] + S[3] * wp0[v + 1] +
+                                 S[4] * wm0[v + 1] + S[5] * w01[v + 1] + S[6] * w0m[v + 1] + S[7] * wm0[v + 2] +
+                                 S[8] * wp0[v] + S[9] * w0m[v + 2] + S[10] * w01[v] + S[11] * wpm[v + 1] +
+                                 S[12] * wm1[v + 1] + S[13] * wm1[v + 2] + S[14] * wpm[v];
+      } else
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int ii = i0 + v;
+        if (ii >= len) break;
+        T acc;
+        const int z = (ii == len - 1) | ((ii == 0) << 1) | ((j == 0) << 2) | ((k == 0) << 3);
+        if (DIRICHLET && z && ((table >> z) & 1u)) {
+          acc = __ldg(xm + rowbase + ii);
+        } else if (__popc(z) <= 1) {
+          // inside the macro, or inside one macro face (its own stencil: the missing micro-tets
+          // drop out; the neighbours outside the macro read as zero)
+          T W[15];
+          if (z == 0) {
+#pragma unroll
+            for (int d = 0; d < 15; ++d) W[d] = S[d];
+          } else {
+            const T* Sf = c.Sface[__ffs(z) - 1];
+#pragma unroll
+            for (int d = 0; d < 15; ++d) W[d] = Sf[d];
+          }
+          acc = W[0] * w00[v + 1] + W[1] * w00[v + 2] + W[2] * w00[v] + W[3] * wp0[v + 1] + W[4] * wm0[v + 1] +
+                W[5] * w01[v + 1] + W[6] * w0m[v + 1] + W[7] * wm0[v + 2] + W[8] * wp0[v] + W[9] * w0m[v + 2] +
+                W[10] * w01[v] + W[11] * wpm[v + 1] + W[12] * wm1[v + 1] + W[13] * wm1[v + 2] + W[14] * wpm[v];
+        } else {
+          // on a macro edge or vertex
+          acc = p1_face_point<T, DIRICHLET>(c, pstart, xm, ii, j, k);
+        }
+        ym[rowbase + ii] = acc;
+      }
+    }
+    if (k == k_end) break;
+    // rotate: plane k becomes k-1, plane k+1 becomes k; load the three new windows
+#pragma unroll
+    for (int t = 0; t < V + 2; ++t) {
+      w0m[t] = w00[t];
+      wpm[t] = wp0[t];
+      w00[t] = w01[t];
+      wm0[t] = wm1[t];
+    }
+    p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j + 1, k + 1, wp0);
+    p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j, k + 2, w01);
+    p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j - 1, k + 2, wm1);
+  }
 }
 
 // diag(A) for the constant-coefficient operators: sum of A_T[a][a] over the incident micro-tets.
@@ -462,13 +649,25 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
   if (op->kind == HHG_DIFFUSION && op->degree == 1 && op->coeff.type == HHG_COEFF_CONST) {
     (void)V;
     const Interface* I = op->itf;
-    dim3 grid((unsigned)I->ncta, nm);
+    if (sizeof(T) == 8) {
+      // FP64: the FP64 pipe bounds the apply; one point per thread keeps the most warps in flight
+      dim3 grid((unsigned)I->ncta, nm);
+      if (op->bc == HHG_DIRICHLET)
+        p1_gather_kernel<T, true><<<grid, 256, 0, s>>>(dconst<T>(op), I->d_cta_plane, I->d_cta_start, I->d_pstart,
+                                                        x, y);
+      else
+        p1_gather_kernel<T, false><<<grid, 256, 0, s>>>(dconst<T>(op), I->d_cta_plane, I->d_cta_start,
+                                                         I->d_pstart, x, y);
+      HHG_CUDA_TRY(cudaGetLastError());
+      return HHG_OK;
+    }
+    const unsigned grid = (unsigned)I->n_stencil_tasks;
     if (op->bc == HHG_DIRICHLET)
-      p1_const_apply_kernel<T, true><<<grid, 256, 0, s>>>(dconst<T>(op), I->d_cta_plane, I->d_cta_start,
-                                                          I->d_pstart, x, y);
+      p1_stencil_kernel<T, kStencilV, true><<<grid, 256, 0, s>>>(dconst<T>(op), I->d_stencil_tasks, I->stencil_kchunk,
+                                                                  I->d_pstart, x, y);
     else
-      p1_const_apply_kernel<T, false><<<grid, 256, 0, s>>>(dconst<T>(op), I->d_cta_plane, I->d_cta_start,
-                                                           I->d_pstart, x, y);
+      p1_stencil_kernel<T, kStencilV, false><<<grid, 256, 0, s>>>(dconst<T>(op), I->d_stencil_tasks,
+                                                                   I->stencil_kchunk, I->d_pstart, x, y);
     HHG_CUDA_TRY(cudaGetLastError());
     return HHG_OK;
   }
@@ -529,6 +728,8 @@ extern "C" int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, 
     return fail(HHG_E_ARG, "op_create: unknown coefficient type %d", coeff->type);
   if ((coeff->type == HHG_COEFF_FIELD_P1 && degree != 1) || (coeff->type == HHG_COEFF_FIELD_P2 && degree != 2))
     return fail(HHG_E_UNSUPPORTED, "op_create: the coefficient field must have the operator's degree");
+  if (kind == HHG_EPSILON && coeff->type != HHG_COEFF_CONST && coeff->type != HHG_COEFF_FIELD_P2)
+    return fail(HHG_E_UNSUPPORTED, "op_create: EPSILON takes a CONST or FIELD_P2 viscosity");
   if ((coeff->type == HHG_COEFF_SIN3 || coeff->type == HHG_COEFF_FIELD_P2) && quad_degree > 5)
     return fail(HHG_E_UNSUPPORTED, "op_create: quadrature degree above 5");
   std::unique_ptr<hhg_op> op(new hhg_op());
@@ -586,6 +787,19 @@ extern "C" int hhg_op_apply(hhg_op_t* op, const void* x, void* y, int dtype, int
   cudaStream_t s = (cudaStream_t)stream;
   const Interface* itf = nullptr;
   HHG_TRY(op->mesh->interface(op->level, op->degree, &itf));
+  if (op->kind == HHG_EPSILON) {
+    const int pp = 3 * nrhs;
+    if (dtype == HHG_F64) {
+      HHG_TRY(launch_eps<double>(op, dconst<double>(op), 0, nrhs, (const double*)x, nullptr, field_ptr<double>(op),
+                                 (double*)y, s));
+      HHG_TRY(launch_interface_sum<double>(itf, (double*)y, pp, op->bc == HHG_DIRICHLET, s));
+    } else {
+      HHG_TRY(launch_eps<float>(op, dconst<float>(op), 0, nrhs, (const float*)x, nullptr, field_ptr<float>(op),
+                                (float*)y, s));
+      HHG_TRY(launch_interface_sum<float>(itf, (float*)y, pp, op->bc == HHG_DIRICHLET, s));
+    }
+    return HHG_OK;
+  }
   if (dtype == HHG_F64) {
     HHG_TRY(launch_apply<double>(op, (const double*)x, (double*)y, s));
     HHG_TRY(launch_interface_sum<double>(itf, (double*)y, 1, op->bc == HHG_DIRICHLET, s));
@@ -612,6 +826,40 @@ extern "C" int hhg_op_diagonal(hhg_op_t* op, void* d, int dtype, void* stream) {
     HHG_TRY(launch_diag<float>(op, (float*)d, s));
     HHG_TRY(launch_interface_sum<float>(itf, (float*)d, 1, op->bc == HHG_DIRICHLET, s));
   }
+  return HHG_OK;
+}
+
+namespace hhg {
+// Physical position of every packed point: P0 + (i e0 + j e1 + k e2) / N.
+__global__ void coordinates_kernel(const MacroGeom* __restrict__ mg, int N, const int* __restrict__ cta_plane,
+                                   const int* __restrict__ cta_start, const int* __restrict__ pstart,
+                                   double* __restrict__ xyz) {
+  const int k = __ldg(cta_plane + blockIdx.x);
+  const int s = N - k;
+  const int q = (blockIdx.x - __ldg(cta_start + k)) * 256 + threadIdx.x;
+  if (q >= tri(s)) return;
+  const float b = 2.0f * s + 3.0f;
+  int j = (int)(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)q, 0.0f))));
+  j = max(0, min(j, s));
+  if (j < s && row32(s, j + 1) <= q) ++j;
+  if (j > 0 && row32(s, j) > q) --j;
+  const int i = q - row32(s, j);
+  const MacroGeom& g = mg[blockIdx.y];
+  const int64_t e = (int64_t)blockIdx.y * dV(N) + __ldg(pstart + k) + q;
+  for (int d = 0; d < 3; ++d)
+    xyz[3 * e + d] = g.p0[d] + ((double)i * g.e[0][d] + (double)j * g.e[1][d] + (double)k * g.e[2][d]) / N;
+}
+}  // namespace hhg
+
+extern "C" int hhg_vec_coordinates(const hhg_mesh_t* mesh, int level, int degree, double* xyz, void* stream) {
+  clear_error();
+  if (!mesh || !xyz) return fail(HHG_E_ARG, "vec_coordinates: null pointer");
+  const Interface* itf = nullptr;
+  HHG_TRY(const_cast<hhg_mesh_t*>(mesh)->interface(level, degree, &itf));
+  dim3 grid((unsigned)itf->ncta, mesh->nmacro());
+  coordinates_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(mesh->d_macros, degree << level, itf->d_cta_plane,
+                                                             itf->d_cta_start, itf->d_pstart, xyz);
+  HHG_CUDA_TRY(cudaGetLastError());
   return HHG_OK;
 }
 
@@ -654,12 +902,24 @@ extern "C" int hhg_op_apply_adjoint_coeff(hhg_op_t* op, const void* u, const voi
   HHG_TRY(check_dtype(dtype));
   if (op->coeff.type != HHG_COEFF_FIELD_P1 && op->coeff.type != HHG_COEFF_FIELD_P2)
     return fail(HHG_E_UNSUPPORTED, "op_apply_adjoint_coeff: the coefficient is not a field");
-  if (op->kind != HHG_DIFFUSION) return fail(HHG_E_UNSUPPORTED, "op_apply_adjoint_coeff: diffusion operators only");
-  if (nrhs != 1) return fail(HHG_E_ARG, "op_apply_adjoint_coeff: nrhs must be 1 for scalar operators");
+  if (nrhs < 1 || (nrhs != 1 && op->kind != HHG_EPSILON))
+    return fail(HHG_E_ARG, "op_apply_adjoint_coeff: nrhs must be 1 for scalar operators");
   HHG_TRY(check_field(op, dtype));
   cudaStream_t s = (cudaStream_t)stream;
   const Interface* itf = nullptr;
   HHG_TRY(op->mesh->interface(op->level, op->degree, &itf));
+  if (op->kind == HHG_EPSILON) {
+    if (dtype == HHG_F64) {
+      HHG_TRY(launch_eps<double>(op, dconst<double>(op), 2, nrhs, (const double*)u, (const double*)g,
+                                 field_ptr<double>(op), (double*)dk, s));
+      HHG_TRY(launch_interface_sum<double>(itf, (double*)dk, 1, false, s));
+    } else {
+      HHG_TRY(launch_eps<float>(op, dconst<float>(op), 2, nrhs, (const float*)u, (const float*)g,
+                                field_ptr<float>(op), (float*)dk, s));
+      HHG_TRY(launch_interface_sum<float>(itf, (float*)dk, 1, false, s));
+    }
+    return HHG_OK;
+  }
   if (dtype == HHG_F64) {
     HHG_TRY(launch_march<double>(op, dconst<double>(op), 2, (const double*)u, (const double*)g,
                                  field_ptr<double>(op), (double*)dk, s));

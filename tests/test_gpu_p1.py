@@ -104,3 +104,12 @@ def test_p1_const_level8_sampled():
     sample = np.concatenate([sample, rng.choice(near, 100, replace=False)])
     ref = OA.sampled_diffusion_rows(v[t[0]], level, 1, ("const", 1.0), 2, "dirichlet", xp, pts[sample])
     assert np.abs(y[sample] - ref).max() <= 1e-12 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("meshname,level,degree", [("cube48", 1, 2), ("reference_tet", 3, 1), ("cuboid36", 1, 1)])
+def test_coordinates(meshname, level, degree):
+    from gpu_helpers import Case
+    c = Case(meshname, level, degree)
+    xyz = c.mesh.coordinates(degree).cpu().numpy()
+    ref = np.concatenate([OM.physical(c.v[c.t[m]], c.S.pts, c.S.N) for m in range(len(c.t))])
+    assert np.abs(xyz - ref).max() <= 1e-15
