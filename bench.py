@@ -157,6 +157,106 @@ def cpu_baseline(seconds_budget: float = 20.0):
             "legs": res}
 
 
+def run_fmg(hhg, torch, level: int, reps: int = 1):
+    """FMG + V(2,2) Chebyshev solves of the manufactured Poisson problem, P2, unit cube as 6 macros.
+
+    All-FP64 against FP32 cycles inside FP64 iterative refinement, to a relative residual of 1e-10.
+    Times are CUDA-event device times of the solve (FMG + iterations); the hierarchy set-up of the
+    first call is reported separately.  The discretisation error is also taken one level coarser.
+    """
+    import workloads as W
+    v, t = W.cube6()
+    out = {"workload": "unit cube as 6 macros, level %d, P2 Poisson, f = 3 pi^2 sin sin sin, FMG + V(2,2), "
+                       "Chebyshev order 2, tol 1e-10" % level}
+    errs = {}
+    for lvl in (level - 1, level):
+        mesh = hhg.Mesh(v, t, lvl)
+        op = hhg.Operator(mesh, degree=2, coeff=("const", 1.0), bc="dirichlet", quad_degree=4)
+        b = mesh.rhs_sin3_poisson(2)
+        tot, inner = mesh.dof_count(2)
+        for name, mixed in (("fp64", 0), ("mixed", 1)):
+            x, st0 = op.mg_solve(b, torch.zeros_like(b), mixed=mixed)
+            ms = []
+            for _ in range(reps if lvl == level else 0):
+                x, st = op.mg_solve(b, torch.zeros_like(b), mixed=mixed)
+                ms.append(st["solve_ms"])
+            e = mesh.l2_error_sin3(x, 2)
+            errs[(name, lvl)] = e
+            if lvl == level:
+                out[name] = {"solve_ms": min(ms), "setup_ms": st0["setup_ms"], "iterations": st["iterations"],
+                             "rel_residual": st["rel_residual"], "l2_error": e, "dofs": inner,
+                             "mdofs_per_s": inner / (min(ms) * 1e-3) / 1e6}
+        del op, mesh
+    for name in ("fp64", "mixed"):
+        out[name]["l2_error_ratio_vs_level_%d" % (level - 1)] = errs[(name, level - 1)] / errs[(name, level)]
+    out["mixed_speedup"] = out["fp64"]["solve_ms"] / out["mixed"]["solve_ms"]
+    return out
+
+
+def time_apply(torch, fn, flush, reps: int, warmup: int = 1):
+    """Mean CUDA-event time (ms) of fn() on the current stream, L2 flushed before every call."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    ms = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.mean(ms)
+
+
+def run_const_legs(hhg, torch, flush, peak_gbs: float, reps: int = 5):
+    """Constant-coefficient applies on working sets larger than L2: P1 at level 9, P2 at level 8."""
+    import workloads as W
+    v, t = W.reference_tet()
+    out = {}
+    for name, level, degree in (("p1_const", 9, 1), ("p2_const", 8, 2)):
+        mesh = hhg.Mesh(v, t, level)
+        op = hhg.Operator(mesh, degree=degree, coeff=("const", 1.0), bc="dirichlet")
+        tot, inner = mesh.dof_count(degree)
+        for dt, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+            x = torch.from_numpy(W.uniform(mesh.vec_size(degree), seed=0)).to("cuda", tdt)
+            y = torch.empty_like(x)
+            ms = time_apply(torch, lambda: op.apply(x, out=y), flush, reps)
+            nbytes = 2 * x.numel() * x.element_size()
+            out["%s_%s" % (name, dt)] = {"level": level, "ms": ms, "mdofs": inner / ms / 1e3,
+                                         "gbs": nbytes / ms / 1e6, "hbm_frac": nbytes / ms / 1e6 / peak_gbs}
+            del x, y
+        del op, mesh
+    return out
+
+
+def run_eps(hhg, torch, flush, level: int = 6, nrhs: int = 16, reps: int = 1):
+    """P2 vector epsilon operator on the unit cube as 48 macros, mu = 10^(3(z-0.5)) as a P2 field,
+    nrhs seeded right-hand sides in one launch (FP64), and its adjoint in mu."""
+    import workloads as W
+    v, t = W.cube48()
+    mesh = hhg.Mesh(v, t, level)
+    n = mesh.vec_size(2)
+    # mu = 10^(3(z - 0.5)) at the packed points of every macro (a P2 field)
+    xyz = mesh.coordinates(2)
+    mu_t = torch.pow(10.0, 3.0 * (xyz[:, 2] - 0.5)).contiguous()
+    op = hhg.Operator(mesh, kind="epsilon", degree=2, coeff=("field_p2", mu_t), bc="dirichlet", quad_degree=4)
+    x = torch.empty(n * 3 * nrhs, dtype=torch.float64, device="cuda")
+    for r in range(nrhs):
+        x.view(n, 3, nrhs)[:, :, r] = torch.from_numpy(W.uniform(3 * n, seed=r)).to("cuda").view(n, 3)
+    mesh.make_consistent(x, 2, per_point=3 * nrhs)
+    y = torch.empty_like(x)
+    tot, inner = mesh.dof_count(2)
+    ms = time_apply(torch, lambda: op.apply(x, out=y, nrhs=nrhs), flush, reps)
+    ms_adj = time_apply(torch, lambda: op.adjoint_coeff(x, y, nrhs=nrhs), flush, reps)
+    ntet = len(t) * 8 ** level
+    return {"workload": "unit cube as 48 macros, level %d, P2 vector epsilon, mu = 10^(3(z-0.5)) P2 field, "
+                        "%d right-hand sides, FP64, Dirichlet" % (level, nrhs),
+            "apply_ms": ms, "adjoint_ms": ms_adj, "mdofs": 3 * inner * nrhs / ms / 1e3,
+            "adjoint_mdofs": 3 * inner * nrhs / ms_adj / 1e3, "micro_tets": ntet}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -186,6 +286,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hhg", choices=["hhg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fmg-level", type=int, default=7)
+    ap.add_argument("--no-fmg", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the constant-coefficient and epsilon legs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -324,6 +427,20 @@ def main():
     roof["traffic"] = tr["bytes_per_launch"] if tr else None
     roof["kernel"] = dom
 
+    extra = {}
+    for L in legs:
+        L["x"] = L["y"] = L["hx"] = L["hy"] = None
+    torch.cuda.empty_cache()
+    if not args.no_extra:
+        extra["const_legs"] = run_const_legs(hhg, torch, flush, peaks["hbm_gbs"])
+        torch.cuda.empty_cache()
+        extra["epsilon"] = run_eps(hhg, torch, flush)
+        torch.cuda.empty_cache()
+    fmg = None
+    if not args.no_fmg:
+        del flush
+        torch.cuda.empty_cache()
+        fmg = run_fmg(hhg, torch, args.fmg_level)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
@@ -337,6 +454,9 @@ def main():
             "legs": details, "legs_not_built": skipped, "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "MDoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "wall_s_timed": wall}
+    line.update(extra)
+    if fmg is not None:
+        line["fmg"] = fmg
     if cb is not None:
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         line["cpu_baseline"]["legs"] = cb["legs"]

@@ -141,6 +141,7 @@ struct alignas(16) OpConst {
   T psi[kMaxQ][10];
   T cs[6][kMaxQ][3][2];
   T qoff[6][kMaxQ][3];   // physical offset delta of point q of class o from the cube origin
+  T rot[3][2];           // cos / sin of 2 pi H[2][d]: rotation of (sin, cos)(2 pi x_d) per k step
   T X0[3];               // x0 and H in the compute type
   T H[3][3];             // H[a][d]: component d of the step along index axis a
 };

@@ -141,8 +141,28 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
   T carry[P * P];
 #pragma unroll
   for (int t = 0; t < P * P; ++t) carry[t] = T(0);
+  // analytic coefficient in FP64: sin / cos of 2 pi x at the cube origin, evaluated once per
+  // chunk and then rotated by the fixed angle 2 pi h_k of one k step (angle addition)
+  constexpr bool kRotate = (COEF == HHG_COEFF_SIN3) && (sizeof(T) == 8);
+  T so[3], co[3];
+  if (kRotate) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T xd = c.X0[d] + T(ci) * c.H[0][d] + T(cj) * c.H[1][d] + T(K0 - 1) * c.H[2][d];
+      sincos2pi<T>(xd, &so[d], &co[d]);
+    }
+  }
 
   for (int ck = K0 - 1; ck <= ck_last; ++ck) {
+    if (kRotate && ck > K0 - 1) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T sn = so[d] * c.rot[d][0] + co[d] * c.rot[d][1];
+        const T cn = co[d] * c.rot[d][0] - so[d] * c.rot[d][1];
+        so[d] = sn;
+        co[d] = cn;
+      }
+    }
     T acc[P3];
 #pragma unroll
     for (int t = 0; t < P3; ++t) acc[t] = T(0);
@@ -167,9 +187,8 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
             if (MODE == MODE_ADJ) gb[s] = live ? __ldg(g + base + idx) : T(0);
             if (COEF == HHG_COEFF_FIELD_P1 || COEF == HHG_COEFF_FIELD_P2) kb[s] = in ? __ldg(kf + c.kbase + idx) : T(0);
           }
-      // analytic coefficient: sin / cos of 2 pi x at the cube origin, per coordinate
-      T so[3], co[3];
-      if (COEF == HHG_COEFF_SIN3) {
+      // analytic coefficient in FP32: sin / cos of 2 pi x at the cube origin, per coordinate
+      if (COEF == HHG_COEFF_SIN3 && !kRotate) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           const T xd = c.X0[d] + T(ci) * c.H[0][d] + T(cj) * c.H[1][d] + T(ck) * c.H[2][d];

@@ -118,7 +118,11 @@ static void build_const(hhg_op* op) {
     // quadrature tables for variable coefficients (the op's rule)
     const QuadRule& rq = op->rule;
     c.nq = rq.nq();
-    for (int d = 0; d < 3; ++d) c.X0[d] = c.x0[d];
+    for (int d = 0; d < 3; ++d) {
+      c.X0[d] = c.x0[d];
+      c.rot[d][0] = std::cos(2.0 * M_PI * c.h[2][d]);
+      c.rot[d][1] = std::sin(2.0 * M_PI * c.h[2][d]);
+    }
     for (int a = 0; a < 3; ++a)
       for (int d = 0; d < 3; ++d) c.H[a][d] = c.h[a][d];
     for (int q = 0; q < rq.nq() && q < kMaxQ; ++q) {
@@ -226,6 +230,8 @@ static OpConst<T> convert_const(const OpConst<double>& c) {
       }
   }
   for (int d = 0; d < 3; ++d) {
+    o.rot[d][0] = (T)c.rot[d][0];
+    o.rot[d][1] = (T)c.rot[d][1];
     o.X0[d] = (T)c.X0[d];
     for (int a = 0; a < 3; ++a) o.H[a][d] = (T)c.H[a][d];
   }
@@ -480,6 +486,154 @@ __global__ void __launch_bounds__(256) p1_stencil_kernel(const OpConst<T>* __res
   }
 }
 
+// P1 constant-coefficient apply with shared-memory plane tiles.  A CTA owns rows j0..j0+7 and
+// points i0..i0+127 of a k-chunk (task list of the stencil kernel).  For every plane it stages
+// the tile plus a one-point halo (10 rows x 130 points) into a three-plane rolling buffer --
+// one coalesced global load per staged value, Dirichlet points staged as zero -- and each thread
+// then evaluates the 15-point stencil of four points (i = i0 + lane + 32 v) from shared memory.
+constexpr int kTileI = 32 * kStencilV;           // 128 points along i
+constexpr int kTileJ = kStencilWarps;            // 8 rows
+constexpr int kTileW = kTileI + 4;               // staged width (130 used, padded)
+constexpr int kTileH = kTileJ + 2;               // staged rows
+
+constexpr int kTileDepth = 4;                      // planes staged ahead of the one being computed
+constexpr int kTileRing = kTileDepth + 2;          // planes k-1 .. k+kTileDepth
+
+__device__ __forceinline__ void cp_async_zfill(void* smem, const void* gmem, int bytes, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int src = valid ? bytes : 0;   // src-size 0: the destination is zero-filled, nothing is read
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(src));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int NPENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(NPENDING));
+}
+
+// Issue the asynchronous staging of plane kk (tile rows j0-1 .. j0+8, points i0-1 .. i0+128);
+// positions outside the macro are zero-filled.
+template <typename T>
+__device__ __forceinline__ void p1_issue_plane(T (*slot)[kTileW], const T* __restrict__ xm,
+                                               const int* __restrict__ pstart, int N, int i0, int j0, int kk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < kTileH; r += kTileJ) {
+    const int jr = j0 - 1 + r;
+    const int len = N - jr - kk + 1;
+    const bool rowok = jr >= 0 && kk >= 0 && kk <= N && len > 0;
+    const T* __restrict__ row = rowok ? xm + __ldg(pstart + kk) + row32(N - kk, jr) : xm;
+    for (int cidx = lane; cidx < kTileI + 2; cidx += 32) {
+      const int ii = i0 - 1 + cidx;
+      const bool ok = rowok && ii >= 0 && ii < len;
+      cp_async_zfill(&slot[r][cidx], ok ? row + ii : xm, (int)sizeof(T), ok);
+    }
+  }
+}
+
+// After plane kk has arrived: zero the Dirichlet points this thread staged.
+template <typename T>
+__device__ __forceinline__ void p1_mask_plane(T (*slot)[kTileW], int N, uint32_t table, int i0, int j0, int kk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < kTileH; r += kTileJ) {
+    const int jr = j0 - 1 + r;
+    const int len = N - jr - kk + 1;
+    if (!(jr >= 0 && kk >= 0 && kk <= N && len > 0)) continue;
+    const bool rowface = (jr == 0) | (kk == 0);
+    for (int cidx = lane; cidx < kTileI + 2; cidx += 32) {
+      const int ii = i0 - 1 + cidx;
+      if (ii < 0 || ii >= len) continue;
+      if ((rowface || ii == 0 || ii == len - 1) && on_dirichlet(table, N, ii, jr, kk)) slot[r][cidx] = T(0);
+    }
+  }
+}
+
+template <typename T, bool DIRICHLET>
+__global__ void __launch_bounds__(256) p1_tile_kernel(const OpConst<T>* __restrict__ cst,
+                                                       const int4* __restrict__ tasks, int kch,
+                                                       const int* __restrict__ pstart, const T* __restrict__ x,
+                                                       T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char tile_smem[];
+  T (*buf)[kTileH][kTileW] = reinterpret_cast<T (*)[kTileH][kTileW]>(tile_smem);
+  const int4 task = tasks[blockIdx.x];
+  const OpConst<T>& c = cst[task.w];
+  const int N = c.N;
+  const uint32_t table = c.bnd_table;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = task.x * kTileI, j0 = task.y * kTileJ, k0 = task.z * kch;
+  const int k_end = min(k0 + kch - 1, N - j0 - i0);   // last plane holding a point of the tile
+  if (k_end < k0) return;
+  const T* __restrict__ xm = x + c.base;
+  T* __restrict__ ym = y + c.base;
+  T S[15];
+#pragma unroll
+  for (int d = 0; d < 15; ++d) S[d] = c.S[d];
+  const int j = j0 + warp;
+  auto slot = [&](int kk) { return buf[(kk - k0 + 1) % kTileRing]; };   // kk >= k0 - 1
+  // prologue: planes k0-1 .. k0+kTileDepth-1, one commit group each
+  for (int kk = k0 - 1; kk < k0 + kTileDepth; ++kk) {
+    if (kk <= k_end + 1) p1_issue_plane<T>(slot(kk), xm, pstart, N, i0, j0, kk);
+    cp_async_commit();
+  }
+  // planes k0-1 and k0 must be complete before the loop (the loop waits for k+1 only)
+  cp_async_wait<kTileDepth - 1>();
+  if (DIRICHLET) {
+    p1_mask_plane<T>(slot(k0 - 1), N, table, i0, j0, k0 - 1);
+    p1_mask_plane<T>(slot(k0), N, table, i0, j0, k0);
+  }
+  for (int k = k0; k <= k_end; ++k) {
+    // plane k+1 has arrived once at most kTileDepth-1 later groups are pending
+    cp_async_wait<kTileDepth - 2>();
+    if (DIRICHLET) p1_mask_plane<T>(slot(k + 1), N, table, i0, j0, k + 1);
+    __syncthreads();
+    const T (*pm)[kTileW] = slot(k - 1);
+    const T (*p0)[kTileW] = slot(k);
+    const T (*pp)[kTileW] = slot(k + 1);
+    const int len = N - j - k + 1;
+    const int r = warp + 1;                     // staged row of j
+    if (len > 0) {
+      const int rowbase = __ldg(pstart + k) + row32(N - k, j);
+#pragma unroll
+      for (int v = 0; v < kStencilV; ++v) {
+        const int cc = lane + 32 * v + 1;       // staged column of i
+        const int ii = i0 + cc - 1;
+        if (ii >= len) continue;
+        const int z = (ii == len - 1) | ((ii == 0) << 1) | ((j == 0) << 2) | ((k == 0) << 3);
+        T acc;
+        if (z == 0) {
+          acc = S[0] * p0[r][cc] + S[1] * p0[r][cc + 1] + S[2] * p0[r][cc - 1] + S[3] * p0[r + 1][cc] +
+                S[4] * p0[r - 1][cc] + S[5] * pp[r][cc] + S[6] * pm[r][cc] + S[7] * p0[r - 1][cc + 1] +
+                S[8] * p0[r + 1][cc - 1] + S[9] * pm[r][cc + 1] + S[10] * pp[r][cc - 1] + S[11] * pm[r + 1][cc] +
+                S[12] * pp[r - 1][cc] + S[13] * pp[r - 1][cc + 1] + S[14] * pm[r + 1][cc - 1];
+        } else if (DIRICHLET && ((table >> z) & 1u)) {
+          acc = __ldg(xm + rowbase + ii);
+        } else if (__popc(z) == 1) {
+          const T* Sf = c.Sface[__ffs(z) - 1];
+          acc = Sf[0] * p0[r][cc] + Sf[1] * p0[r][cc + 1] + Sf[2] * p0[r][cc - 1] + Sf[3] * p0[r + 1][cc] +
+                Sf[4] * p0[r - 1][cc] + Sf[5] * pp[r][cc] + Sf[6] * pm[r][cc] + Sf[7] * p0[r - 1][cc + 1] +
+                Sf[8] * p0[r + 1][cc - 1] + Sf[9] * pm[r][cc + 1] + Sf[10] * pp[r][cc - 1] +
+                Sf[11] * pm[r + 1][cc] + Sf[12] * pp[r - 1][cc] + Sf[13] * pp[r - 1][cc + 1] +
+                Sf[14] * pm[r + 1][cc - 1];
+        } else {
+          acc = p1_face_point<T, DIRICHLET>(c, pstart, xm, ii, j, k);
+        }
+        ym[rowbase + ii] = acc;
+      }
+    }
+    __syncthreads();   // every thread is done with plane k-1: its slot takes plane k+kTileDepth
+    const int kn = k + kTileDepth;
+    if (kn <= k_end + 1) p1_issue_plane<T>(slot(kn), xm, pstart, N, i0, j0, kn);
+    cp_async_commit();
+  }
+  cp_async_wait<0>();
+}
+
+template <typename T>
+constexpr size_t p1_tile_smem() {
+  return sizeof(T) * kTileRing * kTileH * kTileW;
+}
+
 // diag(A) for the constant-coefficient operators: sum of A_T[a][a] over the incident micro-tets.
 template <typename T>
 __global__ void const_diag_kernel(const OpConst<T>* __restrict__ cst, int degree, bool dirichlet, T* __restrict__ d) {
@@ -662,12 +816,13 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
       return HHG_OK;
     }
     const unsigned grid = (unsigned)I->n_stencil_tasks;
+    const size_t smem = p1_tile_smem<T>();
     if (op->bc == HHG_DIRICHLET)
-      p1_stencil_kernel<T, kStencilV, true><<<grid, 256, 0, s>>>(dconst<T>(op), I->d_stencil_tasks, I->stencil_kchunk,
-                                                                  I->d_pstart, x, y);
+      p1_tile_kernel<T, true><<<grid, 256, smem, s>>>(dconst<T>(op), I->d_stencil_tasks, I->stencil_kchunk,
+                                                      I->d_pstart, x, y);
     else
-      p1_stencil_kernel<T, kStencilV, false><<<grid, 256, 0, s>>>(dconst<T>(op), I->d_stencil_tasks,
-                                                                   I->stencil_kchunk, I->d_pstart, x, y);
+      p1_tile_kernel<T, false><<<grid, 256, smem, s>>>(dconst<T>(op), I->d_stencil_tasks, I->stencil_kchunk,
+                                                       I->d_pstart, x, y);
     HHG_CUDA_TRY(cudaGetLastError());
     return HHG_OK;
   }

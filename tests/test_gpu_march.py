@@ -126,3 +126,23 @@ def test_level8_sampled_sin3(degree):
         assert allpos(pts[e:e + 1], N)[0] == p
     ref = OA.sampled_diffusion_rows(v[t[0]], level, degree, ("sin3",), QD[degree], "dirichlet", xp, pts)
     assert np.abs(y[sample] - ref).max() <= 1e-12 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("meshname,level", [("reference_tet", 3), ("cube6", 2), ("cube48", 1)])
+@pytest.mark.parametrize("kind", ["sin3", "field"])
+@pytest.mark.parametrize("qd", [1, 2])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_p2_under_integration_parity(meshname, level, kind, qd, dtype):
+    """P2 variable coefficient with a rule of degree 2 (4 points) or 1: the paper's under-integration (U)."""
+    from gpu_helpers import Case, rel_err
+    import paper_2404_08371_gb300 as hhg
+    c = Case(meshname, level, 2)
+    lc, oc = _coeff(c, kind, dtype)
+    op = hhg.Operator(c.mesh, degree=2, coeff=lc, bc="dirichlet", quad_degree=qd)
+    xg = W.uniform(c.S.ndof, seed=0)
+    if dtype == torch.float32:
+        xg = xg.astype(np.float32).astype(np.float64)
+    y = op.apply(c.packed(xg, dtype))
+    ref = OA.diffusion_matrix(c.S, oc, qd, "dirichlet") @ xg
+    got, spread = c.unpack(y)
+    assert rel_err(got, ref) <= TOL[dtype] and spread == 0.0
