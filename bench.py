@@ -49,11 +49,11 @@ def flops_per_unit(name: str, degree: int, nq: int):
     if name.startswith("p1_const"):
         return ("dof", 30.0)                       # 15-point stencil: 15 FMA per point
     if name.startswith("p1_sin3"):
-        return ("tet", 2.0 * (nq * 8 + 16))        # k at nq points + 4x4 scaled apply
+        return ("tet", nq * 15.0 + 36.0)           # k at nq points (angle addition), kbar, 4x4 apply
     if name.startswith("p2_const"):
-        return ("tet", 2.0 * 100)
+        return ("tet", 2.0 * 100)                  # 10x10 apply
     if name.startswith("p2_sin3"):
-        return ("tet", 2.0 * nq * (30 + 10 + 30 + 8))
+        return ("tet", 117.0 * nq)                 # fused quadrature: grad u, k, metric, test (per point)
     return ("dof", 0.0)
 
 
@@ -66,16 +66,32 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-# FP64 / FP32 FMA-chain rates measured on this GPU type (see profiles/alu_peaks.md)
-ALU_PEAK_TFLOPS = {"f64": 1.01, "f32": 73.1}
+# FP64 / FP32 peaks from unit counts at the maximum SM clock (152 SMs x 2 / 128 FMA per clock x
+# 2 FLOP x 2.07 GHz); FMA-chain probes measure 1.10 / 77.0 TFLOP/s (profiles/alu_peaks.md)
+ALU_PEAK_TFLOPS = {"f64": 1.26, "f32": 80.5}
 
 
 def load_traffic():
+    """DRAM bytes per launch from an ncu capture (profiles/traffic.json), dropped when the kernel's
+    sources changed after the capture (their sha256 no longer matches)."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(path):
-        with open(path) as f:
-            return json.load(f)
-    return {}
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        table = json.load(f)
+    out = {}
+    for leg, rec in table.items():
+        h = hashlib.sha256()
+        try:
+            for fn in rec["sources"]:
+                with open(os.path.join(ROOT, fn), "rb") as f:
+                    h.update(f.read())
+        except OSError:
+            continue
+        if h.hexdigest() == rec["sources_sha256"]:
+            out[leg] = rec
+    return out
 
 
 class ClockSampler:
@@ -191,6 +207,20 @@ def run_fmg(hhg, torch, level: int, reps: int = 1):
         out[name]["l2_error_ratio_vs_level_%d" % (level - 1)] = errs[(name, level - 1)] / errs[(name, level)]
     out["mixed_speedup"] = out["fp64"]["solve_ms"] / out["mixed"]["solve_ms"]
     return out
+
+
+def aggregate_replicas(step_ms: float, dofs_step: float, device="cpu"):
+    """Whole-job figures of independent per-rank replicas: (max step time over ranks in ms, sum of
+    the ranks' DoFs per step, rate in MDoF/s = that sum / that max time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    d = torch.tensor([float(dofs_step)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(d, op=dist.ReduceOp.SUM)
+    ms, dofs = float(t.item()), float(d.item())
+    return ms, dofs, dofs / (ms * 1e-3) / 1e6
 
 
 def time_apply(torch, fn, flush, reps: int, warmup: int = 1):
@@ -370,12 +400,8 @@ def main():
     for L in legs:
         L["ms"] = [a.elapsed_time(b) for a, b in L["ev"]]
         step_ms += sum(L["ms"]) / args.steps
-    t_step = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
-    step_ms = float(t_step.item())
     dofs_step = sum(L["dofs"] for L in legs)
-    value = world * dofs_step / (step_ms * 1e-3) / 1e6
+    step_ms, dofs_all, value = aggregate_replicas(step_ms, dofs_step, dev)
 
     # end to end through the C-ABI with host buffers: pinned H2D of x, apply, D2H of y
     h2d = d2h = 0
@@ -395,7 +421,7 @@ def main():
         torch.cuda.synchronize()
         if s >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_value = world * dofs_step / (statistics.mean(e2e_ms) * 1e-3) / 1e6
+    _, _, e2e_value = aggregate_replicas(statistics.mean(e2e_ms), dofs_step, dev)
 
     peaks = load_peaks()
     traffic = load_traffic()
@@ -419,7 +445,7 @@ def main():
     dom_leg = [L for L in legs if L["name"] == dom][0]
     if D["alu_frac"] > D["hbm_frac"]:
         roof = {"bound": "alu", "achieved": D["tflops"], "peak": ALU_PEAK_TFLOPS[dom_leg["dt"]], "unit": "TFLOP/s",
-                "frac": D["alu_frac"], "peak_src": "measured FMA-chain rate (profiles/alu_peaks.md)"}
+                "frac": D["alu_frac"], "peak_src": "unit-count peak at 2.07 GHz (profiles/alu_peaks.md)"}
     else:
         roof = {"bound": "hbm", "achieved": D["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": D["hbm_frac"],
                 "peak_src": peaks["src"] + " (burst copy)"}

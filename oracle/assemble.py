@@ -243,3 +243,101 @@ def sampled_diffusion_rows(macro_xyz, level: int, degree: int, coeff, quad_degre
             xl = np.where(on_boundary(nodes), 0.0, xl)
         out[s] = sum(loc[e, rows[e], :] @ xl[e] for e in range(len(tv)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Nedelec edge space (Eq. N1)
+# ---------------------------------------------------------------------------
+
+# Canonical index-space direction of the edge whose doubled-lattice midpoint has this parity.
+EDGE_DIRS = {(1, 0, 0): (1, 0, 0), (0, 1, 0): (0, 1, 0), (0, 0, 1): (0, 0, 1), (1, 1, 0): (1, -1, 0),
+             (1, 0, 1): (1, 0, -1), (0, 1, 1): (0, 1, -1), (1, 1, 1): (1, -1, 1)}
+
+
+class EdgeSpace:
+    """One DoF per micro-edge: the tangential integral of u along the edge.
+
+    Global orientation: from the endpoint with the smaller global vertex number to the larger.
+    The library's packed layout uses the doubled lattice of each macro (the P2 layout); an edge's
+    entry is its tangential integral along the macro's canonical index direction of that edge
+    (EDGE_DIRS), i.e. local_sign times the global value; vertex entries are zero.
+    """
+
+    def __init__(self, mesh: MacroMesh, level: int):
+        self.mesh, self.level = mesh, level
+        self.n = n = 2 ** level
+        self.V1 = Space(mesh, level, 1)                                # vertices (global numbering)
+        pts2 = lattice_points(2 * n)
+        par = pts2 % 2
+        self.edge_pos = np.nonzero(par.any(axis=1))[0]                 # packed positions of edge points
+        ep = pts2[self.edge_pos]
+        d = np.array([EDGE_DIRS[tuple(q)] for q in par[self.edge_pos]])
+        tail, head = (ep - d) // 2, (ep + d) // 2
+        vpos_t = packed_position(tail, n)
+        vpos_h = packed_position(head, n)
+        keys = np.concatenate([point_keys(mesh.tets[m], ep, 2 * n) for m in range(mesh.nmacro)], axis=0)
+        _, inv = np.unique(keys, axis=0, return_inverse=True)
+        E = len(ep)
+        self.gid = inv.reshape(mesh.nmacro, E)
+        self.ndof = int(inv.max()) + 1
+        vt = np.stack([self.V1.gid[m][vpos_t] for m in range(mesh.nmacro)])
+        vh = np.stack([self.V1.gid[m][vpos_h] for m in range(mesh.nmacro)])
+        self.local_sign = np.where(vt < vh, 1.0, -1.0)                 # macro-local vs global orientation
+        # global endpoints (tail -> head in global orientation)
+        self.g_tail = np.empty(self.ndof, dtype=np.int64)
+        self.g_head = np.empty(self.ndof, dtype=np.int64)
+        self.g_tail[self.gid.reshape(-1)] = np.minimum(vt, vh).reshape(-1)
+        self.g_head[self.gid.reshape(-1)] = np.maximum(vt, vh).reshape(-1)
+        # Dirichlet (tangential trace): edges whose midpoint lies on a boundary face
+        w = np.stack([2 * n - ep.sum(axis=1), ep[:, 0], ep[:, 1], ep[:, 2]], axis=1)
+        self.boundary = np.zeros(self.ndof, dtype=bool)
+        for m in range(mesh.nmacro):
+            for a in range(4):
+                if mesh.boundary_face[m, a]:
+                    self.boundary[self.gid[m, w[:, a] == 0]] = True
+        # elements: the micro-tets of the P1 space, their 6 edges and orientation signs
+        Vg = self.V1.elem_dofs                                          # (nel, 4) global vertex ids
+        cls, tv = micro_tets(n)
+        mids = np.stack([tv[:, a] + tv[:, b] for a, b in P2_EDGES], axis=1)   # doubled midpoints
+        edge_index = -np.ones(len(pts2), dtype=np.int64)
+        edge_index[self.edge_pos] = np.arange(E)
+        loc = edge_index[packed_position(mids.reshape(-1, 3), 2 * n)].reshape(len(tv), 6)
+        self.elem_dofs = np.concatenate([self.gid[m][loc] for m in range(mesh.nmacro)], axis=0)
+        a_idx = np.array([a for a, b in P2_EDGES])
+        b_idx = np.array([b for a, b in P2_EDGES])
+        self.elem_sign = np.where(Vg[:, a_idx] < Vg[:, b_idx], 1.0, -1.0)
+        self.elem_X = self.V1.elem_X
+
+    def interpolate_field(self, u) -> np.ndarray:
+        """Tangential integrals (global orientation) of a vector field u(points) -> (npts, 3),
+        by the 3-point Gauss rule on each edge (exact for fields of degree <= 5 along the edge)."""
+        xt = self.V1.coords[self.g_tail]
+        xh = self.V1.coords[self.g_head]
+        g = np.array([0.5 - np.sqrt(15) / 10, 0.5, 0.5 + np.sqrt(15) / 10])
+        gw = np.array([5.0, 8.0, 5.0]) / 18.0
+        out = np.zeros(self.ndof)
+        for t, wt in zip(g, gw):
+            out += wt * np.einsum("ed,ed->e", u(xt + t * (xh - xt)), xh - xt)
+        return out
+
+
+def n1_matrix(space: EdgeSpace, alpha, beta, quad_degree: int = 4, bc: str = "dirichlet"):
+    """Global curl-curl + mass matrix (Eq. N1); alpha / beta as in coefficient_at_quadrature
+    (("const", v), ("func", f) or ("field", p1space, values))."""
+    P1 = space.V1
+    aq = coefficient_at_quadrature(P1, alpha, quad_degree)
+    bq = coefficient_at_quadrature(P1, beta, quad_degree)
+    loc = fe.n1_local(space.elem_X, quad_degree, aq, bq)
+    s = space.elem_sign
+    loc = loc * s[:, :, None] * s[:, None, :]
+    A = _scatter(None, space.elem_dofs, space.elem_dofs, loc, space.ndof, space.ndof)
+    return apply_bc(A, space.boundary, bc)
+
+
+def n1_gradient(space: EdgeSpace) -> sp.csr_matrix:
+    """Discrete gradient: (G p)_e = p(head) - p(tail) in the global orientation."""
+    E = space.ndof
+    rows = np.concatenate([np.arange(E), np.arange(E)])
+    cols = np.concatenate([space.g_head, space.g_tail])
+    vals = np.concatenate([np.ones(E), -np.ones(E)])
+    return sp.coo_matrix((vals, (rows, cols)), shape=(E, space.V1.ndof)).tocsr()

@@ -146,3 +146,34 @@ def epsilon_coeff_derivative(X: np.ndarray, quad_degree: int) -> np.ndarray:
     for m in range(10):
         out[:, m] = epsilon_local(X, quad_degree, np.broadcast_to(psi[None, :, m], (len(X), len(w))))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Lowest-order Nedelec (first kind) edge elements, Eq. N1 (Section 7.3)
+# ---------------------------------------------------------------------------
+
+def n1_local(X: np.ndarray, quad_degree: int, alpha_q, beta_q) -> np.ndarray:
+    """Local curl-curl + mass matrices (E, 6, 6) on the local edges (a, b) of P2_EDGES, oriented a -> b.
+
+    Basis (Whitney): phi_e = lambda_a grad lambda_b - lambda_b grad lambda_a, curl phi_e =
+    2 grad lambda_a x grad lambda_b;  A[e, f] = sum_q |det J| w_q (alpha(x_q) curl phi_e . curl phi_f
+    + beta(x_q) phi_e . phi_f).  alpha_q / beta_q: (E, nq) values or callables of points.
+    """
+    xi, w = quadrature.rule(quad_degree)
+    J, adet, Jinv = jacobians(X)
+    G = np.einsum("eji,aj->eai", Jinv, GRAD_BARY)                  # grad lambda_a, (E, 4, 3)
+
+    def values(c):
+        if callable(c):
+            return c(map_points(X, J, xi).reshape(-1, 3)).reshape(len(X), len(w))
+        return np.asarray(c, dtype=np.float64)
+    av, bv = values(alpha_q), values(beta_q)
+    lam = bary(xi)                                                 # (nq, 4)
+    curl = np.stack([2.0 * np.cross(G[:, a], G[:, b]) for a, b in P2_EDGES], axis=1)   # (E, 6, 3)
+    phi = np.stack([lam[None, :, a, None] * G[:, None, b, :] - lam[None, :, b, None] * G[:, None, a, :]
+                    for a, b in P2_EDGES], axis=2)                 # (E, nq, 6, 3)
+    sa = adet[:, None] * w[None, :] * av
+    sb = adet[:, None] * w[None, :] * bv
+    A = np.einsum("eq,eia,eja->eij", sa, curl, curl)
+    A += np.einsum("eq,eqia,eqja->eij", sb, phi, phi)
+    return A

@@ -42,3 +42,36 @@ def copies_spread(space: Space, xp: np.ndarray, ncomp: int = 1, nrhs: int = 1) -
     np.minimum.at(lo, flat, xp)
     np.maximum.at(hi, flat, xp)
     return float(np.max(hi - lo)) if len(flat) else 0.0
+
+
+def n1_to_packed(space, xg: np.ndarray) -> np.ndarray:
+    """Global N1 vector -> packed (doubled-lattice) layout in macro-local orientation."""
+    from .mesh import lattice_size
+    P = lattice_size(2 * space.n)
+    out = np.zeros((space.mesh.nmacro, P))
+    out[:, space.edge_pos] = space.local_sign * np.asarray(xg)[space.gid]
+    return out.reshape(-1)
+
+
+def n1_from_packed(space, xp: np.ndarray) -> np.ndarray:
+    """Packed N1 vector -> global vector, from the copy in the lowest-numbered macro."""
+    from .mesh import lattice_size
+    P = lattice_size(2 * space.n)
+    xp = np.asarray(xp, dtype=np.float64).reshape(space.mesh.nmacro, P)[:, space.edge_pos]
+    vals = space.local_sign * xp
+    flat = space.gid.reshape(-1)
+    _, first = np.unique(flat, return_index=True)
+    return vals.reshape(-1)[first]
+
+
+def n1_copies_spread(space, xp: np.ndarray) -> float:
+    """Largest difference between the copies (global orientation) of a shared edge."""
+    from .mesh import lattice_size
+    P = lattice_size(2 * space.n)
+    vals = (space.local_sign * np.asarray(xp, dtype=np.float64).reshape(space.mesh.nmacro, P)[:, space.edge_pos])
+    flat, v = space.gid.reshape(-1), vals.reshape(-1)
+    lo = np.full(space.ndof, np.inf)
+    hi = np.full(space.ndof, -np.inf)
+    np.minimum.at(lo, flat, v)
+    np.maximum.at(hi, flat, v)
+    return float(np.max(hi - lo))
