@@ -287,6 +287,31 @@ def run_eps(hhg, torch, flush, level: int = 6, nrhs: int = 16, reps: int = 1):
             "adjoint_mdofs": 3 * inner * nrhs / ms_adj / 1e3, "micro_tets": ntet}
 
 
+def run_n1(hhg, torch, flush, level: int = 7, reps: int = 3):
+    """Nedelec curl-curl + mass (Eq. N1) on the 36-macro 3x2x1 cuboid (the paper's test domain) at
+    level 7, alpha and beta P1 fields, FP64 and FP32, Dirichlet; MDoF/s counts interior edges."""
+    import workloads as W
+    v, t = W.cuboid36()
+    mesh = hhg.Mesh(v, t, level)
+    out = {"workload": "3x2x1 cuboid as 36 macros, level %d, N1 curl-curl + mass, alpha = 1 + x/3, "
+                       "beta = 1 + z (P1 fields), Dirichlet" % level}
+    xyz1 = mesh.coordinates(1)
+    # interior edges: the distinct edge midpoints minus the boundary ones (from the degree-2 counts)
+    tot2, int2 = mesh.dof_count(2)
+    tot1, int1 = mesh.dof_count(1)
+    n_edges_interior = int2 - int1
+    for dt, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+        a = (1.0 + xyz1[:, 0] / 3.0).to(tdt).contiguous()
+        b = (1.0 + xyz1[:, 2]).to(tdt).contiguous()
+        op = hhg.CurlCurl(mesh, ("field_p1", a), ("field_p1", b), bc="dirichlet")
+        x = torch.from_numpy(W.uniform(mesh.vec_size(2), seed=0)).to("cuda", tdt)
+        y = torch.empty_like(x)
+        ms = time_apply(torch, lambda: op.apply(x, out=y), flush, reps)
+        out[dt] = {"ms": ms, "mdofs": n_edges_interior / ms / 1e3, "interior_edges": n_edges_interior}
+        del op, x, y
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -461,6 +486,8 @@ def main():
         extra["const_legs"] = run_const_legs(hhg, torch, flush, peaks["hbm_gbs"])
         torch.cuda.empty_cache()
         extra["epsilon"] = run_eps(hhg, torch, flush)
+        torch.cuda.empty_cache()
+        extra["n1"] = run_n1(hhg, torch, flush)
         torch.cuda.empty_cache()
     fmg = None
     if not args.no_fmg:

@@ -60,7 +60,7 @@ extern "C" {
 #define HHG_E_UNSUPPORTED (-8)   /* valid but not implemented combination */
 
 enum { HHG_F32 = 0, HHG_F64 = 1 };
-enum { HHG_DIFFUSION = 0, HHG_EPSILON = 1 };
+enum { HHG_DIFFUSION = 0, HHG_EPSILON = 1, HHG_CURLCURL = 2 };
 enum { HHG_DIRICHLET = 0, HHG_NEUMANN = 1 };
 enum {
   HHG_COEFF_CONST = 0,    /* k(x) = value */
@@ -116,6 +116,23 @@ int hhg_dof_count(const hhg_mesh_t* mesh, int level, int degree, int64_t* total,
 int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, const hhg_coeff_t* coeff, int bc,
                   int quad_degree, hhg_op_t** out);
 int hhg_op_destroy(hhg_op_t* op);
+
+/* Create the lowest-order Nedelec (first kind) operator
+ *     a(u, v) = int alpha curl u . curl v + beta u . v        (Eq. N1)
+ * at `level` (-1 = finest).  alpha, beta: HHG_COEFF_CONST or HHG_COEFF_FIELD_P1
+ * (a P1 packed vector at the op's level, borrowed as for hhg_coeff_t).  The
+ * DoFs are the micro-edges, stored in the degree-2 packed layout: the entry of
+ * the edge midpoint holds the tangential integral of u along the macro's
+ * canonical index direction of that edge -- (1,0,0), (0,1,0), (0,0,1),
+ * (1,-1,0), (1,0,-1), (0,1,-1) or (1,-1,1) for midpoints whose doubled
+ * coordinates have the odd entries (i), (j), (k), (i,j), (i,k), (j,k), (i,j,k)
+ * -- and vertex entries are zero.  A point shared by macros holds the value
+ * of its own macro's orientation (copies may differ in sign).  DIRICHLET
+ * fixes the tangential trace: edges on boundary faces return their input.
+ * Apply with hhg_op_apply (nrhs = 1).  Errors: HHG_E_ARG, HHG_E_UNSUPPORTED,
+ * HHG_E_OOM, HHG_E_CUDA. */
+int hhg_op_create_curlcurl(hhg_mesh_t* mesh, int level, const hhg_coeff_t* alpha, const hhg_coeff_t* beta, int bc,
+                           hhg_op_t** out);
 
 /* Replace the borrowed coefficient field pointer of a FIELD operator. */
 int hhg_op_set_field(hhg_op_t* op, const void* field, int field_dtype);

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (HHG_F32, HHG_F64, HHG_DIFFUSION, HHG_EPSILON, HHG_DIRICHLET, HHG_NEUMANN, HHG_COEFF_CONST,
                    HHG_COEFF_SIN3, HHG_COEFF_FIELD_P1, HHG_COEFF_FIELD_P2, HHGError, check, lib)
 
-__all__ = ["Mesh", "Operator", "HHGError", "lib", "dtype_code"]
+__all__ = ["Mesh", "Operator", "CurlCurl", "HHGError", "lib", "dtype_code"]
 
 
 def dtype_code(t: torch.Tensor) -> int:
@@ -211,3 +211,39 @@ class Operator:
                  "setup_ms": st.setup_ms, "solve_ms": st.solve_ms, "status": code}
         check(code, "hhg_mg_solve")
         return x, stats
+
+
+class CurlCurl(Operator):
+    """Lowest-order Nedelec operator alpha curl curl + beta (Eq. N1) on the micro-edges.
+
+    Vectors use the degree-2 packed layout (edge-midpoint entries; vertex entries zero).
+    alpha, beta: ("const", value) or ("field_p1", tensor) -- a P1 packed vector, borrowed.
+    """
+
+    def __init__(self, mesh: Mesh, alpha=("const", 1.0), beta=("const", 1.0), bc: str = "dirichlet",
+                 level: int | None = None):
+        self.mesh = mesh
+        self.kind = _lib.HHG_CURLCURL
+        self.degree = 2
+        self.level = mesh.level if level is None else level
+        self.ncomp = 1
+        self.field = None
+        self.fields = []
+        cs = []
+        for spec in (alpha, beta):
+            c = _lib.hhg_coeff_t()
+            c.type = _COEFF_TYPES[spec[0]]
+            if spec[0] == "const":
+                c.value = float(spec[1])
+            else:
+                self.fields.append(spec[1])
+                c.field = _dev_ptr(spec[1])
+                c.field_dtype = dtype_code(spec[1])
+            cs.append(c)
+        h = ctypes.c_void_p()
+        check(lib.hhg_op_create_curlcurl(mesh.handle, self.level, ctypes.byref(cs[0]), ctypes.byref(cs[1]),
+                                         {"dirichlet": HHG_DIRICHLET, "neumann": HHG_NEUMANN}[bc], ctypes.byref(h)),
+              "hhg_op_create_curlcurl")
+        self.handle = h
+        self.bc = bc
+        self.coeff = (alpha, beta)

@@ -16,7 +16,7 @@ HHG_OK = 0
 HHG_E_ARG, HHG_E_DEGENERATE, HHG_E_NONMANIFOLD, HHG_E_OOM, HHG_E_CUDA, HHG_E_NOT_CONVERGED, HHG_E_NAN, \
     HHG_E_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7, -8
 HHG_F32, HHG_F64 = 0, 1
-HHG_DIFFUSION, HHG_EPSILON = 0, 1
+HHG_DIFFUSION, HHG_EPSILON, HHG_CURLCURL = 0, 1, 2
 HHG_DIRICHLET, HHG_NEUMANN = 0, 1
 HHG_COEFF_CONST, HHG_COEFF_SIN3, HHG_COEFF_FIELD_P1, HHG_COEFF_FIELD_P2 = 0, 1, 2, 3
 
@@ -48,6 +48,8 @@ SIGNATURES = {
     "hhg_vec_size": ([_vp, _i, _i, ctypes.POINTER(_i64)], _i),
     "hhg_dof_count": ([_vp, _i, _i, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _i),
     "hhg_op_create": ([_vp, _i, _i, _i, ctypes.POINTER(hhg_coeff_t), _i, _i, ctypes.POINTER(_vp)], _i),
+    "hhg_op_create_curlcurl": ([_vp, _i, ctypes.POINTER(hhg_coeff_t), ctypes.POINTER(hhg_coeff_t), _i,
+                                ctypes.POINTER(_vp)], _i),
     "hhg_op_destroy": ([_vp], _i),
     "hhg_op_set_field": ([_vp, _vp, _i], _i),
     "hhg_op_apply": ([_vp, _vp, _vp, _i, _i, _vp], _i),

@@ -58,6 +58,9 @@ struct Interface {
   int64_t ndof_interior = 0;
   std::vector<int64_t> h_ptr, h_idx;   // host copies of the groups (set-up code)
   std::vector<uint8_t> h_bnd;
+  // degree-2 data: orientation of each copy of an edge point relative to the group's first copy
+  // (+1 / -1; +1 for vertex points), used by the Nedelec operator
+  int8_t* d_sign = nullptr;
   // launch tables of the gather kernels: CTAs of 256 points never cross a plane
   int64_t ncta = 0;
   int* d_cta_plane = nullptr;   // plane of each CTA
@@ -160,6 +163,12 @@ int launch_make_consistent(const Interface* itf, T* x, int per_point, cudaStream
 template <typename T>
 int launch_march(const struct ::hhg_op* op, const OpConst<T>* cst, int mode, const T* x, const T* g, const T* kf,
                  T* out, cudaStream_t s);
+// Nedelec curl-curl + mass apply (march.cu, R = 2 traversal of the doubled lattice).
+template <typename T>
+int launch_n1(const struct ::hhg_op* op, const T* x, T* y, cudaStream_t s);
+// Interface sum with orientation signs (edge points of the doubled lattice).
+template <typename T>
+int launch_interface_sum_signed(const Interface* itf, T* y, bool dirichlet, cudaStream_t s);
 // P2 vector epsilon operator (eps.cu): mode 0 apply to nrhs right-hand sides, 2 adjoint in mu.
 template <typename T>
 int launch_eps(const struct ::hhg_op* op, const OpConst<T>* cst, int mode, int nrhs, const T* x, const T* g,
@@ -170,10 +179,27 @@ int launch_l2_error(const struct ::hhg_op* op, const double* uh, double* partial
 
 }  // namespace hhg
 
+namespace hhg {
+// Hoisted per-class data of the Nedelec operator (one block per macro):
+//   C[o][e][f] = |T| curl phi_e . curl phi_f   (curl phi_e = 2 grad l_a x grad l_b, constant)
+//   M[o][v][e][f] = int_T lambda_v phi_e . phi_f  (exact)
+//   sgn[o][e] = +1 if local edge e (a -> b) runs along the canonical lattice direction, else -1
+template <typename T>
+struct alignas(16) N1Const {
+  T C[6][6][6];
+  T M[6][4][6][6];
+  T sgn[6][6];
+  int64_t vbase;     // offset of the macro in a packed P1 vector (coefficient fields)
+};
+}  // namespace hhg
+
 struct hhg_op {
   hhg_mesh* mesh = nullptr;
   int level = 0, kind = 0, degree = 1, bc = 0, quad_degree = 2;
   hhg_coeff_t coeff{};
+  hhg_coeff_t coeff2{};      // second coefficient (beta of the Nedelec operator)
+  void* d_n1_64 = nullptr;   // N1Const<double>[nmacro]
+  void* d_n1_32 = nullptr;
   int N = 0, n = 0;
   int64_t npts = 0;          // packed scalar entries of the space
   void* d_const64 = nullptr; // OpConst<double>[nmacro]

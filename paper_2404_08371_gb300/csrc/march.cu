@@ -19,6 +19,8 @@
 // against the basis gradients.  Gradients of the P2 basis are written through the
 // barycentric coordinates, so grad u = sum_a grad lambda_a s_a with
 // s_a = u_a (4 lambda_a - 1) + 4 sum_b u_ab lambda_b.
+#include <type_traits>
+
 #include "hhg_internal.h"
 #include "lattice.cuh"
 
@@ -26,7 +28,17 @@ namespace hhg {
 
 constexpr int kWarps = kMarchWarps;   // warps per CTA along j
 
-enum { MODE_APPLY = 0, MODE_DIAG = 1, MODE_ADJ = 2, MODE_RHS = 3 };
+enum { MODE_APPLY = 0, MODE_DIAG = 1, MODE_ADJ = 2, MODE_RHS = 3, MODE_N1 = 4 };
+
+// Extra inputs of the Nedelec mode (unused otherwise).
+template <typename T>
+struct N1Args {
+  const N1Const<T>* n1 = nullptr;
+  const T* alpha = nullptr;   // P1 fields (packed degree-1 vectors) or null for constants
+  const T* beta = nullptr;
+  T alpha_c = T(0), beta_c = T(0);
+  int n = 0;                  // cubes per edge (P1 lattice resolution)
+};
 
 __host__ __device__ constexpr int coff(int o, int v, int d) {
   constexpr int t[6][4][3] = {
@@ -110,12 +122,14 @@ template <typename T, int R, int COEF, int MODE, bool DIR>
 __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __restrict__ cst,
                                                             const int4* __restrict__ tasks, int kChunk,
                                                             const T* __restrict__ x, const T* __restrict__ g,
-                                                            const T* __restrict__ kf, T* __restrict__ out) {
+                                                            const T* __restrict__ kf, T* __restrict__ out,
+                                                            N1Args<T> n1a) {
   constexpr int P = R + 1;
   constexpr int P3 = P * P * P;
   constexpr int NL = R == 1 ? 4 : 10;
   __shared__ OpConst<T> c;
   __shared__ T xch[kWarps][P][R][32];
+  __shared__ typename std::conditional<MODE == MODE_N1, N1Const<T>, char>::type n1c;
   const int4 task = tasks[blockIdx.x];   // (i-tile, j-tile, k-chunk, macro), heaviest first
   const int macro = task.w;
   const int kc = task.z;
@@ -123,6 +137,11 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
     const int4* src = reinterpret_cast<const int4*>(cst + macro);
     int4* dst = reinterpret_cast<int4*>(&c);
     for (int t = threadIdx.x; t < (int)(sizeof(OpConst<T>) / sizeof(int4)); t += blockDim.x) dst[t] = src[t];
+    if constexpr (MODE == MODE_N1) {
+      const int4* s1 = reinterpret_cast<const int4*>(n1a.n1 + macro);
+      int4* d1 = reinterpret_cast<int4*>(&n1c);
+      for (int t = threadIdx.x; t < (int)(sizeof(N1Const<T>) / sizeof(int4)); t += blockDim.x) d1[t] = s1[t];
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -183,7 +202,7 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
             const bool in = pi + pj + pk <= N;
             const int64_t idx = in ? packed_index(N, pi, pj, pk) : 0;
             const bool live = in && !(DIR && on_dirichlet(table, N, pi, pj, pk));
-            if (MODE == MODE_APPLY || MODE == MODE_ADJ) xb[s] = live ? __ldg(x + base + idx) : T(0);
+            if (MODE == MODE_APPLY || MODE == MODE_ADJ || MODE == MODE_N1) xb[s] = live ? __ldg(x + base + idx) : T(0);
             if (MODE == MODE_ADJ) gb[s] = live ? __ldg(g + base + idx) : T(0);
             if (COEF == HHG_COEFF_FIELD_P1 || COEF == HHG_COEFF_FIELD_P2) kb[s] = in ? __ldg(kf + c.kbase + idx) : T(0);
           }
@@ -201,10 +220,44 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
         T ul[NL], yl[NL];
 #pragma unroll
         for (int a = 0; a < NL; ++a) {
-          ul[a] = (MODE == MODE_APPLY || MODE == MODE_ADJ) ? xb[node_slot<R>(o, a)] : T(0);
+          ul[a] = (MODE == MODE_APPLY || MODE == MODE_ADJ || MODE == MODE_N1) ? xb[node_slot<R>(o, a)] : T(0);
           yl[a] = T(0);
         }
-        if (MODE == MODE_RHS) {
+        if constexpr (MODE == MODE_N1) {
+          // Nedelec edge element (Eq. N1): the six edge nodes of the P2 numbering carry the DoFs
+          if constexpr (R == 2) {
+            const int nn = n1a.n;
+            T av[4], bv[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const int vi = ci + coff(o, v, 0), vj = cj + coff(o, v, 1), vk = ck + coff(o, v, 2);
+              const int64_t vidx = n1c.vbase + packed_index(nn, vi, vj, vk);
+              av[v] = n1a.alpha ? __ldg(n1a.alpha + vidx) : n1a.alpha_c;
+              bv[v] = n1a.beta ? __ldg(n1a.beta + vidx) : n1a.beta_c;
+            }
+            const T abar = T(0.25) * (av[0] + av[1] + av[2] + av[3]);
+            T ue[6], ye[6];
+#pragma unroll
+            for (int e = 0; e < 6; ++e) {
+              ue[e] = n1c.sgn[o][e] * ul[4 + e];
+              ye[e] = T(0);
+            }
+#pragma unroll
+            for (int e = 0; e < 6; ++e) {
+              T sc = T(0), sm = T(0);
+#pragma unroll
+              for (int f = 0; f < 6; ++f) {
+                sc += n1c.C[o][e][f] * ue[f];
+                const T mb = bv[0] * n1c.M[o][0][e][f] + bv[1] * n1c.M[o][1][e][f] + bv[2] * n1c.M[o][2][e][f] +
+                             bv[3] * n1c.M[o][3][e][f];
+                sm += mb * ue[f];
+              }
+              ye[e] = abar * sc + sm;
+            }
+#pragma unroll
+            for (int e = 0; e < 6; ++e) yl[4 + e] = n1c.sgn[o][e] * ye[e];
+          }
+        } else if (MODE == MODE_RHS) {
           // b_a += sum_q w_q |det J| f(x_q) phi_a(xi_q), f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
           for (int q = 0; q < c.nq; ++q) {
             T xq[3];
@@ -370,7 +423,7 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
             const int64_t idx = base + packed_index(N, pi, pj, pk);
             T v = acc[cx + P * (cy + P * cz)];
             if (DIR && MODE != MODE_ADJ && on_dirichlet(table, N, pi, pj, pk))
-              v = MODE == MODE_APPLY ? x[idx] : (MODE == MODE_DIAG ? T(1) : T(0));
+              v = (MODE == MODE_APPLY || MODE == MODE_N1) ? x[idx] : (MODE == MODE_DIAG ? T(1) : T(0));
             out[idx] = v;
           }
     }
@@ -379,15 +432,15 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
 
 template <typename T, int R, int COEF, int MODE>
 static int launch_march_t(const hhg_op* op, const OpConst<T>* cst, const T* x, const T* g, const T* kf, T* out,
-                          cudaStream_t s) {
+                          cudaStream_t s, N1Args<T> n1a = N1Args<T>()) {
   const Interface* I = op->itf;
   const unsigned grid = (unsigned)I->n_march_tasks;
   if (op->bc == HHG_DIRICHLET)
     march_kernel<T, R, COEF, MODE, true><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x, g, kf,
-                                                                       out);
+                                                                       out, n1a);
   else
     march_kernel<T, R, COEF, MODE, false><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x, g,
-                                                                        kf, out);
+                                                                        kf, out, n1a);
   HHG_CUDA_TRY(cudaGetLastError());
   return HHG_OK;
 }
@@ -479,6 +532,21 @@ int launch_l2_error(const hhg_op* op, const double* uh, double* partial, cudaStr
   HHG_CUDA_TRY(cudaGetLastError());
   return HHG_OK;
 }
+
+template <typename T>
+int launch_n1(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
+  N1Args<T> a;
+  a.n1 = (const N1Const<T>*)(sizeof(T) == 8 ? op->d_n1_64 : op->d_n1_32);
+  a.alpha = op->coeff.type == HHG_COEFF_FIELD_P1 ? (const T*)op->coeff.field : nullptr;
+  a.beta = op->coeff2.type == HHG_COEFF_FIELD_P1 ? (const T*)op->coeff2.field : nullptr;
+  a.alpha_c = (T)op->coeff.value;
+  a.beta_c = (T)op->coeff2.value;
+  a.n = op->n;
+  const OpConst<T>* cst = (const OpConst<T>*)(sizeof(T) == 8 ? op->d_const64 : op->d_const32);
+  return launch_march_t<T, 2, HHG_COEFF_CONST, MODE_N1>(op, cst, x, nullptr, nullptr, y, s, a);
+}
+template int launch_n1<double>(const hhg_op*, const double*, double*, cudaStream_t);
+template int launch_n1<float>(const hhg_op*, const float*, float*, cudaStream_t);
 
 template int launch_march<double>(const hhg_op*, const OpConst<double>*, int, const double*, const double*,
                                   const double*, double*, cudaStream_t);

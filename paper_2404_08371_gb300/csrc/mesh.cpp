@@ -55,6 +55,7 @@ Interface::~Interface() {
   cudaFree(d_pstart);
   cudaFree(d_march_tasks);
   cudaFree(d_stencil_tasks);
+  cudaFree(d_sign);
 }
 
 // ---------------------------------------------------------------------------
@@ -221,6 +222,7 @@ struct PointKey {
   uint64_t k[4];
   int64_t pos;
   uint8_t bnd;
+  int8_t dir_tail_first;   // edge points: +1 if the canonical direction's tail has the smaller key
   bool operator<(const PointKey& o) const {
     for (int t = 0; t < 4; ++t)
       if (k[t] != o.k[t]) return k[t] < o.k[t];
@@ -400,6 +402,32 @@ int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
             pk.k[t] = t < c ? ((uint64_t)(uint32_t)pr[t].first << 32) | (uint64_t)pr[t].second : ~0ull;
           pk.pos = mac * V + rowbase + i;
           pk.bnd = (g.bnd_table >> z) & 1;
+          pk.dir_tail_first = 1;
+          if (degree == 2 && ((i | j | k) & 1)) {
+            // edge midpoint: endpoints (p -+ d) / 2 along the canonical direction d of its parity;
+            // orientation relative to a macro-independent order of the endpoints' keys
+            const int pi = (int)(i & 1), pj = (int)(j & 1), pkk = (int)(k & 1);
+            int d[3] = {pi, pj, pkk};
+            if (pi && pj && !pkk) d[1] = -1;
+            if (pi && !pj && pkk) d[2] = -1;
+            if (!pi && pj && pkk) d[2] = -1;
+            if (pi && pj && pkk) d[1] = -1;
+            std::array<std::array<uint64_t, 4>, 2> ek;
+            for (int side = 0; side < 2; ++side) {
+              const int sg = side == 0 ? -1 : 1;
+              const int64_t ti = (i + sg * d[0]) / 2, tj = (j + sg * d[1]) / 2, tk = (k + sg * d[2]) / 2;
+              const int64_t n1 = N / 2;
+              const int64_t wv[4] = {n1 - ti - tj - tk, ti, tj, tk};
+              std::array<std::pair<int32_t, int64_t>, 4> pv;
+              int cv = 0;
+              for (int a = 0; a < 4; ++a)
+                if (wv[a] > 0) pv[cv++] = {g.vid[a], wv[a]};
+              std::sort(pv.begin(), pv.begin() + cv);
+              for (int t = 0; t < 4; ++t)
+                ek[side][t] = t < cv ? ((uint64_t)(uint32_t)pv[t].first << 32) | (uint64_t)pv[t].second : ~0ull;
+            }
+            pk.dir_tail_first = ek[0] < ek[1] ? 1 : -1;
+          }
           keys.push_back(pk);
         }
       }
@@ -407,12 +435,16 @@ int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
   std::sort(keys.begin(), keys.end());
   std::vector<int64_t> ptr{0}, idx;
   std::vector<uint8_t> bnd;
+  std::vector<int8_t> sgn;
   int64_t dup = 0, dup_bnd = 0;
   for (size_t a = 0; a < keys.size();) {
     size_t b = a + 1;
     while (b < keys.size() && keys[b].same(keys[a])) ++b;
     if (b - a >= 2) {
-      for (size_t t = a; t < b; ++t) idx.push_back(keys[t].pos);
+      for (size_t t = a; t < b; ++t) {
+        idx.push_back(keys[t].pos);
+        sgn.push_back((int8_t)(keys[t].dir_tail_first * keys[a].dir_tail_first));
+      }
       ptr.push_back((int64_t)idx.size());
       uint8_t isb = keys[a].bnd;   // equal for all copies
       bnd.push_back(isb);
@@ -529,6 +561,8 @@ int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
     HHG_CUDA_TRY(cudaMemcpy(I->d_ptr, ptr.data(), sizeof(int64_t) * ptr.size(), cudaMemcpyHostToDevice));
     HHG_CUDA_TRY(cudaMemcpy(I->d_idx, idx.data(), sizeof(int64_t) * idx.size(), cudaMemcpyHostToDevice));
     HHG_CUDA_TRY(cudaMemcpy(I->d_bnd, bnd.data(), bnd.size(), cudaMemcpyHostToDevice));
+    HHG_CUDA_TRY(cudaMalloc(&I->d_sign, sgn.size()));
+    HHG_CUDA_TRY(cudaMemcpy(I->d_sign, sgn.data(), sgn.size(), cudaMemcpyHostToDevice));
   }
   *out = I.get();
   iface[key] = std::move(I);

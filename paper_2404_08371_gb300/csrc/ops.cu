@@ -362,142 +362,18 @@ __global__ void __launch_bounds__(256) p1_gather_kernel(const OpConst<T>* __rest
 }
 
 
-// Window of row (jr, kr): x at i = i0 - 1 .. i0 + V, zero outside the row and (DIRICHLET) at
-// Dirichlet points.
-template <typename T, int V, bool DIRICHLET>
-__device__ __forceinline__ void p1_window(const T* __restrict__ xm, const int* __restrict__ pstart, int N,
-                                          uint32_t table, int i0, int jr, int kr, T w[V + 2]) {
-  const int len = N - jr - kr + 1;   // points of the row (none if <= 0)
-  if (jr < 0 || kr < 0 || kr > N || len <= 0) {
-#pragma unroll
-    for (int t = 0; t < V + 2; ++t) w[t] = T(0);
-    return;
-  }
-  const T* __restrict__ row = xm + __ldg(pstart + kr) + row32(N - kr, jr);
-  const bool rowface = (jr == 0) | (kr == 0);
-  if (!rowface && i0 >= 2 && i0 + V < len - 1) {
-    // the window lies inside the row, away from its end points: no bounds, no Dirichlet points
-#pragma unroll
-    for (int t = 0; t < V + 2; ++t) w[t] = __ldg(row + i0 - 1 + t);
-    return;
-  }
-#pragma unroll
-  for (int t = 0; t < V + 2; ++t) {
-    const int ii = i0 - 1 + t;
-    T v = (ii >= 0 && ii < len) ? __ldg(row + ii) : T(0);
-    if (DIRICHLET && (rowface || ii == 0 || ii == len - 1) && ii >= 0 && ii < len &&
-        on_dirichlet(table, N, ii, jr, kr))
-      v = T(0);
-    w[t] = v;
-  }
-}
-
-// P1 constant-coefficient apply.  A CTA of 8 warps owns 8 rows j (one per warp) of an i-chunk of
-// 32*V points (V consecutive points per lane) and climbs the planes k of a k-chunk.  Each lane
-// keeps the seven row windows of the 15-point stencil -- rows (j,k), (j+-1,k), (j,k+1),
-// (j-1,k+1), (j,k-1), (j+1,k-1) -- in registers and rotates them when k advances, so a step
-// loads three new windows.  All 24 micro-tets around a point off the macro faces exist, so its
-// row of A is the 15-point stencil folded from the six hoisted class matrices; Dirichlet
-// columns were zeroed when the windows were loaded.
-template <typename T, int V, bool DIRICHLET>
-__global__ void __launch_bounds__(256) p1_stencil_kernel(const OpConst<T>* __restrict__ cst,
-                                                          const int4* __restrict__ tasks, int kch,
-                                                          const int* __restrict__ pstart, const T* __restrict__ x,
-                                                          T* __restrict__ y) {
-  const int4 task = tasks[blockIdx.x];
-  const OpConst<T>& c = cst[task.w];
-  const int N = c.N;
-  const uint32_t table = c.bnd_table;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = task.x * 32 * V + V * lane;
-  const int j = task.y * kStencilWarps + warp;
-  const int k0 = task.z * kch;
-  // last plane with a point of this warp's row segment
-  const int k_end = min(k0 + kch - 1, N - j - task.x * 32 * V);
-  if (k_end < k0) return;
-  const T* __restrict__ xm = x + c.base;
-  T* __restrict__ ym = y + c.base;
-  T S[15];
-#pragma unroll
-  for (int d = 0; d < 15; ++d) S[d] = c.S[d];
-  T w00[V + 2], wp0[V + 2], wm0[V + 2], w01[V + 2], wm1[V + 2], w0m[V + 2], wpm[V + 2];
-  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j, k0, w00);
-  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j + 1, k0, wp0);
-  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j - 1, k0, wm0);
-  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j, k0 + 1, w01);
-  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j - 1, k0 + 1, wm1);
-  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j, k0 - 1, w0m);
-  p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j + 1, k0 - 1, wpm);
-  for (int k = k0; k <= k_end; ++k) {
-    const int len = N - j - k + 1;
-    if (i0 < len) {
-      const int rowbase = __ldg(pstart + k) + row32(N - k, j);
-      if (j >= 1 && k >= 1 && i0 >= 1 && i0 + V <= len - 2) {
-        // all V points lie off the macro faces: the interior stencil
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-          ym[rowbase + i0 + v] = S[0] * w00[v + 1] + S[1] * w00[v + 2] + S[2] * w00[v] + S[3] * wp0[v + 1] +
-                                 S[4] * wm0[v + 1] + S[5] * w01[v + 1] + S[6] * w0m[v + 1] + S[7] * wm0[v + 2] +
-                                 S[8] * wp0[v] + S[9] * w0m[v + 2] + S[10] * w01[v] + S[11] * wpm[v + 1] +
-                                 S[12] * wm1[v + 1] + S[13] * wm1[v + 2] + S[14] * wpm[v];
-      } else
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int ii = i0 + v;
-        if (ii >= len) break;
-        T acc;
-        const int z = (ii == len - 1) | ((ii == 0) << 1) | ((j == 0) << 2) | ((k == 0) << 3);
-        if (DIRICHLET && z && ((table >> z) & 1u)) {
-          acc = __ldg(xm + rowbase + ii);
-        } else if (__popc(z) <= 1) {
-          // inside the macro, or inside one macro face (its own stencil: the missing micro-tets
-          // drop out; the neighbours outside the macro read as zero)
-          T W[15];
-          if (z == 0) {
-#pragma unroll
-            for (int d = 0; d < 15; ++d) W[d] = S[d];
-          } else {
-            const T* Sf = c.Sface[__ffs(z) - 1];
-#pragma unroll
-            for (int d = 0; d < 15; ++d) W[d] = Sf[d];
-          }
-          acc = W[0] * w00[v + 1] + W[1] * w00[v + 2] + W[2] * w00[v] + W[3] * wp0[v + 1] + W[4] * wm0[v + 1] +
-                W[5] * w01[v + 1] + W[6] * w0m[v + 1] + W[7] * wm0[v + 2] + W[8] * wp0[v] + W[9] * w0m[v + 2] +
-                W[10] * w01[v] + W[11] * wpm[v + 1] + W[12] * wm1[v + 1] + W[13] * wm1[v + 2] + W[14] * wpm[v];
-        } else {
-          // on a macro edge or vertex
-          acc = p1_face_point<T, DIRICHLET>(c, pstart, xm, ii, j, k);
-        }
-        ym[rowbase + ii] = acc;
-      }
-    }
-    if (k == k_end) break;
-    // rotate: plane k becomes k-1, plane k+1 becomes k; load the three new windows
-#pragma unroll
-    for (int t = 0; t < V + 2; ++t) {
-      w0m[t] = w00[t];
-      wpm[t] = wp0[t];
-      w00[t] = w01[t];
-      wm0[t] = wm1[t];
-    }
-    p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j + 1, k + 1, wp0);
-    p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j, k + 2, w01);
-    p1_window<T, V, DIRICHLET>(xm, pstart, N, table, i0, j - 1, k + 2, wm1);
-  }
-}
-
-// P1 constant-coefficient apply with shared-memory plane tiles.  A CTA owns rows j0..j0+7 and
-// points i0..i0+127 of a k-chunk (task list of the stencil kernel).  For every plane it stages
-// the tile plus a one-point halo (10 rows x 130 points) into a three-plane rolling buffer --
-// one coalesced global load per staged value, Dirichlet points staged as zero -- and each thread
-// then evaluates the 15-point stencil of four points (i = i0 + lane + 32 v) from shared memory.
-constexpr int kTileI = 32 * kStencilV;           // 128 points along i
+// P1 constant-coefficient apply in FP32 from shared-memory plane tiles.  A CTA owns rows
+// j0..j0+7 and points i0..i0+kTileI-1 of a k-chunk (task list of the stencil kernel) and climbs
+// its planes.  Each plane of the tile plus a one-point halo is staged with cp.async into a ring of
+// shared-memory planes, kTileDepth planes ahead of the plane being computed (one global load per
+// staged value; Dirichlet points zeroed after arrival); each thread evaluates the 15-point
+// stencil of its pairs of points from three staged planes with packed FMA.
+constexpr int kTileI = 32 * kStencilV;           // points along i (kStencilV per lane)
 constexpr int kTileJ = kStencilWarps;            // 8 rows
-constexpr int kTileW = kTileI + 4;               // staged width (130 used, padded)
 constexpr int kTileH = kTileJ + 2;               // staged rows
 
 constexpr int kTileDepth = 4;                      // planes staged ahead of the one being computed
-constexpr int kTileRing = kTileDepth + 2;          // planes k-1 .. k+kTileDepth
+constexpr int kTileRing = kTileDepth + 3;          // planes k-2 .. k+kTileDepth: one barrier per plane
 
 __device__ __forceinline__ void cp_async_zfill(void* smem, const void* gmem, int bytes, bool valid) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -513,126 +389,203 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(NPENDING));
 }
 
-// Issue the asynchronous staging of plane kk (tile rows j0-1 .. j0+8, points i0-1 .. i0+128);
-// positions outside the macro are zero-filled.
-template <typename T>
-__device__ __forceinline__ void p1_issue_plane(T (*slot)[kTileW], const T* __restrict__ xm,
-                                               const int* __restrict__ pstart, int N, int i0, int j0, int kk) {
+// FP32 variant with packed FMA (Blackwell fma.rn.f32x2): each thread owns the pairs of points
+// (i, i+1), i = i0 + 2 (lane + 32 v), v < kTileI / 64.  Staged column c holds point i = i0 - 2 + c, so every
+// pair starts at an even column and a stencil row needs two or three 8-byte shared loads per pair.
+constexpr int kPairW = kTileI + 4;                 // staged columns (1 .. kTileI + 2 used)
+constexpr int kPairSlot = kTileH * kPairW;
+
+__device__ __forceinline__ void p1_issue_plane_f32(float* slot, const float* __restrict__ xm,
+                                                   const int* __restrict__ pstart, int N, int i0, int j0, int kk) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = warp; r < kTileH; r += kTileJ) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = warp + kTileJ * h;
+    if (r >= kTileH) break;
     const int jr = j0 - 1 + r;
     const int len = N - jr - kk + 1;
     const bool rowok = jr >= 0 && kk >= 0 && kk <= N && len > 0;
-    const T* __restrict__ row = rowok ? xm + __ldg(pstart + kk) + row32(N - kk, jr) : xm;
-    for (int cidx = lane; cidx < kTileI + 2; cidx += 32) {
-      const int ii = i0 - 1 + cidx;
+    const float* __restrict__ row = rowok ? xm + __ldg(pstart + kk) + row32(N - kk, jr) : xm;
+#pragma unroll
+    for (int t = 0; t < (kTileI + 2 + 31) / 32; ++t) {
+      const int col = 1 + lane + 32 * t;
+      if (col > kTileI + 2) break;
+      const int ii = i0 - 2 + col;
       const bool ok = rowok && ii >= 0 && ii < len;
-      cp_async_zfill(&slot[r][cidx], ok ? row + ii : xm, (int)sizeof(T), ok);
+      cp_async_zfill(slot + r * kPairW + col, ok ? row + ii : xm, 4, ok);
     }
   }
 }
 
-// After plane kk has arrived: zero the Dirichlet points this thread staged.
-template <typename T>
-__device__ __forceinline__ void p1_mask_plane(T (*slot)[kTileW], int N, uint32_t table, int i0, int j0, int kk) {
+// After plane kk has arrived: zero the staged Dirichlet points.  Off the faces j = 0 and k = 0
+// only the two row ends i = 0 and i = len - 1 can be Dirichlet points; the thread that staged a
+// position zeroes it.
+__device__ __forceinline__ void p1_mask_plane_f32(float* slot, int N, uint32_t table, int i0, int j0, int kk) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = warp; r < kTileH; r += kTileJ) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = warp + kTileJ * h;
+    if (r >= kTileH) break;
     const int jr = j0 - 1 + r;
     const int len = N - jr - kk + 1;
     if (!(jr >= 0 && kk >= 0 && kk <= N && len > 0)) continue;
-    const bool rowface = (jr == 0) | (kk == 0);
-    for (int cidx = lane; cidx < kTileI + 2; cidx += 32) {
-      const int ii = i0 - 1 + cidx;
-      if (ii < 0 || ii >= len) continue;
-      if ((rowface || ii == 0 || ii == len - 1) && on_dirichlet(table, N, ii, jr, kk)) slot[r][cidx] = T(0);
+    if (jr == 0 || kk == 0) {
+#pragma unroll
+      for (int t = 0; t < (kTileI + 2 + 31) / 32; ++t) {
+        const int col = 1 + lane + 32 * t;
+        if (col > kTileI + 2) break;
+        const int ii = i0 - 2 + col;
+        if (ii >= 0 && ii < len && on_dirichlet(table, N, ii, jr, kk)) slot[r * kPairW + col] = 0.0f;
+      }
+    } else {
+      const int cand[2] = {2 - i0, len + 1 - i0};   // columns of i = 0 and i = len - 1
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int col = cand[e];
+        if (col >= 1 && col <= kTileI + 2 && ((col - 1) & 31) == lane) {
+          const int ii = i0 - 2 + col;
+          if (on_dirichlet(table, N, ii, jr, kk)) slot[r * kPairW + col] = 0.0f;
+        }
+      }
     }
   }
 }
 
-template <typename T, bool DIRICHLET>
-__global__ void __launch_bounds__(256) p1_tile_kernel(const OpConst<T>* __restrict__ cst,
-                                                       const int4* __restrict__ tasks, int kch,
-                                                       const int* __restrict__ pstart, const T* __restrict__ x,
-                                                       T* __restrict__ y) {
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float2 fma2(float w, float2 v, float2 acc) { return __ffma2_rn(make_float2(w, w), v, acc); }
+
+// Stencil of the point pair at even column b of staged row r (planes k-1, k, k+1).
+__device__ __forceinline__ float2 p1_pair_stencil(const float* W, const float* pm, const float* p0, const float* pp,
+                                                  int r, int b) {
+  const int o = r * kPairW + b;
+  // centre row: columns b-2 .. b+3
+  const float2 c0 = ld2(p0 + o - 2), c1 = ld2(p0 + o), c2 = ld2(p0 + o + 2);
+  float2 acc = make_float2(0.0f, 0.0f);
+  acc = fma2(W[0], c1, acc);                                  // (0,0,0)
+  acc = fma2(W[1], make_float2(c1.y, c2.x), acc);             // (1,0,0)
+  acc = fma2(W[2], make_float2(c0.y, c1.x), acc);             // (-1,0,0)
+  // rows needing i-1, i: (j+1,k) [3: (0,1,0), 8: (-1,1,0)], (j,k+1) [5, 10], (j+1,k-1) [11, 14]
+  {
+    const float2 a0 = ld2(p0 + o + kPairW - 2), a1 = ld2(p0 + o + kPairW);
+    acc = fma2(W[3], a1, acc);
+    acc = fma2(W[8], make_float2(a0.y, a1.x), acc);
+    const float2 b0 = ld2(pp + o - 2), b1 = ld2(pp + o);
+    acc = fma2(W[5], b1, acc);
+    acc = fma2(W[10], make_float2(b0.y, b1.x), acc);
+    const float2 d0 = ld2(pm + o + kPairW - 2), d1 = ld2(pm + o + kPairW);
+    acc = fma2(W[11], d1, acc);
+    acc = fma2(W[14], make_float2(d0.y, d1.x), acc);
+  }
+  // rows needing i, i+1: (j-1,k) [4: (0,-1,0), 7: (1,-1,0)], (j-1,k+1) [12, 13], (j,k-1) [6, 9]
+  {
+    const float2 a1 = ld2(p0 + o - kPairW), a2 = ld2(p0 + o - kPairW + 2);
+    acc = fma2(W[4], a1, acc);
+    acc = fma2(W[7], make_float2(a1.y, a2.x), acc);
+    const float2 b1 = ld2(pp + o - kPairW), b2 = ld2(pp + o - kPairW + 2);
+    acc = fma2(W[12], b1, acc);
+    acc = fma2(W[13], make_float2(b1.y, b2.x), acc);
+    const float2 d1 = ld2(pm + o), d2 = ld2(pm + o + 2);
+    acc = fma2(W[6], d1, acc);
+    acc = fma2(W[9], make_float2(d1.y, d2.x), acc);
+  }
+  return acc;
+}
+
+// Scalar stencil of the point at column cc (used next to the macro faces).
+__device__ __forceinline__ float p1_point_stencil(const float* W, const float* pm, const float* p0, const float* pp,
+                                                  int r, int cc) {
+  const int o = r * kPairW + cc;
+  return W[0] * p0[o] + W[1] * p0[o + 1] + W[2] * p0[o - 1] + W[3] * p0[o + kPairW] + W[4] * p0[o - kPairW] +
+         W[5] * pp[o] + W[6] * pm[o] + W[7] * p0[o - kPairW + 1] + W[8] * p0[o + kPairW - 1] + W[9] * pm[o + 1] +
+         W[10] * pp[o - 1] + W[11] * pm[o + kPairW] + W[12] * pp[o - kPairW] + W[13] * pp[o - kPairW + 1] +
+         W[14] * pm[o + kPairW - 1];
+}
+
+template <bool DIRICHLET>
+__global__ void __launch_bounds__(256, 3) p1_tile_f32_kernel(const OpConst<float>* __restrict__ cst,
+                                                              const int4* __restrict__ tasks, int kch,
+                                                              const int* __restrict__ pstart,
+                                                              const float* __restrict__ x, float* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char tile_smem[];
-  T (*buf)[kTileH][kTileW] = reinterpret_cast<T (*)[kTileH][kTileW]>(tile_smem);
+  float* buf = reinterpret_cast<float*>(tile_smem);
   const int4 task = tasks[blockIdx.x];
-  const OpConst<T>& c = cst[task.w];
+  const OpConst<float>& c = cst[task.w];
   const int N = c.N;
   const uint32_t table = c.bnd_table;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = task.x * kTileI, j0 = task.y * kTileJ, k0 = task.z * kch;
-  const int k_end = min(k0 + kch - 1, N - j0 - i0);   // last plane holding a point of the tile
+  const int k_end = min(k0 + kch - 1, N - j0 - i0);
   if (k_end < k0) return;
-  const T* __restrict__ xm = x + c.base;
-  T* __restrict__ ym = y + c.base;
-  T S[15];
+  const float* __restrict__ xm = x + c.base;
+  float* __restrict__ ym = y + c.base;
+  float S[15];
 #pragma unroll
   for (int d = 0; d < 15; ++d) S[d] = c.S[d];
   const int j = j0 + warp;
-  auto slot = [&](int kk) { return buf[(kk - k0 + 1) % kTileRing]; };   // kk >= k0 - 1
-  // prologue: planes k0-1 .. k0+kTileDepth-1, one commit group each
-  for (int kk = k0 - 1; kk < k0 + kTileDepth; ++kk) {
-    if (kk <= k_end + 1) p1_issue_plane<T>(slot(kk), xm, pstart, N, i0, j0, kk);
+  const int r = warp + 1;
+  for (int q = 0; q <= kTileDepth; ++q) {
+    const int kk = k0 - 1 + q;
+    if (kk <= k_end + 1) p1_issue_plane_f32(buf + q * kPairSlot, xm, pstart, N, i0, j0, kk);
     cp_async_commit();
   }
-  // planes k0-1 and k0 must be complete before the loop (the loop waits for k+1 only)
   cp_async_wait<kTileDepth - 1>();
   if (DIRICHLET) {
-    p1_mask_plane<T>(slot(k0 - 1), N, table, i0, j0, k0 - 1);
-    p1_mask_plane<T>(slot(k0), N, table, i0, j0, k0);
+    p1_mask_plane_f32(buf, N, table, i0, j0, k0 - 1);
+    p1_mask_plane_f32(buf + kPairSlot, N, table, i0, j0, k0);
   }
+  int sm = 0;
   for (int k = k0; k <= k_end; ++k) {
-    // plane k+1 has arrived once at most kTileDepth-1 later groups are pending
+    const int s0 = sm + 1 == kTileRing ? 0 : sm + 1;
+    const int sp = s0 + 1 == kTileRing ? 0 : s0 + 1;
     cp_async_wait<kTileDepth - 2>();
-    if (DIRICHLET) p1_mask_plane<T>(slot(k + 1), N, table, i0, j0, k + 1);
+    if (DIRICHLET) p1_mask_plane_f32(buf + sp * kPairSlot, N, table, i0, j0, k + 1);
     __syncthreads();
-    const T (*pm)[kTileW] = slot(k - 1);
-    const T (*p0)[kTileW] = slot(k);
-    const T (*pp)[kTileW] = slot(k + 1);
+    {
+      const int kn = k + kTileDepth;
+      int sn = sm + kTileDepth + 1;
+      if (sn >= kTileRing) sn -= kTileRing;
+      if (kn <= k_end + 1) p1_issue_plane_f32(buf + sn * kPairSlot, xm, pstart, N, i0, j0, kn);
+      cp_async_commit();
+    }
+    const float* pm = buf + sm * kPairSlot;
+    const float* p0 = buf + s0 * kPairSlot;
+    const float* pp = buf + sp * kPairSlot;
     const int len = N - j - k + 1;
-    const int r = warp + 1;                     // staged row of j
     if (len > 0) {
-      const int rowbase = __ldg(pstart + k) + row32(N - k, j);
+      float* __restrict__ yrow = ym + __ldg(pstart + k) + row32(N - k, j);
+      const bool rowface = (j == 0) | (k == 0);
 #pragma unroll
-      for (int v = 0; v < kStencilV; ++v) {
-        const int cc = lane + 32 * v + 1;       // staged column of i
-        const int ii = i0 + cc - 1;
+      for (int v = 0; v < kTileI / 64; ++v) {
+        const int p2 = lane + 32 * v;
+        const int ii = i0 + 2 * p2;
         if (ii >= len) continue;
-        const int z = (ii == len - 1) | ((ii == 0) << 1) | ((j == 0) << 2) | ((k == 0) << 3);
-        T acc;
-        if (z == 0) {
-          acc = S[0] * p0[r][cc] + S[1] * p0[r][cc + 1] + S[2] * p0[r][cc - 1] + S[3] * p0[r + 1][cc] +
-                S[4] * p0[r - 1][cc] + S[5] * pp[r][cc] + S[6] * pm[r][cc] + S[7] * p0[r - 1][cc + 1] +
-                S[8] * p0[r + 1][cc - 1] + S[9] * pm[r][cc + 1] + S[10] * pp[r][cc - 1] + S[11] * pm[r + 1][cc] +
-                S[12] * pp[r - 1][cc] + S[13] * pp[r - 1][cc + 1] + S[14] * pm[r + 1][cc - 1];
-        } else if (DIRICHLET && ((table >> z) & 1u)) {
-          acc = __ldg(xm + rowbase + ii);
-        } else if (__popc(z) == 1) {
-          const T* Sf = c.Sface[__ffs(z) - 1];
-          acc = Sf[0] * p0[r][cc] + Sf[1] * p0[r][cc + 1] + Sf[2] * p0[r][cc - 1] + Sf[3] * p0[r + 1][cc] +
-                Sf[4] * p0[r - 1][cc] + Sf[5] * pp[r][cc] + Sf[6] * pm[r][cc] + Sf[7] * p0[r - 1][cc + 1] +
-                Sf[8] * p0[r + 1][cc - 1] + Sf[9] * pm[r][cc + 1] + Sf[10] * pp[r][cc - 1] +
-                Sf[11] * pm[r + 1][cc] + Sf[12] * pp[r - 1][cc] + Sf[13] * pp[r - 1][cc + 1] +
-                Sf[14] * pm[r + 1][cc - 1];
-        } else {
-          acc = p1_face_point<T, DIRICHLET>(c, pstart, xm, ii, j, k);
+        // packed stencil of the pair; points on a macro face are patched below
+        const float2 acc = rowface ? make_float2(0.0f, 0.0f) : p1_pair_stencil(S, pm, p0, pp, r, 2 * p2 + 2);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int ie = ii + e;
+          if (ie >= len) break;
+          float val = e == 0 ? acc.x : acc.y;
+          const int z = (ie == len - 1) | ((ie == 0) << 1) | ((j == 0) << 2) | ((k == 0) << 3);
+          if (z != 0) {
+            const int cc = 2 * p2 + 2 + e;
+            if (DIRICHLET && ((table >> z) & 1u))
+              val = __ldg(xm + (yrow - ym) + ie);
+            else if (__popc(z) == 1)
+              val = p1_point_stencil(c.Sface[__ffs(z) - 1], pm, p0, pp, r, cc);
+            else
+              val = p1_face_point<float, DIRICHLET>(c, pstart, xm, ie, j, k);
+          }
+          yrow[ie] = val;
         }
-        ym[rowbase + ii] = acc;
       }
     }
-    __syncthreads();   // every thread is done with plane k-1: its slot takes plane k+kTileDepth
-    const int kn = k + kTileDepth;
-    if (kn <= k_end + 1) p1_issue_plane<T>(slot(kn), xm, pstart, N, i0, j0, kn);
-    cp_async_commit();
+    sm = s0;
   }
   cp_async_wait<0>();
 }
 
-template <typename T>
-constexpr size_t p1_tile_smem() {
-  return sizeof(T) * kTileRing * kTileH * kTileW;
-}
+constexpr size_t p1_tile_f32_smem() { return sizeof(float) * kTileRing * kPairSlot; }
 
 // diag(A) for the constant-coefficient operators: sum of A_T[a][a] over the incident micro-tets.
 template <typename T>
@@ -759,6 +712,32 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int nb, 
   if (threadIdx.x == 0) out[0] = red[0];
 }
 
+// Edge DoFs of the Nedelec operator: copies are related by orientation signs.
+template <typename T>
+__global__ void iface_sum_signed_kernel(const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
+                                        const int8_t* __restrict__ sgn, const uint8_t* __restrict__ bnd,
+                                        int64_t ngroups, bool dirichlet, T* __restrict__ y) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ngroups) return;
+  if (dirichlet && bnd[g]) return;
+  const int64_t a = ptr[g], b = ptr[g + 1];
+  T s = T(0);
+  for (int64_t t = a; t < b; ++t) s += T(sgn[t]) * y[idx[t]];
+  for (int64_t t = a; t < b; ++t) y[idx[t]] = T(sgn[t]) * s;
+}
+
+template <typename T>
+int launch_interface_sum_signed(const Interface* itf, T* y, bool dirichlet, cudaStream_t s) {
+  if (itf->ngroups == 0) return HHG_OK;
+  const int th = 128;
+  iface_sum_signed_kernel<T><<<(unsigned)((itf->ngroups + th - 1) / th), th, 0, s>>>(
+      itf->d_ptr, itf->d_idx, itf->d_sign, itf->d_bnd, itf->ngroups, dirichlet, y);
+  HHG_CUDA_TRY(cudaGetLastError());
+  return HHG_OK;
+}
+template int launch_interface_sum_signed<double>(const Interface*, double*, bool, cudaStream_t);
+template int launch_interface_sum_signed<float>(const Interface*, float*, bool, cudaStream_t);
+
 template int launch_interface_sum<double>(const Interface*, double*, int, bool, cudaStream_t);
 template int launch_interface_sum<float>(const Interface*, float*, int, bool, cudaStream_t);
 template int launch_make_consistent<double>(const Interface*, double*, int, cudaStream_t);
@@ -816,13 +795,14 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
       return HHG_OK;
     }
     const unsigned grid = (unsigned)I->n_stencil_tasks;
-    const size_t smem = p1_tile_smem<T>();
+    const size_t smem = p1_tile_f32_smem();
+    const OpConst<float>* cf = (const OpConst<float>*)op->d_const32;
     if (op->bc == HHG_DIRICHLET)
-      p1_tile_kernel<T, true><<<grid, 256, smem, s>>>(dconst<T>(op), I->d_stencil_tasks, I->stencil_kchunk,
-                                                      I->d_pstart, x, y);
+      p1_tile_f32_kernel<true><<<grid, 256, smem, s>>>(cf, I->d_stencil_tasks, I->stencil_kchunk, I->d_pstart,
+                                                       (const float*)x, (float*)y);
     else
-      p1_tile_kernel<T, false><<<grid, 256, smem, s>>>(dconst<T>(op), I->d_stencil_tasks, I->stencil_kchunk,
-                                                       I->d_pstart, x, y);
+      p1_tile_f32_kernel<false><<<grid, 256, smem, s>>>(cf, I->d_stencil_tasks, I->stencil_kchunk, I->d_pstart,
+                                                        (const float*)x, (float*)y);
     HHG_CUDA_TRY(cudaGetLastError());
     return HHG_OK;
   }
@@ -853,6 +833,8 @@ hhg_op::~hhg_op() {
   if (work) hhg::destroy_work(work);
   cudaFree(d_const64);
   cudaFree(d_const32);
+  cudaFree(d_n1_64);
+  cudaFree(d_n1_32);
 }
 
 static int check_dtype(int dtype) {
@@ -860,11 +842,16 @@ static int check_dtype(int dtype) {
   return HHG_OK;
 }
 
+static int check_one_field(const hhg_coeff_t& c, int dtype) {
+  if (c.type != HHG_COEFF_FIELD_P1 && c.type != HHG_COEFF_FIELD_P2) return HHG_OK;
+  if (!c.field) return fail(HHG_E_ARG, "coefficient field pointer is null");
+  if (c.field_dtype != dtype)
+    return fail(HHG_E_ARG, "coefficient field dtype %d differs from the apply dtype %d", c.field_dtype, dtype);
+  return HHG_OK;
+}
 static int check_field(const hhg_op* op, int dtype) {
-  if (op->coeff.type != HHG_COEFF_FIELD_P1 && op->coeff.type != HHG_COEFF_FIELD_P2) return HHG_OK;
-  if (!op->coeff.field) return fail(HHG_E_ARG, "coefficient field pointer is null");
-  if (op->coeff.field_dtype != dtype)
-    return fail(HHG_E_ARG, "coefficient field dtype %d differs from the apply dtype %d", op->coeff.field_dtype, dtype);
+  HHG_TRY(check_one_field(op->coeff, dtype));
+  if (op->kind == HHG_CURLCURL) HHG_TRY(check_one_field(op->coeff2, dtype));
   return HHG_OK;
 }
 
@@ -942,6 +929,17 @@ extern "C" int hhg_op_apply(hhg_op_t* op, const void* x, void* y, int dtype, int
   cudaStream_t s = (cudaStream_t)stream;
   const Interface* itf = nullptr;
   HHG_TRY(op->mesh->interface(op->level, op->degree, &itf));
+  if (op->kind == HHG_CURLCURL) {
+    if (nrhs != 1) return fail(HHG_E_ARG, "op_apply: the curl-curl operator takes nrhs = 1");
+    if (dtype == HHG_F64) {
+      HHG_TRY(launch_n1<double>(op, (const double*)x, (double*)y, s));
+      HHG_TRY(launch_interface_sum_signed<double>(itf, (double*)y, op->bc == HHG_DIRICHLET, s));
+    } else {
+      HHG_TRY(launch_n1<float>(op, (const float*)x, (float*)y, s));
+      HHG_TRY(launch_interface_sum_signed<float>(itf, (float*)y, op->bc == HHG_DIRICHLET, s));
+    }
+    return HHG_OK;
+  }
   if (op->kind == HHG_EPSILON) {
     const int pp = 3 * nrhs;
     if (dtype == HHG_F64) {
@@ -1084,5 +1082,134 @@ extern "C" int hhg_op_apply_adjoint_coeff(hhg_op_t* op, const void* u, const voi
                                 (float*)dk, s));
     HHG_TRY(launch_interface_sum<float>(itf, (float*)dk, 1, false, s));
   }
+  return HHG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Nedelec curl-curl + mass operator (Eq. N1): hoisted per-class edge matrices
+// ---------------------------------------------------------------------------
+namespace hhg {
+// int_T lambda^m = |T| 3! prod(m_a!) / (|m| + 3)!, here |m| = 3: |T| 6 prod(m_a!) / 720
+static double tri_int(int x, int y, int z, double vol) {
+  int m[4] = {0, 0, 0, 0};
+  m[x]++;
+  m[y]++;
+  m[z]++;
+  double num = 1.0;
+  for (int a = 0; a < 4; ++a)
+    for (int t = 2; t <= m[a]; ++t) num *= t;
+  return vol * 6.0 * num / 720.0;
+}
+
+static void build_n1(hhg_op* op, std::vector<N1Const<double>>& out) {
+  const hhg_mesh* mesh = op->mesh;
+  out.assign(mesh->nmacro(), N1Const<double>{});
+  for (int m = 0; m < mesh->nmacro(); ++m) {
+    N1Const<double>& q = out[m];
+    std::memset(&q, 0, sizeof(q));
+    q.vbase = (int64_t)m * lattice_size(op->n);
+    const OpConst<double>& c = op->h_const[m];
+    for (int o = 0; o < 6; ++o) {
+      // grad lambda_a = J^{-T} grad_ref lambda_a
+      const double gl[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+      double G[4][3];
+      for (int a = 0; a < 4; ++a)
+        for (int d = 0; d < 3; ++d) {
+          double s = 0;
+          for (int e = 0; e < 3; ++e) s += c.Jinv[o][e * 3 + d] * gl[a][e];
+          G[a][d] = s;
+        }
+      const double vol = c.adet[o] / 6.0;
+      double cu[6][3];
+      for (int e = 0; e < 6; ++e) {
+        const int a = kP2Edges[e][0], b = kP2Edges[e][1];
+        cu[e][0] = 2.0 * (G[a][1] * G[b][2] - G[a][2] * G[b][1]);
+        cu[e][1] = 2.0 * (G[a][2] * G[b][0] - G[a][0] * G[b][2]);
+        cu[e][2] = 2.0 * (G[a][0] * G[b][1] - G[a][1] * G[b][0]);
+        // orientation of local edge a -> b against the canonical lattice direction of its midpoint
+        int vec[3], par[3];
+        for (int d = 0; d < 3; ++d) {
+          vec[d] = kClassOffsets[o][b][d] - kClassOffsets[o][a][d];
+          par[d] = (kClassOffsets[o][a][d] + kClassOffsets[o][b][d]) & 1;
+        }
+        int can[3] = {par[0], par[1], par[2]};
+        if (par[0] && par[1] && !par[2]) can[1] = -1;
+        if (par[0] && !par[1] && par[2]) can[2] = -1;
+        if (!par[0] && par[1] && par[2]) can[2] = -1;
+        if (par[0] && par[1] && par[2]) can[1] = -1;
+        q.sgn[o][e] = (vec[0] == can[0] && vec[1] == can[1] && vec[2] == can[2]) ? 1.0 : -1.0;
+      }
+      auto dot = [](const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; };
+      for (int e = 0; e < 6; ++e)
+        for (int f = 0; f < 6; ++f) {
+          q.C[o][e][f] = vol * dot(cu[e], cu[f]);
+          const int a = kP2Edges[e][0], b = kP2Edges[e][1], cc = kP2Edges[f][0], dd = kP2Edges[f][1];
+          for (int v = 0; v < 4; ++v)
+            q.M[o][v][e][f] = tri_int(v, a, cc, vol) * dot(G[b], G[dd]) - tri_int(v, a, dd, vol) * dot(G[b], G[cc]) -
+                              tri_int(v, b, cc, vol) * dot(G[a], G[dd]) + tri_int(v, b, dd, vol) * dot(G[a], G[cc]);
+        }
+    }
+  }
+}
+}  // namespace hhg
+
+extern "C" int hhg_op_create_curlcurl(hhg_mesh_t* mesh, int level, const hhg_coeff_t* alpha, const hhg_coeff_t* beta,
+                                      int bc, hhg_op_t** out) {
+  clear_error();
+  if (!mesh || !alpha || !beta || !out) return fail(HHG_E_ARG, "op_create_curlcurl: null pointer");
+  *out = nullptr;
+  if (level < 0) level = mesh->level;
+  if (level > mesh->level) return fail(HHG_E_ARG, "op_create_curlcurl: level %d above the mesh's %d", level, mesh->level);
+  if (bc != HHG_DIRICHLET && bc != HHG_NEUMANN) return fail(HHG_E_ARG, "op_create_curlcurl: unknown boundary mode");
+  for (const hhg_coeff_t* c : {alpha, beta})
+    if (c->type != HHG_COEFF_CONST && c->type != HHG_COEFF_FIELD_P1)
+      return fail(HHG_E_UNSUPPORTED, "op_create_curlcurl: alpha and beta must be CONST or FIELD_P1");
+  std::unique_ptr<hhg_op> op(new hhg_op());
+  op->mesh = mesh;
+  op->level = level;
+  op->kind = HHG_CURLCURL;
+  op->degree = 2;   // edge DoFs live in the doubled lattice
+  op->bc = bc;
+  op->quad_degree = 2;
+  op->coeff = *alpha;
+  op->coeff2 = *beta;
+  op->n = 1 << level;
+  op->N = 2 << level;
+  op->npts = (int64_t)mesh->nmacro() * lattice_size(op->N);
+  HHG_TRY(quad_rule(2, &op->rule));
+  const Interface* itf1 = nullptr;
+  HHG_TRY(mesh->interface(level, 1, &itf1));
+  HHG_TRY(mesh->interface(level, 2, &op->itf));
+  hhg_coeff_t cc{HHG_COEFF_CONST, 1.0, nullptr, HHG_F64};
+  op->coeff = cc;   // geometry tables only
+  build_const(op.get());
+  op->coeff = *alpha;
+  std::vector<N1Const<double>> n64;
+  build_n1(op.get(), n64);
+  const int nm = mesh->nmacro();
+  std::vector<N1Const<float>> n32(nm);
+  for (int m = 0; m < nm; ++m) {
+    std::memset(&n32[m], 0, sizeof(N1Const<float>));
+    n32[m].vbase = n64[m].vbase;
+    for (int o = 0; o < 6; ++o)
+      for (int e = 0; e < 6; ++e) {
+        n32[m].sgn[o][e] = (float)n64[m].sgn[o][e];
+        for (int f = 0; f < 6; ++f) {
+          n32[m].C[o][e][f] = (float)n64[m].C[o][e][f];
+          for (int v = 0; v < 4; ++v) n32[m].M[o][v][e][f] = (float)n64[m].M[o][v][e][f];
+        }
+      }
+  }
+  std::vector<OpConst<float>> c32(nm);
+  for (int m = 0; m < nm; ++m) c32[m] = convert_const<float>(op->h_const[m]);
+  HHG_CUDA_TRY(cudaMalloc(&op->d_const64, sizeof(OpConst<double>) * nm));
+  HHG_CUDA_TRY(cudaMalloc(&op->d_const32, sizeof(OpConst<float>) * nm));
+  HHG_CUDA_TRY(cudaMalloc(&op->d_n1_64, sizeof(N1Const<double>) * nm));
+  HHG_CUDA_TRY(cudaMalloc(&op->d_n1_32, sizeof(N1Const<float>) * nm));
+  HHG_CUDA_TRY(cudaMemcpy(op->d_const64, op->h_const.data(), sizeof(OpConst<double>) * nm, cudaMemcpyHostToDevice));
+  HHG_CUDA_TRY(cudaMemcpy(op->d_const32, c32.data(), sizeof(OpConst<float>) * nm, cudaMemcpyHostToDevice));
+  HHG_CUDA_TRY(cudaMemcpy(op->d_n1_64, n64.data(), sizeof(N1Const<double>) * nm, cudaMemcpyHostToDevice));
+  HHG_CUDA_TRY(cudaMemcpy(op->d_n1_32, n32.data(), sizeof(N1Const<float>) * nm, cudaMemcpyHostToDevice));
+  *out = op.release();
   return HHG_OK;
 }

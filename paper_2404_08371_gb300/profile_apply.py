@@ -43,7 +43,9 @@ def main():
     dt = torch.float64 if args.dtype == "f64" else torch.float32
     qd = args.quad or (2 if args.degree == 1 else 4)
     field = None
-    if args.coeff == "const":
+    if args.kind == "curlcurl":
+        coeff = None
+    elif args.coeff == "const":
         coeff = ("const", 1.0)
     elif args.coeff == "sin3":
         coeff = ("sin3",)
@@ -52,7 +54,18 @@ def main():
         field = torch.from_numpy(1.0 + 0.5 * W.uniform(mesh.vec_size(kdeg), seed=7)).to("cuda", dt)
         mesh.make_consistent(field, kdeg)
         coeff = (args.coeff, field)
-    op = hhg.Operator(mesh, kind=args.kind, degree=args.degree, coeff=coeff, bc=args.bc, quad_degree=qd)
+    if args.kind == "curlcurl":
+        if args.coeff == "field_p1":
+            a = torch.from_numpy(1.0 + 0.5 * W.uniform(mesh.vec_size(1), seed=8)).to("cuda", dt)
+            b = torch.from_numpy(1.0 + 0.5 * W.uniform(mesh.vec_size(1), seed=9)).to("cuda", dt)
+            mesh.make_consistent(a, 1)
+            mesh.make_consistent(b, 1)
+            op = hhg.CurlCurl(mesh, ("field_p1", a), ("field_p1", b), bc=args.bc)
+        else:
+            op = hhg.CurlCurl(mesh, ("const", 1.0), ("const", 1.0), bc=args.bc)
+        args.degree = 2
+    else:
+        op = hhg.Operator(mesh, kind=args.kind, degree=args.degree, coeff=coeff, bc=args.bc, quad_degree=qd)
     ncomp = 3 if args.kind == "epsilon" else 1
     n = mesh.vec_size(args.degree) * ncomp * args.nrhs
     x = torch.from_numpy(W.uniform(n, seed=0)).to("cuda", dt)
