@@ -180,15 +180,17 @@ int launch_l2_error(const struct ::hhg_op* op, const double* uh, double* partial
 }  // namespace hhg
 
 namespace hhg {
-// Hoisted per-class data of the Nedelec operator (one block per macro):
-//   C[o][e][f] = |T| curl phi_e . curl phi_f   (curl phi_e = 2 grad l_a x grad l_b, constant)
-//   M[o][v][e][f] = int_T lambda_v phi_e . phi_f  (exact)
-//   sgn[o][e] = +1 if local edge e (a -> b) runs along the canonical lattice direction, else -1
+// Hoisted per-class data of the Nedelec operator (one block per macro), in the macro's canonical
+// edge orientation (the local orientation a -> b times s_e = +-1, folded into the entries) and
+// stored as the upper triangle e <= f (index n1_sym(e, f)):
+//   C[o][.] = s_e s_f |T| curl phi_e . curl phi_f   (curl phi_e = 2 grad l_a x grad l_b, constant)
+//   M[o][v][.] = s_e s_f int_T lambda_v phi_e . phi_f  (exact)
+constexpr int kN1Sym = 21;
+__host__ __device__ constexpr int n1_sym(int e, int f) { return e * 6 - e * (e - 1) / 2 + (f - e); }
 template <typename T>
 struct alignas(16) N1Const {
-  T C[6][6][6];
-  T M[6][4][6][6];
-  T sgn[6][6];
+  T C[6][kN1Sym];
+  T M[6][4][kN1Sym];
   int64_t vbase;     // offset of the macro in a packed P1 vector (coefficient fields)
 };
 }  // namespace hhg

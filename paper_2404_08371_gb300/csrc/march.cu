@@ -206,6 +206,18 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
             if (MODE == MODE_ADJ) gb[s] = live ? __ldg(g + base + idx) : T(0);
             if (COEF == HHG_COEFF_FIELD_P1 || COEF == HHG_COEFF_FIELD_P2) kb[s] = in ? __ldg(kf + c.kbase + idx) : T(0);
           }
+      // Nedelec coefficients: P1 alpha / beta at the eight cube corners (inside the macro)
+      T ca[MODE == MODE_N1 ? 8 : 1], cb[MODE == MODE_N1 ? 8 : 1];
+      if constexpr (MODE == MODE_N1) {
+#pragma unroll
+        for (int cn = 0; cn < 8; ++cn) {
+          const int vi = ci + (cn & 1), vj = cj + ((cn >> 1) & 1), vk = ck + (cn >> 2);
+          const bool in = vi + vj + vk <= n1a.n;
+          const int64_t vidx = n1c.vbase + (in ? packed_index(n1a.n, vi, vj, vk) : 0);
+          ca[cn] = n1a.alpha ? (in ? __ldg(n1a.alpha + vidx) : T(0)) : n1a.alpha_c;
+          cb[cn] = n1a.beta ? (in ? __ldg(n1a.beta + vidx) : T(0)) : n1a.beta_c;
+        }
+      }
       // analytic coefficient in FP32: sin / cos of 2 pi x at the cube origin, per coordinate
       if (COEF == HHG_COEFF_SIN3 && !kRotate) {
 #pragma unroll
@@ -224,38 +236,30 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
           yl[a] = T(0);
         }
         if constexpr (MODE == MODE_N1) {
-          // Nedelec edge element (Eq. N1): the six edge nodes of the P2 numbering carry the DoFs
+          // Nedelec edge element (Eq. N1): the six edge nodes of the P2 numbering carry the DoFs.
+          // A_T = mean(alpha) C_o + sum_v beta_v M_o^v (symmetric, canonical orientation), formed
+          // once per micro-tet and applied to the six edge values.
           if constexpr (R == 2) {
-            const int nn = n1a.n;
             T av[4], bv[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-              const int vi = ci + coff(o, v, 0), vj = cj + coff(o, v, 1), vk = ck + coff(o, v, 2);
-              const int64_t vidx = n1c.vbase + packed_index(nn, vi, vj, vk);
-              av[v] = n1a.alpha ? __ldg(n1a.alpha + vidx) : n1a.alpha_c;
-              bv[v] = n1a.beta ? __ldg(n1a.beta + vidx) : n1a.beta_c;
+              const int cn = coff(o, v, 0) + 2 * coff(o, v, 1) + 4 * coff(o, v, 2);
+              av[v] = ca[cn];
+              bv[v] = cb[cn];
             }
             const T abar = T(0.25) * (av[0] + av[1] + av[2] + av[3]);
-            T ue[6], ye[6];
+            T A[kN1Sym];
+#pragma unroll
+            for (int t = 0; t < kN1Sym; ++t)
+              A[t] = abar * n1c.C[o][t] + bv[0] * n1c.M[o][0][t] + bv[1] * n1c.M[o][1][t] +
+                     bv[2] * n1c.M[o][2][t] + bv[3] * n1c.M[o][3][t];
 #pragma unroll
             for (int e = 0; e < 6; ++e) {
-              ue[e] = n1c.sgn[o][e] * ul[4 + e];
-              ye[e] = T(0);
+              T s = T(0);
+#pragma unroll
+              for (int f = 0; f < 6; ++f) s += A[e <= f ? n1_sym(e, f) : n1_sym(f, e)] * ul[4 + f];
+              yl[4 + e] = s;
             }
-#pragma unroll
-            for (int e = 0; e < 6; ++e) {
-              T sc = T(0), sm = T(0);
-#pragma unroll
-              for (int f = 0; f < 6; ++f) {
-                sc += n1c.C[o][e][f] * ue[f];
-                const T mb = bv[0] * n1c.M[o][0][e][f] + bv[1] * n1c.M[o][1][e][f] + bv[2] * n1c.M[o][2][e][f] +
-                             bv[3] * n1c.M[o][3][e][f];
-                sm += mb * ue[f];
-              }
-              ye[e] = abar * sc + sm;
-            }
-#pragma unroll
-            for (int e = 0; e < 6; ++e) yl[4 + e] = n1c.sgn[o][e] * ye[e];
           }
         } else if (MODE == MODE_RHS) {
           // b_a += sum_q w_q |det J| f(x_q) phi_a(xi_q), f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)

@@ -1120,7 +1120,7 @@ static void build_n1(hhg_op* op, std::vector<N1Const<double>>& out) {
           G[a][d] = s;
         }
       const double vol = c.adet[o] / 6.0;
-      double cu[6][3];
+      double cu[6][3], sg[6];
       for (int e = 0; e < 6; ++e) {
         const int a = kP2Edges[e][0], b = kP2Edges[e][1];
         cu[e][0] = 2.0 * (G[a][1] * G[b][2] - G[a][2] * G[b][1]);
@@ -1137,16 +1137,18 @@ static void build_n1(hhg_op* op, std::vector<N1Const<double>>& out) {
         if (par[0] && !par[1] && par[2]) can[2] = -1;
         if (!par[0] && par[1] && par[2]) can[2] = -1;
         if (par[0] && par[1] && par[2]) can[1] = -1;
-        q.sgn[o][e] = (vec[0] == can[0] && vec[1] == can[1] && vec[2] == can[2]) ? 1.0 : -1.0;
+        sg[e] = (vec[0] == can[0] && vec[1] == can[1] && vec[2] == can[2]) ? 1.0 : -1.0;
       }
       auto dot = [](const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; };
       for (int e = 0; e < 6; ++e)
-        for (int f = 0; f < 6; ++f) {
-          q.C[o][e][f] = vol * dot(cu[e], cu[f]);
+        for (int f = e; f < 6; ++f) {
+          const double s = sg[e] * sg[f];
+          q.C[o][n1_sym(e, f)] = s * vol * dot(cu[e], cu[f]);
           const int a = kP2Edges[e][0], b = kP2Edges[e][1], cc = kP2Edges[f][0], dd = kP2Edges[f][1];
           for (int v = 0; v < 4; ++v)
-            q.M[o][v][e][f] = tri_int(v, a, cc, vol) * dot(G[b], G[dd]) - tri_int(v, a, dd, vol) * dot(G[b], G[cc]) -
-                              tri_int(v, b, cc, vol) * dot(G[a], G[dd]) + tri_int(v, b, dd, vol) * dot(G[a], G[cc]);
+            q.M[o][v][n1_sym(e, f)] =
+                s * (tri_int(v, a, cc, vol) * dot(G[b], G[dd]) - tri_int(v, a, dd, vol) * dot(G[b], G[cc]) -
+                     tri_int(v, b, cc, vol) * dot(G[a], G[dd]) + tri_int(v, b, dd, vol) * dot(G[a], G[cc]));
         }
     }
   }
@@ -1192,12 +1194,9 @@ extern "C" int hhg_op_create_curlcurl(hhg_mesh_t* mesh, int level, const hhg_coe
     std::memset(&n32[m], 0, sizeof(N1Const<float>));
     n32[m].vbase = n64[m].vbase;
     for (int o = 0; o < 6; ++o)
-      for (int e = 0; e < 6; ++e) {
-        n32[m].sgn[o][e] = (float)n64[m].sgn[o][e];
-        for (int f = 0; f < 6; ++f) {
-          n32[m].C[o][e][f] = (float)n64[m].C[o][e][f];
-          for (int v = 0; v < 4; ++v) n32[m].M[o][v][e][f] = (float)n64[m].M[o][v][e][f];
-        }
+      for (int t = 0; t < kN1Sym; ++t) {
+        n32[m].C[o][t] = (float)n64[m].C[o][t];
+        for (int v = 0; v < 4; ++v) n32[m].M[o][v][t] = (float)n64[m].M[o][v][t];
       }
   }
   std::vector<OpConst<float>> c32(nm);
