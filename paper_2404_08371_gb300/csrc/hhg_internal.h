@@ -185,6 +185,21 @@ namespace hhg {
 // stored as the upper triangle e <= f (index n1_sym(e, f)):
 //   C[o][.] = s_e s_f |T| curl phi_e . curl phi_f   (curl phi_e = 2 grad l_a x grad l_b, constant)
 //   M[o][v][.] = s_e s_f int_T lambda_v phi_e . phi_f  (exact)
+// P2 constant-coefficient stencils: the row of a point of the doubled lattice is fixed by the
+// parity (I & 1, J & 1, K & 1) of its coordinates and by the macro faces it lies on (zero mask z).
+// The 8 parities have 65, 27, 19, 27, 27, 19, 27, 19 structural neighbours (230 in all); entry d of
+// parity p (start[p] <= d < start[p + 1]) is the offset off[d] (packed (dx+2) | (dy+2) << 4 |
+// (dz+2) << 8) with weight w[z][d] (zero for neighbours outside the macro).
+constexpr int kP2StTotal = 230;
+struct P2StencilIndex {
+  int start[9];
+  int off[kP2StTotal];
+};
+template <typename T>
+struct alignas(16) P2Stencil {
+  T w[16][kP2StTotal];
+};
+
 constexpr int kN1Sym = 21;
 __host__ __device__ constexpr int n1_sym(int e, int f) { return e * 6 - e * (e - 1) / 2 + (f - e); }
 template <typename T>
@@ -200,6 +215,9 @@ struct hhg_op {
   int level = 0, kind = 0, degree = 1, bc = 0, quad_degree = 2;
   hhg_coeff_t coeff{};
   hhg_coeff_t coeff2{};      // second coefficient (beta of the Nedelec operator)
+  void* d_p2st64 = nullptr;  // P2Stencil<double>[nmacro] (P2 constant-coefficient diffusion)
+  void* d_p2st32 = nullptr;
+  void* d_p2idx = nullptr;   // P2StencilIndex
   void* d_n1_64 = nullptr;   // N1Const<double>[nmacro]
   void* d_n1_32 = nullptr;
   int N = 0, n = 0;

@@ -10,6 +10,9 @@
 // explicit validity test of each incident micro-tet.  The apply gathers into
 // each output point (no atomics); every point is written by exactly one thread.
 #include <algorithm>
+#include <array>
+#include <tuple>
+#include <utility>
 #include <cmath>
 #include <cstring>
 
@@ -357,6 +360,168 @@ __global__ void __launch_bounds__(256) p1_gather_kernel(const OpConst<T>* __rest
       // on a macro edge or vertex: sum the incident micro-tets that exist
       acc = p1_face_point<T, DIRICHLET>(c, pstart, xm, i, j, k);
     }
+  }
+  ym[p] = acc;
+}
+
+
+// Structural P2 stencil lists, rebuilt at compile time in the order of the host table (ascending
+// packed offset = by dz, then dy, then dx), so that interior rows unroll with constant offsets.
+__host__ __device__ constexpr int p2c_off(int o, int v, int d) {
+  constexpr int t[6][4][3] = {
+      {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, {{0, 1, 0}, {1, 0, 1}, {1, 0, 0}, {1, 1, 0}},
+      {{0, 1, 0}, {1, 0, 1}, {1, 1, 0}, {0, 1, 1}}, {{0, 1, 0}, {1, 0, 1}, {0, 1, 1}, {0, 0, 1}},
+      {{0, 1, 0}, {1, 0, 1}, {0, 0, 1}, {1, 0, 0}}, {{1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}}};
+  return t[o][v][d];
+}
+__host__ __device__ constexpr int p2c_node(int o, int a, int d) {
+  constexpr int e[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+  return a < 4 ? 2 * p2c_off(o, a, d) : p2c_off(o, e[a - 4][0], d) + p2c_off(o, e[a - 4][1], d);
+}
+struct P2OffList {
+  int n;
+  int off[65];
+};
+__host__ __device__ constexpr P2OffList p2_struct_list(int par) {
+  P2OffList L{};
+  for (int o = 0; o < 6; ++o)
+    for (int a = 0; a < 10; ++a) {
+      const int pa = (p2c_node(o, a, 0) & 1) | ((p2c_node(o, a, 1) & 1) << 1) | ((p2c_node(o, a, 2) & 1) << 2);
+      if (pa != par) continue;
+      for (int b = 0; b < 10; ++b) {
+        const int v = (p2c_node(o, b, 0) - p2c_node(o, a, 0) + 2) | ((p2c_node(o, b, 1) - p2c_node(o, a, 1) + 2) << 4) |
+                      ((p2c_node(o, b, 2) - p2c_node(o, a, 2) + 2) << 8);
+        int pos = 0;
+        while (pos < L.n && L.off[pos] < v) ++pos;
+        if (pos < L.n && L.off[pos] == v) continue;
+        for (int t = L.n; t > pos; --t) L.off[t] = L.off[t - 1];
+        L.off[pos] = v;
+        ++L.n;
+      }
+    }
+  return L;
+}
+template <int PAR>
+struct P2Cnt {
+  static constexpr int v = p2_struct_list(PAR).n;
+};
+template <int PAR>
+struct P2Start {
+  static constexpr int v = P2Start<PAR - 1>::v + P2Cnt<PAR - 1>::v;
+};
+template <>
+struct P2Start<0> {
+  static constexpr int v = 0;
+};
+template <int PAR, int D>
+struct P2Off {
+  static constexpr int v = p2_struct_list(PAR).off[D];
+};
+static_assert(P2Start<7>::v + P2Cnt<7>::v == kP2StTotal, "P2 structural stencil size");
+
+template <typename T, int O>
+__device__ __forceinline__ T p2_ld(const T* __restrict__ xm, const int (&ps)[5], int N, int i, int j, int k) {
+  constexpr int dx = (O & 15) - 2, dy = ((O >> 4) & 15) - 2, dz = ((O >> 8) & 15) - 2;
+  return __ldg(xm + ps[dz + 2] + row32(N - (k + dz), j + dy) + i + dx);
+}
+
+// Interior row of parity PAR: all loads issued first, then the weighted sum.
+template <typename T, int PAR, int... D>
+__device__ __forceinline__ T p2_row_fast(const T* __restrict__ w, const T* __restrict__ xm, const int (&ps)[5], int N,
+                                         int i, int j, int k, std::integer_sequence<int, D...>) {
+  const T v[] = {p2_ld<T, P2Off<PAR, D>::v>(xm, ps, N, i, j, k)...};
+  T acc = T(0);
+#pragma unroll
+  for (int t = 0; t < (int)sizeof...(D); ++t) acc += w[P2Start<PAR>::v + t] * v[t];
+  return acc;
+}
+
+template <typename T, int PAR>
+__device__ __forceinline__ T p2_row(const T* __restrict__ w, const T* __restrict__ xm, const int (&ps)[5], int N, int i,
+                                    int j, int k) {
+  return p2_row_fast<T, PAR>(w, xm, ps, N, i, j, k, std::make_integer_sequence<int, P2Cnt<PAR>::v>{});
+}
+
+// P2 constant-coefficient apply, one thread per output point of the doubled lattice (gather).
+// The row of a point is the stencil of its parity class and zero mask, assembled on the host from
+// the hoisted class matrices; interior rows come from shared memory, rows of points on macro faces
+// from the per-macro table.  Threads 0..127 take the even, 128..255 the odd positions of the CTA's
+// 256 consecutive points, so a warp mostly holds points of one parity and runs one stencil.
+template <typename T, bool DIRICHLET>
+__global__ void __launch_bounds__(256) p2_stencil_kernel(const OpConst<T>* __restrict__ cst,
+                                                         const P2Stencil<T>* __restrict__ st,
+                                                         const P2StencilIndex* __restrict__ sidx,
+                                                         const int* __restrict__ cta_plane,
+                                                         const int* __restrict__ cta_start,
+                                                         const int* __restrict__ pstart, const T* __restrict__ x,
+                                                         T* __restrict__ y) {
+  __shared__ T w0[kP2StTotal];
+  __shared__ int offs[kP2StTotal];
+  __shared__ int starts[9];
+  const P2Stencil<T>* __restrict__ S = st + blockIdx.y;
+  for (int t = threadIdx.x; t < kP2StTotal; t += blockDim.x) {
+    w0[t] = S->w[0][t];
+    offs[t] = sidx->off[t];
+  }
+  if (threadIdx.x < 9) starts[threadIdx.x] = sidx->start[threadIdx.x];
+  __syncthreads();
+  const OpConst<T>& c = cst[blockIdx.y];
+  const int N = c.N;
+  const int k = __ldg(cta_plane + blockIdx.x);
+  const int s = N - k;
+  const int l = ((threadIdx.x & 127) << 1) | (threadIdx.x >> 7);
+  const int q = (blockIdx.x - __ldg(cta_start + k)) * 256 + l;
+  if (q >= tri(s)) return;
+  const float b = 2.0f * s + 3.0f;
+  int j = (int)(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)q, 0.0f))));
+  j = max(0, min(j, s));
+  if (j < s && row32(s, j + 1) <= q) ++j;
+  if (j > 0 && row32(s, j) > q) --j;
+  const int i = q - row32(s, j);
+  const int p = __ldg(pstart + k) + q;
+  const T* __restrict__ xm = x + c.base;
+  T* __restrict__ ym = y + c.base;
+  const uint32_t table = c.bnd_table;
+  const int z = zero_mask(N, i, j, k);
+  if (DIRICHLET && z != 0 && on_dirichlet(table, N, i, j, k)) {
+    ym[p] = xm[p];
+    return;
+  }
+  // a neighbour can lie on a Dirichlet face only within two lattice steps of one
+  const bool near = DIRICHLET && (i <= 2 || j <= 2 || k <= 2 || N - i - j - k <= 2);
+  const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+  if (z == 0 && !near) {
+    // interior row: constant offsets, loads in flight together
+    int ps[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      const int kk = k - 2 + t;
+      ps[t] = (kk >= 0 && kk <= N) ? __ldg(pstart + kk) : 0;
+    }
+    T acc;
+    switch (par) {
+      case 0: acc = p2_row<T, 0>(w0, xm, ps, N, i, j, k); break;
+      case 1: acc = p2_row<T, 1>(w0, xm, ps, N, i, j, k); break;
+      case 2: acc = p2_row<T, 2>(w0, xm, ps, N, i, j, k); break;
+      case 3: acc = p2_row<T, 3>(w0, xm, ps, N, i, j, k); break;
+      case 4: acc = p2_row<T, 4>(w0, xm, ps, N, i, j, k); break;
+      case 5: acc = p2_row<T, 5>(w0, xm, ps, N, i, j, k); break;
+      case 6: acc = p2_row<T, 6>(w0, xm, ps, N, i, j, k); break;
+      default: acc = p2_row<T, 7>(w0, xm, ps, N, i, j, k); break;
+    }
+    ym[p] = acc;
+    return;
+  }
+  const T* __restrict__ wz = S->w[z];
+  T acc = T(0);
+  const int d1 = starts[par + 1];
+  for (int d = starts[par]; d < d1; ++d) {
+    const T w = z == 0 ? w0[d] : __ldg(wz + d);
+    if (w == T(0)) continue;   // no micro-tet couples the two points (outside the macro on a face)
+    const int o = offs[d];
+    const int ii = i + (o & 15) - 2, jj = j + ((o >> 4) & 15) - 2, kk = k + ((o >> 8) & 15) - 2;
+    if (near && on_dirichlet(table, N, ii, jj, kk)) continue;
+    acc += w * __ldg(xm + __ldg(pstart + kk) + row32(N - kk, jj) + ii);
   }
   ym[p] = acc;
 }
@@ -806,6 +971,23 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
     HHG_CUDA_TRY(cudaGetLastError());
     return HHG_OK;
   }
+  // P2 constant coefficient in FP64: stencil rows (28.75 FMA per point against about 74 in element
+  // form) on the FP64 pipe; in FP32 the marching kernel, whose loads stay in L1, is faster
+  if (op->kind == HHG_DIFFUSION && op->degree == 2 && op->coeff.type == HHG_COEFF_CONST && op->d_p2st64 &&
+      sizeof(T) == 8) {
+    const Interface* I = op->itf;
+    dim3 grid((unsigned)I->ncta, nm);
+    const P2Stencil<T>* st = (const P2Stencil<T>*)(sizeof(T) == 8 ? op->d_p2st64 : op->d_p2st32);
+    const P2StencilIndex* ix = (const P2StencilIndex*)op->d_p2idx;
+    if (op->bc == HHG_DIRICHLET)
+      p2_stencil_kernel<T, true><<<grid, 256, 0, s>>>(dconst<T>(op), st, ix, I->d_cta_plane, I->d_cta_start,
+                                                      I->d_pstart, x, y);
+    else
+      p2_stencil_kernel<T, false><<<grid, 256, 0, s>>>(dconst<T>(op), st, ix, I->d_cta_plane, I->d_cta_start,
+                                                       I->d_pstart, x, y);
+    HHG_CUDA_TRY(cudaGetLastError());
+    return HHG_OK;
+  }
   if (op->kind == HHG_DIFFUSION) return launch_march<T>(op, dconst<T>(op), 0, x, nullptr, field_ptr<T>(op), y, s);
   return fail(HHG_E_UNSUPPORTED, "apply: operator kind %d degree %d coefficient %d not implemented", op->kind,
               op->degree, op->coeff.type);
@@ -835,6 +1017,9 @@ hhg_op::~hhg_op() {
   cudaFree(d_const32);
   cudaFree(d_n1_64);
   cudaFree(d_n1_32);
+  cudaFree(d_p2st64);
+  cudaFree(d_p2st32);
+  cudaFree(d_p2idx);
 }
 
 static int check_dtype(int dtype) {
@@ -852,6 +1037,94 @@ static int check_one_field(const hhg_coeff_t& c, int dtype) {
 static int check_field(const hhg_op* op, int dtype) {
   HHG_TRY(check_one_field(op->coeff, dtype));
   if (op->kind == HHG_CURLCURL) HHG_TRY(check_one_field(op->coeff2, dtype));
+  return HHG_OK;
+}
+
+
+// Stencils of the P2 constant-coefficient operator from the hoisted class matrices A_o.  The
+// structural neighbours of a parity class are the node offsets of all micro-tets that have a node
+// of that parity; the weights for parity p and zero mask z are accumulated over the micro-tets
+// around one representative point with that parity and mask in a virtual macro of 8 cubes per
+// edge (the micro-tets around a point are fixed by its parity and the faces it lies on).
+static int p2_node(int o, int a, int d) {
+  return a < 4 ? 2 * kClassOffsets[o][a][d] : kClassOffsets[o][kP2Edges[a - 4][0]][d] + kClassOffsets[o][kP2Edges[a - 4][1]][d];
+}
+
+static int build_p2_stencil(const hhg_op* op, P2StencilIndex& ix, std::vector<P2Stencil<double>>& W) {
+  std::vector<std::array<int, 3>> lists[8];
+  for (int o = 0; o < 6; ++o)
+    for (int a = 0; a < 10; ++a) {
+      const int par = (p2_node(o, a, 0) & 1) | ((p2_node(o, a, 1) & 1) << 1) | ((p2_node(o, a, 2) & 1) << 2);
+      for (int b = 0; b < 10; ++b) {
+        const std::array<int, 3> d = {p2_node(o, b, 0) - p2_node(o, a, 0), p2_node(o, b, 1) - p2_node(o, a, 1),
+                                      p2_node(o, b, 2) - p2_node(o, a, 2)};
+        if (std::find(lists[par].begin(), lists[par].end(), d) == lists[par].end()) lists[par].push_back(d);
+      }
+    }
+  int tot = 0;
+  for (int par = 0; par < 8; ++par) {
+    std::sort(lists[par].begin(), lists[par].end(), [](const std::array<int, 3>& u, const std::array<int, 3>& v) {
+      return std::make_tuple(u[2], u[1], u[0]) < std::make_tuple(v[2], v[1], v[0]);
+    });
+    ix.start[par] = tot;
+    for (auto& d : lists[par]) {
+      if (tot >= kP2StTotal) return fail(HHG_E_UNSUPPORTED, "P2 stencil: more structural entries than expected");
+      ix.off[tot++] = (d[0] + 2) | ((d[1] + 2) << 4) | ((d[2] + 2) << 8);
+    }
+  }
+  ix.start[8] = tot;
+  if (tot != kP2StTotal) return fail(HHG_E_UNSUPPORTED, "P2 stencil: %d structural entries, expected %d", tot, kP2StTotal);
+  const int nv = 8, Nv = 2 * nv;
+  W.assign(op->mesh->nmacro(), P2Stencil<double>{});
+  for (int m = 0; m < op->mesh->nmacro(); ++m) {
+    std::memset(&W[m], 0, sizeof(P2Stencil<double>));
+    const OpConst<double>& c = op->h_const[m];
+    for (int par = 0; par < 8; ++par)
+      for (int z = 0; z < 15; ++z) {
+        // representative point: coordinate d is 0 on face d+1, else 2 + parity; on face 0 the
+        // last free coordinate closes i + j + k = Nv
+        int P[3], last = -1;
+        bool ok = true;
+        for (int d = 0; d < 3; ++d) {
+          const int pd = (par >> d) & 1;
+          if ((z >> (d + 1)) & 1) {
+            if (pd) ok = false;
+            P[d] = 0;
+          } else {
+            P[d] = 2 + pd;
+            last = d;
+          }
+        }
+        if (!ok) continue;
+        if (z & 1) {
+          if (last < 0) continue;
+          int rest = 0;
+          for (int d = 0; d < 3; ++d)
+            if (d != last) rest += P[d];
+          P[last] = Nv - rest;
+          if ((P[last] & 1) != ((par >> last) & 1) || P[last] < 2) continue;
+        }
+        for (int ck = 0; ck < nv; ++ck)
+          for (int cj = 0; cj + ck < nv; ++cj)
+            for (int ci = 0; ci + cj + ck < nv; ++ci)
+              for (int o = 0; o < 6; ++o) {
+                if (ci + cj + ck > nv - 1 - kClassShrink[o]) continue;
+                const int cc[3] = {ci, cj, ck};
+                for (int a = 0; a < 10; ++a) {
+                  if (2 * cc[0] + p2_node(o, a, 0) != P[0] || 2 * cc[1] + p2_node(o, a, 1) != P[1] ||
+                      2 * cc[2] + p2_node(o, a, 2) != P[2])
+                    continue;
+                  for (int b = 0; b < 10; ++b) {
+                    const std::array<int, 3> d = {p2_node(o, b, 0) - p2_node(o, a, 0),
+                                                  p2_node(o, b, 1) - p2_node(o, a, 1),
+                                                  p2_node(o, b, 2) - p2_node(o, a, 2)};
+                    const auto it = std::find(lists[par].begin(), lists[par].end(), d);
+                    W[m].w[z][ix.start[par] + (int)(it - lists[par].begin())] += c.A[o][a][b];
+                  }
+                }
+              }
+      }
+  }
   return HHG_OK;
 }
 
@@ -899,6 +1172,21 @@ extern "C" int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, 
   HHG_CUDA_TRY(cudaMalloc(&op->d_const32, sizeof(OpConst<float>) * nm));
   HHG_CUDA_TRY(cudaMemcpy(op->d_const64, op->h_const.data(), sizeof(OpConst<double>) * nm, cudaMemcpyHostToDevice));
   HHG_CUDA_TRY(cudaMemcpy(op->d_const32, c32.data(), sizeof(OpConst<float>) * nm, cudaMemcpyHostToDevice));
+  if (kind == HHG_DIFFUSION && degree == 2 && coeff->type == HHG_COEFF_CONST) {
+    P2StencilIndex ix;
+    std::vector<P2Stencil<double>> w64;
+    HHG_TRY(build_p2_stencil(op.get(), ix, w64));
+    std::vector<P2Stencil<float>> w32(nm);
+    for (int m = 0; m < nm; ++m)
+      for (int z = 0; z < 16; ++z)
+        for (int t = 0; t < kP2StTotal; ++t) w32[m].w[z][t] = (float)w64[m].w[z][t];
+    HHG_CUDA_TRY(cudaMalloc(&op->d_p2idx, sizeof(P2StencilIndex)));
+    HHG_CUDA_TRY(cudaMalloc(&op->d_p2st64, sizeof(P2Stencil<double>) * nm));
+    HHG_CUDA_TRY(cudaMalloc(&op->d_p2st32, sizeof(P2Stencil<float>) * nm));
+    HHG_CUDA_TRY(cudaMemcpy(op->d_p2idx, &ix, sizeof(P2StencilIndex), cudaMemcpyHostToDevice));
+    HHG_CUDA_TRY(cudaMemcpy(op->d_p2st64, w64.data(), sizeof(P2Stencil<double>) * nm, cudaMemcpyHostToDevice));
+    HHG_CUDA_TRY(cudaMemcpy(op->d_p2st32, w32.data(), sizeof(P2Stencil<float>) * nm, cudaMemcpyHostToDevice));
+  }
   *out = op.release();
   return HHG_OK;
 }

@@ -48,6 +48,25 @@ def test_apply_parity(meshname, level, degree, kind, bc, dtype):
     assert spread == 0.0
 
 
+@pytest.mark.parametrize("meshname,level", [("reference_tet", 5), ("cube6", 4), ("cuboid36", 3)])
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_p2_const_parity_large(meshname, level, bc, dtype):
+    """P2 constant coefficient (stencil rows per node parity) at sizes with many interior rows."""
+    from gpu_helpers import Case, rel_err
+    import paper_2404_08371_gb300 as hhg
+    c = Case(meshname, level, 2)
+    op = hhg.Operator(c.mesh, degree=2, coeff=("const", 0.8), bc=bc, quad_degree=QD[2])
+    xg = W.uniform(c.S.ndof, seed=4)
+    if dtype == torch.float32:
+        xg = xg.astype(np.float32).astype(np.float64)
+    y = op.apply(c.packed(xg, dtype))
+    ref = OA.diffusion_matrix(c.S, ("const", 0.8), QD[2], bc) @ xg
+    got, spread = c.unpack(y)
+    assert rel_err(got, ref) <= TOL[dtype], rel_err(got, ref)
+    assert spread == 0.0
+
+
 @pytest.mark.parametrize("meshname,level", [("reference_tet", 2), ("cube6", 1), ("cube48", 1)])
 @pytest.mark.parametrize("degree,kind", [(1, "sin3"), (1, "field"), (2, "const"), (2, "sin3"), (2, "field")])
 @pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
