@@ -48,6 +48,12 @@ struct MacroGeom {
 };
 
 // Interface groups of one (level, degree): the copies of every point shared by several macros.
+struct TileTasks {
+  int4* d = nullptr;
+  int64_t n = 0;
+  int kchunk = 32;
+};
+
 struct Interface {
   int64_t ngroups = 0;
   int64_t nmembers = 0;
@@ -70,10 +76,9 @@ struct Interface {
   int4* d_march_tasks = nullptr;
   int64_t n_march_tasks = 0;
   int march_kchunk = 32;
-  // task list of the P1 stencil kernel: (i-chunk, row group, k-chunk, macro), heaviest first
-  int4* d_stencil_tasks = nullptr;
-  int64_t n_stencil_tasks = 0;
-  int stencil_kchunk = 32;
+  // task lists of the plane-tile kernels: (i-chunk, row group, k-chunk, macro), heaviest first;
+  // tile[0] for chunks of 128 points along i, tile[1] for chunks of 64 (degree 2 only)
+  TileTasks tile[2];
   ~Interface();
 };
 
@@ -106,6 +111,7 @@ struct hhg_mesh {
   size_t scratch_bytes = 0;
   int nmacro() const { return (int)macros.size(); }
   int interface(int level, int degree, const hhg::Interface** out);
+  int build_tile_tasks(int64_t N, int64_t iw, int64_t jw, hhg::TileTasks* out) const;
   int scratch_reserve(size_t bytes);
   ~hhg_mesh();
 };
@@ -217,7 +223,7 @@ struct hhg_op {
   hhg_coeff_t coeff2{};      // second coefficient (beta of the Nedelec operator)
   void* d_p2st64 = nullptr;  // P2Stencil<double>[nmacro] (P2 constant-coefficient diffusion)
   void* d_p2st32 = nullptr;
-  void* d_p2idx = nullptr;   // P2StencilIndex
+  void* d_p2idx = nullptr;   // P2StencilIndex (structural neighbour lists)
   void* d_n1_64 = nullptr;   // N1Const<double>[nmacro]
   void* d_n1_32 = nullptr;
   int N = 0, n = 0;

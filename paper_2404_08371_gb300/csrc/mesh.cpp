@@ -54,7 +54,8 @@ Interface::~Interface() {
   cudaFree(d_cta_start);
   cudaFree(d_pstart);
   cudaFree(d_march_tasks);
-  cudaFree(d_stencil_tasks);
+  cudaFree(tile[0].d);
+  cudaFree(tile[1].d);
   cudaFree(d_sign);
 }
 
@@ -363,6 +364,42 @@ extern "C" int hhg_mesh_destroy(hhg_mesh_t* mesh) {
 }
 
 // Build (once) the interface groups of (level, degree).
+// Tasks of a plane-tile kernel on one macro lattice of resolution N: tiles of iw points along i
+// and jw rows, k-chunks halved until the list (times the macros) fills the GPU, heaviest first.
+int hhg_mesh::build_tile_tasks(int64_t N, int64_t iw, int64_t jw, TileTasks* out) const {
+  int kch = 32;
+  std::vector<std::pair<int64_t, int4>> tasks;
+  for (;;) {
+    tasks.clear();
+    for (int64_t kc = 0; kc * kch <= N; ++kc)
+      for (int64_t ty = 0; ty * jw + kc * kch <= N; ++ty)
+        for (int64_t tx = 0; tx * iw + ty * jw + kc * kch <= N; ++tx) {
+          int64_t work = 0;
+          for (int64_t k = kc * kch; k < std::min<int64_t>(kc * kch + kch, N + 1); ++k)
+            for (int64_t j = ty * jw; j < ty * jw + jw; ++j) {
+              const int64_t len = N - j - k + 1 - tx * iw;   // points of the row from the chunk start
+              if (len > 0) work += std::min<int64_t>(len, iw);
+            }
+          tasks.push_back({work, int4{(int)tx, (int)ty, (int)kc, 0}});
+        }
+    if (kch <= 4 || (int64_t)tasks.size() * nmacro() >= 8 * 152) break;
+    kch /= 2;
+  }
+  std::vector<std::pair<int64_t, int4>> all;
+  for (int mac = 0; mac < nmacro(); ++mac)
+    for (auto& t : tasks) all.push_back({t.first, int4{t.second.x, t.second.y, t.second.z, mac}});
+  std::stable_sort(all.begin(), all.end(), [](const std::pair<int64_t, int4>& a, const std::pair<int64_t, int4>& b) {
+    return a.first > b.first;
+  });
+  std::vector<int4> tv(all.size());
+  for (size_t t = 0; t < all.size(); ++t) tv[t] = all[t].second;
+  out->kchunk = kch;
+  out->n = (int64_t)tv.size();
+  HHG_CUDA_TRY(cudaMalloc(&out->d, sizeof(int4) * tv.size()));
+  HHG_CUDA_TRY(cudaMemcpy(out->d, tv.data(), sizeof(int4) * tv.size(), cudaMemcpyHostToDevice));
+  return HHG_OK;
+}
+
 int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
   if (lvl < 0 || lvl > level) return fail(HHG_E_ARG, "level %d outside 0..%d", lvl, level);
   if (degree != 1 && degree != 2) return fail(HHG_E_ARG, "degree must be 1 or 2");
@@ -517,39 +554,11 @@ int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
     HHG_CUDA_TRY(cudaMalloc(&I->d_march_tasks, sizeof(int4) * tv.size()));
     HHG_CUDA_TRY(cudaMemcpy(I->d_march_tasks, tv.data(), sizeof(int4) * tv.size(), cudaMemcpyHostToDevice));
   }
-  // P1 stencil-kernel tasks: (i-chunk, row group, k-chunk), sorted by their number of points
-  if (degree == 1) {
-    const int64_t iw = 32 * kStencilV, jw = kStencilWarps;
-    int kch = 32;
-    std::vector<std::pair<int64_t, int4>> tasks;
-    for (;;) {
-      tasks.clear();
-      for (int64_t kc = 0; kc * kch <= N; ++kc)
-        for (int64_t ty = 0; ty * jw + kc * kch <= N; ++ty)
-          for (int64_t tx = 0; tx * iw + ty * jw + kc * kch <= N; ++tx) {
-            int64_t work = 0;
-            for (int64_t k = kc * kch; k < std::min<int64_t>(kc * kch + kch, N + 1); ++k)
-              for (int64_t j = ty * jw; j < ty * jw + jw; ++j) {
-                const int64_t len = N - j - k + 1 - tx * iw;   // points of the row from the chunk start
-                if (len > 0) work += std::min<int64_t>(len, iw);
-              }
-            tasks.push_back({work, int4{(int)tx, (int)ty, (int)kc, 0}});
-          }
-      if (kch <= 4 || (int64_t)tasks.size() * nmacro() >= 8 * 152) break;
-      kch /= 2;
-    }
-    std::vector<std::pair<int64_t, int4>> all;
-    for (int mac = 0; mac < nmacro(); ++mac)
-      for (auto& t : tasks) all.push_back({t.first, int4{t.second.x, t.second.y, t.second.z, mac}});
-    std::stable_sort(all.begin(), all.end(), [](const std::pair<int64_t, int4>& a, const std::pair<int64_t, int4>& b) {
-      return a.first > b.first;
-    });
-    std::vector<int4> tv(all.size());
-    for (size_t t = 0; t < all.size(); ++t) tv[t] = all[t].second;
-    I->stencil_kchunk = kch;
-    I->n_stencil_tasks = (int64_t)tv.size();
-    HHG_CUDA_TRY(cudaMalloc(&I->d_stencil_tasks, sizeof(int4) * tv.size()));
-    HHG_CUDA_TRY(cudaMemcpy(I->d_stencil_tasks, tv.data(), sizeof(int4) * tv.size(), cudaMemcpyHostToDevice));
+  // plane-tile kernel tasks: (i-chunk, row group, k-chunk), sorted by their number of points
+  if (degree == 1) HHG_TRY(build_tile_tasks(N, 32 * kStencilV, kStencilWarps, &I->tile[0]));
+  if (degree == 2) {
+    HHG_TRY(build_tile_tasks(N, 128, kStencilWarps, &I->tile[0]));
+    HHG_TRY(build_tile_tasks(N, 64, kStencilWarps, &I->tile[1]));
   }
   I->h_ptr = ptr;
   I->h_idx = idx;

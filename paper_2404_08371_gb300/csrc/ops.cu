@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <array>
 #include <tuple>
+#include <type_traits>
 #include <utility>
 #include <cmath>
 #include <cstring>
@@ -419,113 +420,50 @@ struct P2Off {
 };
 static_assert(P2Start<7>::v + P2Cnt<7>::v == kP2StTotal, "P2 structural stencil size");
 
-template <typename T, int O>
-__device__ __forceinline__ T p2_ld(const T* __restrict__ xm, const int (&ps)[5], int N, int i, int j, int k) {
-  constexpr int dx = (O & 15) - 2, dy = ((O >> 4) & 15) - 2, dz = ((O >> 8) & 15) - 2;
-  return __ldg(xm + ps[dz + 2] + row32(N - (k + dz), j + dy) + i + dx);
-}
-
-// Interior row of parity PAR: all loads issued first, then the weighted sum.
-template <typename T, int PAR, int... D>
-__device__ __forceinline__ T p2_row_fast(const T* __restrict__ w, const T* __restrict__ xm, const int (&ps)[5], int N,
-                                         int i, int j, int k, std::integer_sequence<int, D...>) {
-  const T v[] = {p2_ld<T, P2Off<PAR, D>::v>(xm, ps, N, i, j, k)...};
-  T acc = T(0);
-#pragma unroll
-  for (int t = 0; t < (int)sizeof...(D); ++t) acc += w[P2Start<PAR>::v + t] * v[t];
-  return acc;
-}
-
-template <typename T, int PAR>
-__device__ __forceinline__ T p2_row(const T* __restrict__ w, const T* __restrict__ xm, const int (&ps)[5], int N, int i,
-                                    int j, int k) {
-  return p2_row_fast<T, PAR>(w, xm, ps, N, i, j, k, std::make_integer_sequence<int, P2Cnt<PAR>::v>{});
-}
-
-// P2 constant-coefficient apply, one thread per output point of the doubled lattice (gather).
-// The row of a point is the stencil of its parity class and zero mask, assembled on the host from
-// the hoisted class matrices; interior rows come from shared memory, rows of points on macro faces
-// from the per-macro table.  Threads 0..127 take the even, 128..255 the odd positions of the CTA's
-// 256 consecutive points, so a warp mostly holds points of one parity and runs one stencil.
-template <typename T, bool DIRICHLET>
-__global__ void __launch_bounds__(256) p2_stencil_kernel(const OpConst<T>* __restrict__ cst,
-                                                         const P2Stencil<T>* __restrict__ st,
-                                                         const P2StencilIndex* __restrict__ sidx,
-                                                         const int* __restrict__ cta_plane,
-                                                         const int* __restrict__ cta_start,
-                                                         const int* __restrict__ pstart, const T* __restrict__ x,
-                                                         T* __restrict__ y) {
-  __shared__ T w0[kP2StTotal];
-  __shared__ int offs[kP2StTotal];
-  __shared__ int starts[9];
-  const P2Stencil<T>* __restrict__ S = st + blockIdx.y;
-  for (int t = threadIdx.x; t < kP2StTotal; t += blockDim.x) {
-    w0[t] = S->w[0][t];
-    offs[t] = sidx->off[t];
-  }
-  if (threadIdx.x < 9) starts[threadIdx.x] = sidx->start[threadIdx.x];
-  __syncthreads();
-  const OpConst<T>& c = cst[blockIdx.y];
-  const int N = c.N;
-  const int k = __ldg(cta_plane + blockIdx.x);
-  const int s = N - k;
-  const int l = ((threadIdx.x & 127) << 1) | (threadIdx.x >> 7);
-  const int q = (blockIdx.x - __ldg(cta_start + k)) * 256 + l;
-  if (q >= tri(s)) return;
-  const float b = 2.0f * s + 3.0f;
-  int j = (int)(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)q, 0.0f))));
-  j = max(0, min(j, s));
-  if (j < s && row32(s, j + 1) <= q) ++j;
-  if (j > 0 && row32(s, j) > q) --j;
-  const int i = q - row32(s, j);
-  const int p = __ldg(pstart + k) + q;
-  const T* __restrict__ xm = x + c.base;
-  T* __restrict__ ym = y + c.base;
-  const uint32_t table = c.bnd_table;
-  const int z = zero_mask(N, i, j, k);
-  if (DIRICHLET && z != 0 && on_dirichlet(table, N, i, j, k)) {
-    ym[p] = xm[p];
-    return;
-  }
-  // a neighbour can lie on a Dirichlet face only within two lattice steps of one
-  const bool near = DIRICHLET && (i <= 2 || j <= 2 || k <= 2 || N - i - j - k <= 2);
-  const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-  if (z == 0 && !near) {
-    // interior row: constant offsets, loads in flight together
-    int ps[5];
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-      const int kk = k - 2 + t;
-      ps[t] = (kk >= 0 && kk <= N) ? __ldg(pstart + kk) : 0;
+// The two points of a lane (even i of parity PA, odd i + 1 of parity PA | 1) share most staged
+// cells: the union of their neighbours, as offsets from the even point, with the entry of each
+// stencil that uses the cell (-1: not used), lets each cell be loaded once.
+struct P2UnionList {
+  int n;
+  int off[65];
+  int ia[65];
+  int ib[65];
+};
+__host__ __device__ constexpr P2UnionList p2_union_list(int pa) {
+  P2UnionList U{};
+  const P2OffList A = p2_struct_list(pa), B = p2_struct_list(pa | 1);
+  for (int s = 0; s < 2; ++s) {
+    const P2OffList& L = s == 0 ? A : B;
+    for (int d = 0; d < L.n; ++d) {
+      const int v = L.off[d] + s;   // dx + 1 for the odd point
+      int pos = 0;
+      while (pos < U.n && U.off[pos] < v) ++pos;
+      if (!(pos < U.n && U.off[pos] == v)) {
+        for (int t = U.n; t > pos; --t) {
+          U.off[t] = U.off[t - 1];
+          U.ia[t] = U.ia[t - 1];
+          U.ib[t] = U.ib[t - 1];
+        }
+        U.off[pos] = v;
+        U.ia[pos] = -1;
+        U.ib[pos] = -1;
+        ++U.n;
+      }
+      (s == 0 ? U.ia[pos] : U.ib[pos]) = d;
     }
-    T acc;
-    switch (par) {
-      case 0: acc = p2_row<T, 0>(w0, xm, ps, N, i, j, k); break;
-      case 1: acc = p2_row<T, 1>(w0, xm, ps, N, i, j, k); break;
-      case 2: acc = p2_row<T, 2>(w0, xm, ps, N, i, j, k); break;
-      case 3: acc = p2_row<T, 3>(w0, xm, ps, N, i, j, k); break;
-      case 4: acc = p2_row<T, 4>(w0, xm, ps, N, i, j, k); break;
-      case 5: acc = p2_row<T, 5>(w0, xm, ps, N, i, j, k); break;
-      case 6: acc = p2_row<T, 6>(w0, xm, ps, N, i, j, k); break;
-      default: acc = p2_row<T, 7>(w0, xm, ps, N, i, j, k); break;
-    }
-    ym[p] = acc;
-    return;
   }
-  const T* __restrict__ wz = S->w[z];
-  T acc = T(0);
-  const int d1 = starts[par + 1];
-  for (int d = starts[par]; d < d1; ++d) {
-    const T w = z == 0 ? w0[d] : __ldg(wz + d);
-    if (w == T(0)) continue;   // no micro-tet couples the two points (outside the macro on a face)
-    const int o = offs[d];
-    const int ii = i + (o & 15) - 2, jj = j + ((o >> 4) & 15) - 2, kk = k + ((o >> 8) & 15) - 2;
-    if (near && on_dirichlet(table, N, ii, jj, kk)) continue;
-    acc += w * __ldg(xm + __ldg(pstart + kk) + row32(N - kk, jj) + ii);
-  }
-  ym[p] = acc;
+  return U;
 }
-
+template <int PA>
+struct P2UCnt {
+  static constexpr int v = p2_union_list(PA).n;
+};
+template <int PA, int C>
+struct P2UCell {
+  static constexpr int off = p2_union_list(PA).off[C];
+  static constexpr int ia = p2_union_list(PA).ia[C];
+  static constexpr int ib = p2_union_list(PA).ib[C];
+};
 
 // P1 constant-coefficient apply in FP32 from shared-memory plane tiles.  A CTA owns rows
 // j0..j0+7 and points i0..i0+kTileI-1 of a k-chunk (task list of the stencil kernel) and climbs
@@ -752,6 +690,310 @@ __global__ void __launch_bounds__(256, 3) p1_tile_f32_kernel(const OpConst<float
 
 constexpr size_t p1_tile_f32_smem() { return sizeof(float) * kTileRing * kPairSlot; }
 
+// ---------------------------------------------------------------------------
+// P2 constant-coefficient apply from shared-memory plane tiles.  A CTA owns rows j0..j0+7 and
+// points i0..i0+TI-1 of a k-chunk and climbs its planes.  Each plane of the tile plus a halo of two
+// points (the reach of a P2 row) is staged with cp.async into a ring of planes, kP2Ahead planes
+// beyond the k+2 that the plane k being computed needs; staged Dirichlet points are zeroed on
+// arrival.  A lane evaluates the points i0 + 64 v + 2 lane + {0, 1}: both node parities of its row,
+// so a warp never diverges between stencils, with offsets known at compile time.  Even and odd
+// staged columns are kept apart (column c at (c & 1) W/2 + c/2), so the 32 lanes of a warp read 32
+// consecutive words.  The tile writes the points off the macro faces; p2_face_kernel the rest.
+constexpr int kP2TileJ = 8;
+constexpr int kP2TileH = kP2TileJ + 4;
+constexpr int kP2Ahead = 2;
+constexpr int kP2Ring = kP2Ahead + 5;   // planes k-2 .. k+2+kP2Ahead; one barrier per plane
+
+template <typename T>
+struct P2W;
+
+template <typename T, int TI>
+constexpr size_t p2_tile_smem() {
+  return sizeof(T) * kP2Ring * (TI + 4) * kP2TileH + sizeof(typename P2W<T>::type) * kP2StTotal;
+}
+
+__host__ __device__ constexpr int p2_scol(int c, int W) { return (c & 1) * (W / 2) + (c >> 1); }
+
+template <typename T, int TI>
+__device__ __forceinline__ void p2_issue_plane(T* slot, const T* __restrict__ xm, const int* __restrict__ pstart, int N,
+                                               int i0, int j0, int kk) {
+  constexpr int W = TI + 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = warp + 8 * h;
+    if (r >= kP2TileH) break;
+    const int jr = j0 - 2 + r;
+    const int len = N - jr - kk + 1;
+    const bool rowok = jr >= 0 && kk >= 0 && kk <= N && len > 0;
+    const T* __restrict__ row = rowok ? xm + __ldg(pstart + kk) + row32(N - kk, jr) : xm;
+#pragma unroll
+    for (int t = 0; t < (W + 31) / 32; ++t) {
+      const int col = lane + 32 * t;
+      if (col >= W) break;
+      const int ii = i0 - 2 + col;
+      // cells outside the macro are never read by a point the tile stores: not staged
+      if (rowok && ii >= 0 && ii < len) cp_async_zfill(slot + r * W + p2_scol(col, W), row + ii, (int)sizeof(T), true);
+    }
+  }
+}
+
+// Zero the staged Dirichlet points of plane kk; each thread clears only what it staged itself.
+template <typename T, int TI>
+__device__ __forceinline__ void p2_mask_plane(T* slot, int N, uint32_t table, int i0, int j0, int kk) {
+  constexpr int W = TI + 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = warp + 8 * h;
+    if (r >= kP2TileH) break;
+    const int jr = j0 - 2 + r;
+    const int len = N - jr - kk + 1;
+    if (!(jr >= 0 && kk >= 0 && kk <= N && len > 0)) continue;
+    if (jr == 0 || kk == 0) {
+#pragma unroll
+      for (int t = 0; t < (W + 31) / 32; ++t) {
+        const int col = lane + 32 * t;
+        if (col >= W) break;
+        const int ii = i0 - 2 + col;
+        if (ii >= 0 && ii < len && on_dirichlet(table, N, ii, jr, kk)) slot[r * W + p2_scol(col, W)] = T(0);
+      }
+    } else {
+      const int cand[2] = {2 - i0, len + 1 - i0};   // columns of i = 0 and i = len - 1
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int col = cand[e];
+        if (col >= 0 && col < W && (col & 31) == lane) {
+          const int ii = i0 - 2 + col;
+          if (on_dirichlet(table, N, ii, jr, kk)) slot[r * W + p2_scol(col, W)] = T(0);
+        }
+      }
+    }
+  }
+}
+
+// Weights of the interior rows in shared memory: FP32 weights stored twice (w, w), so that one
+// 8-byte load feeds a packed FMA over the lane's two points 64 apart.
+template <typename T>
+struct P2W {
+  using type = T;
+};
+template <>
+struct P2W<float> {
+  using type = float2;
+};
+
+// Cell C of the union list of row parity PA (even point) for the lane; ob = r W + 1 + lane.
+template <typename T, int W, int NV, int PA, int C>
+__device__ __forceinline__ void p2_tile_cell(const typename P2W<T>::type* w, const T* const (&pl)[5], int ob,
+                                             T (&a0)[NV], T (&a1)[NV]) {
+  constexpr int O = P2UCell<PA, C>::off, IA = P2UCell<PA, C>::ia, IB = P2UCell<PA, C>::ib;
+  constexpr int dx = (O & 15) - 2, dy = ((O >> 4) & 15) - 2, dz = ((O >> 8) & 15) - 2;
+  constexpr int off = dy * W + (dx & 1) * (W / 2) + ((dx + 4) >> 1) - 2;   // staged column 2 + 2 lane + dx
+  const T* p = pl[dz + 2] + ob + off;
+  if constexpr (std::is_same<T, float>::value && NV == 2) {
+    const float2 xv = make_float2(p[0], p[32]);
+    if constexpr (IA >= 0) {
+      float2 acc = make_float2(a0[0], a0[1]);
+      acc = __ffma2_rn(w[P2Start<PA>::v + IA], xv, acc);
+      a0[0] = acc.x;
+      a0[1] = acc.y;
+    }
+    if constexpr (IB >= 0) {
+      float2 acc = make_float2(a1[0], a1[1]);
+      acc = __ffma2_rn(w[P2Start<PA | 1>::v + IB], xv, acc);
+      a1[0] = acc.x;
+      a1[1] = acc.y;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T xv = p[32 * v];
+      if constexpr (IA >= 0) {
+        if constexpr (std::is_same<T, float>::value)
+          a0[v] += w[P2Start<PA>::v + IA].x * xv;
+        else
+          a0[v] += w[P2Start<PA>::v + IA] * xv;
+      }
+      if constexpr (IB >= 0) {
+        if constexpr (std::is_same<T, float>::value)
+          a1[v] += w[P2Start<PA | 1>::v + IB].x * xv;
+        else
+          a1[v] += w[P2Start<PA | 1>::v + IB] * xv;
+      }
+    }
+  }
+}
+
+template <typename T, int W, int NV, int PA, int... C>
+__device__ __forceinline__ void p2_tile_cells(const typename P2W<T>::type* w, const T* const (&pl)[5], int ob,
+                                              T (&a0)[NV], T (&a1)[NV], std::integer_sequence<int, C...>) {
+  (p2_tile_cell<T, W, NV, PA, C>(w, pl, ob, a0, a1), ...);
+}
+
+// Interior rows of parities PA (even i) and PA | 1 (odd i) over the union of their cells.
+template <typename T, int W, int NV, int PA>
+__device__ __forceinline__ void p2_tile_pair(const typename P2W<T>::type* w, const T* const (&pl)[5], int ob,
+                                             T (&a0)[NV], T (&a1)[NV]) {
+  p2_tile_cells<T, W, NV, PA>(w, pl, ob, a0, a1, std::make_integer_sequence<int, P2UCnt<PA>::v>{});
+}
+
+// Interior points of one tile row (row parity PA): the second half of a 128-point tile only when
+// the row reaches into it.  Points on macro faces are left to p2_face_kernel.
+template <typename T, int W, int NV, int PA>
+__device__ __forceinline__ void p2_tile_row(const typename P2W<T>::type* w, const T* const (&pl)[5], int ob, int i0,
+                                            int len, T* __restrict__ yrow) {
+  const int lane = threadIdx.x & 31;
+  if (NV == 2 && len - i0 <= 64) {
+    T a0[1] = {T(0)}, a1[1] = {T(0)};
+    p2_tile_pair<T, W, 1, PA>(w, pl, ob, a0, a1);
+    const int ii = i0 + 2 * lane;
+    if (ii > 0 && ii < len - 1) yrow[ii] = a0[0];
+    if (ii + 1 < len - 1) yrow[ii + 1] = a1[0];
+    return;
+  }
+  T a0[NV], a1[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) a0[v] = a1[v] = T(0);
+  p2_tile_pair<T, W, NV, PA>(w, pl, ob, a0, a1);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int ii = i0 + 64 * v + 2 * lane;
+    if (ii > 0 && ii < len - 1) yrow[ii] = a0[v];
+    if (ii + 1 < len - 1) yrow[ii + 1] = a1[v];
+  }
+}
+
+template <typename T, int TI, bool DIRICHLET>
+__global__ void __launch_bounds__(256) p2_tile_kernel(const OpConst<T>* __restrict__ cst,
+                                                      const P2Stencil<T>* __restrict__ st,
+                                                      const int4* __restrict__ tasks, int kch,
+                                                      const int* __restrict__ pstart, const T* __restrict__ x,
+                                                      T* __restrict__ y) {
+  constexpr int W = TI + 4;
+  constexpr int SLOT = W * kP2TileH;
+  constexpr int NV = TI / 64;
+  extern __shared__ __align__(16) unsigned char p2_tile_smem_raw[];
+  using WT = typename P2W<T>::type;
+  T* buf = reinterpret_cast<T*>(p2_tile_smem_raw);
+  WT* w0 = reinterpret_cast<WT*>(buf + kP2Ring * SLOT);
+  const int4 task = tasks[blockIdx.x];
+  const OpConst<T>& c = cst[task.w];
+  const int N = c.N;
+  const int i0 = task.x * TI, j0 = task.y * kP2TileJ, k0 = task.z * kch;
+  const int k_end = min(k0 + kch - 1, N - j0 - i0);
+  if (k_end < k0) return;   // uniform over the CTA
+  for (int t = threadIdx.x; t < kP2StTotal; t += blockDim.x) {
+    const T wt = st[task.w].w[0][t];
+    if constexpr (std::is_same<T, float>::value)
+      w0[t] = make_float2(wt, wt);
+    else
+      w0[t] = wt;
+  }
+  const uint32_t table = c.bnd_table;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T* __restrict__ xm = x + c.base;
+  T* __restrict__ ym = y + c.base;
+  for (int q = 0; q < kP2Ring - 1; ++q) {
+    const int kk = k0 - 2 + q;
+    if (kk <= k_end + 2) p2_issue_plane<T, TI>(buf + q * SLOT, xm, pstart, N, i0, j0, kk);
+    cp_async_commit();
+  }
+  cp_async_wait<kP2Ahead>();   // planes k0-2 .. k0+1 have arrived
+  if (DIRICHLET) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p2_mask_plane<T, TI>(buf + q * SLOT, N, table, i0, j0, k0 - 2 + q);
+  }
+  const int j = j0 + warp;
+  const int ob = (warp + 2) * W + 1 + lane;
+  for (int k = k0; k <= k_end; ++k) {
+    const int q = k - k0;   // plane kk sits in ring slot (kk - k0 + 2) mod kP2Ring
+    cp_async_wait<kP2Ahead - 1>();   // plane k+2 has arrived
+    if (DIRICHLET) p2_mask_plane<T, TI>(buf + ((q + 4) % kP2Ring) * SLOT, N, table, i0, j0, k + 2);
+    __syncthreads();
+    {
+      const int kn = k + 2 + kP2Ahead;   // into the slot of plane k-3, read for the last time in step k-1
+      if (kn <= k_end + 2) p2_issue_plane<T, TI>(buf + ((q + 4 + kP2Ahead) % kP2Ring) * SLOT, xm, pstart, N, i0, j0, kn);
+      cp_async_commit();
+    }
+    const int len = N - j - k + 1;
+    // rows j = 0 and planes k = 0 hold only points on macro faces
+    if (j > 0 && k > 0 && len > 0 && i0 < len) {
+      const T* pl[5];
+#pragma unroll
+      for (int t = 0; t < 5; ++t) pl[t] = buf + ((q + t) % kP2Ring) * SLOT;
+      T* __restrict__ yrow = ym + __ldg(pstart + k) + row32(N - k, j);
+      switch ((j & 1) | ((k & 1) << 1)) {
+        case 0: p2_tile_row<T, W, NV, 0>(w0, pl, ob, i0, len, yrow); break;
+        case 1: p2_tile_row<T, W, NV, 2>(w0, pl, ob, i0, len, yrow); break;
+        case 2: p2_tile_row<T, W, NV, 4>(w0, pl, ob, i0, len, yrow); break;
+        default: p2_tile_row<T, W, NV, 6>(w0, pl, ob, i0, len, yrow); break;
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// Points on the faces of the macros (zero mask z != 0), one thread each: face a of the macro has the
+// points (a, b) with a + b <= N of its triangle; a point on several faces is written by the lowest.
+// Its row comes from the face table (zero weights outside the macro); x is read from global memory.
+template <typename T, bool DIRICHLET>
+__global__ void __launch_bounds__(256) p2_face_kernel(const OpConst<T>* __restrict__ cst,
+                                                      const P2Stencil<T>* __restrict__ st,
+                                                      const P2StencilIndex* __restrict__ sidx,
+                                                      const int* __restrict__ pstart, const T* __restrict__ x,
+                                                      T* __restrict__ y) {
+  __shared__ int offs[kP2StTotal];
+  __shared__ int starts[9];
+  for (int t = threadIdx.x; t < kP2StTotal; t += blockDim.x) offs[t] = sidx->off[t];
+  if (threadIdx.x < 9) starts[threadIdx.x] = sidx->start[threadIdx.x];
+  __syncthreads();
+  const int macro = blockIdx.z, f = blockIdx.y;
+  const OpConst<T>& c = cst[macro];
+  const int N = c.N;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tri(N)) return;
+  const float bq = 2.0f * N + 3.0f;
+  int b = (int)(0.5f * (bq - sqrtf(fmaxf(bq * bq - 8.0f * (float)t, 0.0f))));
+  b = max(0, min(b, N));
+  if (b < N && row32(N, b + 1) <= t) ++b;
+  if (b > 0 && row32(N, b) > t) --b;
+  const int a = t - row32(N, b);
+  int i, j, k;
+  if (f == 0) {
+    i = 0; j = a; k = b;
+  } else if (f == 1) {
+    i = a; j = 0; k = b;
+  } else if (f == 2) {
+    i = a; j = b; k = 0;
+  } else {
+    i = N - a - b; j = a; k = b;
+  }
+  if ((f >= 1 && i == 0) || (f >= 2 && j == 0) || (f == 3 && k == 0)) return;
+  const T* __restrict__ xm = x + c.base;
+  T* __restrict__ ym = y + c.base;
+  const uint32_t table = c.bnd_table;
+  const int p = __ldg(pstart + k) + row32(N - k, j) + i;
+  if (DIRICHLET && on_dirichlet(table, N, i, j, k)) {
+    ym[p] = xm[p];
+    return;
+  }
+  const int z = zero_mask(N, i, j, k);
+  const T* __restrict__ wz = st[macro].w[z];
+  const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+  T acc = T(0);
+  const int d1 = starts[par + 1];
+  for (int d = starts[par]; d < d1; ++d) {
+    const T w = __ldg(wz + d);
+    if (w == T(0)) continue;   // no micro-tet of the macro couples the two points
+    const int o = offs[d];
+    const int ii = i + (o & 15) - 2, jj = j + ((o >> 4) & 15) - 2, kk = k + ((o >> 8) & 15) - 2;
+    if (DIRICHLET && on_dirichlet(table, N, ii, jj, kk)) continue;
+    acc += w * __ldg(xm + __ldg(pstart + kk) + row32(N - kk, jj) + ii);
+  }
+  ym[p] = acc;
+}
+
 // diag(A) for the constant-coefficient operators: sum of A_T[a][a] over the incident micro-tets.
 template <typename T>
 __global__ void const_diag_kernel(const OpConst<T>* __restrict__ cst, int degree, bool dirichlet, T* __restrict__ d) {
@@ -940,6 +1182,8 @@ const T* field_ptr(const hhg_op* op) {
                                                                                           : nullptr;
 }
 
+static inline int64_t tri_host(int64_t s) { return (s + 1) * (s + 2) / 2; }
+
 template <typename T>
 int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
   const int64_t V = lattice_size(op->N);
@@ -959,32 +1203,38 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
       HHG_CUDA_TRY(cudaGetLastError());
       return HHG_OK;
     }
-    const unsigned grid = (unsigned)I->n_stencil_tasks;
+    const unsigned grid = (unsigned)I->tile[0].n;
     const size_t smem = p1_tile_f32_smem();
     const OpConst<float>* cf = (const OpConst<float>*)op->d_const32;
     if (op->bc == HHG_DIRICHLET)
-      p1_tile_f32_kernel<true><<<grid, 256, smem, s>>>(cf, I->d_stencil_tasks, I->stencil_kchunk, I->d_pstart,
+      p1_tile_f32_kernel<true><<<grid, 256, smem, s>>>(cf, I->tile[0].d, I->tile[0].kchunk, I->d_pstart,
                                                        (const float*)x, (float*)y);
     else
-      p1_tile_f32_kernel<false><<<grid, 256, smem, s>>>(cf, I->d_stencil_tasks, I->stencil_kchunk, I->d_pstart,
+      p1_tile_f32_kernel<false><<<grid, 256, smem, s>>>(cf, I->tile[0].d, I->tile[0].kchunk, I->d_pstart,
                                                         (const float*)x, (float*)y);
     HHG_CUDA_TRY(cudaGetLastError());
     return HHG_OK;
   }
-  // P2 constant coefficient in FP64: stencil rows (28.75 FMA per point against about 74 in element
-  // form) on the FP64 pipe; in FP32 the marching kernel, whose loads stay in L1, is faster
-  if (op->kind == HHG_DIFFUSION && op->degree == 2 && op->coeff.type == HHG_COEFF_CONST && op->d_p2st64 &&
-      sizeof(T) == 8) {
+  // P2 constant coefficient: stencil rows (28.75 FMA per point against about 74 in element form)
+  // from shared-memory plane tiles; 128-point tiles in FP32, 64-point tiles in FP64
+  if (op->kind == HHG_DIFFUSION && op->degree == 2 && op->coeff.type == HHG_COEFF_CONST && op->d_p2st64) {
     const Interface* I = op->itf;
-    dim3 grid((unsigned)I->ncta, nm);
     const P2Stencil<T>* st = (const P2Stencil<T>*)(sizeof(T) == 8 ? op->d_p2st64 : op->d_p2st32);
+    constexpr int TI = sizeof(T) == 8 ? 64 : 128;
+    const TileTasks& tt = I->tile[sizeof(T) == 8 ? 1 : 0];
+    constexpr size_t smem = p2_tile_smem<T, TI>();
+    static_assert(smem <= 48 * 1024, "P2 tile exceeds the default dynamic shared memory");
     const P2StencilIndex* ix = (const P2StencilIndex*)op->d_p2idx;
-    if (op->bc == HHG_DIRICHLET)
-      p2_stencil_kernel<T, true><<<grid, 256, 0, s>>>(dconst<T>(op), st, ix, I->d_cta_plane, I->d_cta_start,
-                                                      I->d_pstart, x, y);
-    else
-      p2_stencil_kernel<T, false><<<grid, 256, 0, s>>>(dconst<T>(op), st, ix, I->d_cta_plane, I->d_cta_start,
-                                                       I->d_pstart, x, y);
+    const dim3 fgrid((unsigned)((tri_host(op->N) + 255) / 256), 4, nm);
+    if (op->bc == HHG_DIRICHLET) {
+      p2_tile_kernel<T, TI, true><<<(unsigned)tt.n, 256, smem, s>>>(dconst<T>(op), st, tt.d, tt.kchunk,
+                                                                    I->d_pstart, x, y);
+      p2_face_kernel<T, true><<<fgrid, 256, 0, s>>>(dconst<T>(op), st, ix, I->d_pstart, x, y);
+    } else {
+      p2_tile_kernel<T, TI, false><<<(unsigned)tt.n, 256, smem, s>>>(dconst<T>(op), st, tt.d, tt.kchunk,
+                                                                     I->d_pstart, x, y);
+      p2_face_kernel<T, false><<<fgrid, 256, 0, s>>>(dconst<T>(op), st, ix, I->d_pstart, x, y);
+    }
     HHG_CUDA_TRY(cudaGetLastError());
     return HHG_OK;
   }
@@ -1074,6 +1324,13 @@ static int build_p2_stencil(const hhg_op* op, P2StencilIndex& ix, std::vector<P2
   }
   ix.start[8] = tot;
   if (tot != kP2StTotal) return fail(HHG_E_UNSUPPORTED, "P2 stencil: %d structural entries, expected %d", tot, kP2StTotal);
+  // the tile kernel unrolls the same lists at compile time: both orders must agree entry by entry
+  for (int par = 0; par < 8; ++par) {
+    const P2OffList L = p2_struct_list(par);
+    if (L.n != ix.start[par + 1] - ix.start[par]) return fail(HHG_E_UNSUPPORTED, "P2 stencil: list size mismatch");
+    for (int d = 0; d < L.n; ++d)
+      if (L.off[d] != ix.off[ix.start[par] + d]) return fail(HHG_E_UNSUPPORTED, "P2 stencil: list order mismatch");
+  }
   const int nv = 8, Nv = 2 * nv;
   W.assign(op->mesh->nmacro(), P2Stencil<double>{});
   for (int m = 0; m < op->mesh->nmacro(); ++m) {
@@ -1181,9 +1438,9 @@ extern "C" int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, 
       for (int z = 0; z < 16; ++z)
         for (int t = 0; t < kP2StTotal; ++t) w32[m].w[z][t] = (float)w64[m].w[z][t];
     HHG_CUDA_TRY(cudaMalloc(&op->d_p2idx, sizeof(P2StencilIndex)));
+    HHG_CUDA_TRY(cudaMemcpy(op->d_p2idx, &ix, sizeof(P2StencilIndex), cudaMemcpyHostToDevice));
     HHG_CUDA_TRY(cudaMalloc(&op->d_p2st64, sizeof(P2Stencil<double>) * nm));
     HHG_CUDA_TRY(cudaMalloc(&op->d_p2st32, sizeof(P2Stencil<float>) * nm));
-    HHG_CUDA_TRY(cudaMemcpy(op->d_p2idx, &ix, sizeof(P2StencilIndex), cudaMemcpyHostToDevice));
     HHG_CUDA_TRY(cudaMemcpy(op->d_p2st64, w64.data(), sizeof(P2Stencil<double>) * nm, cudaMemcpyHostToDevice));
     HHG_CUDA_TRY(cudaMemcpy(op->d_p2st32, w32.data(), sizeof(P2Stencil<float>) * nm, cudaMemcpyHostToDevice));
   }
