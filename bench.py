@@ -254,8 +254,11 @@ def run_const_legs(hhg, torch, flush, peak_gbs: float, reps: int = 5):
             y = torch.empty_like(x)
             ms = time_apply(torch, lambda: op.apply(x, out=y), flush, reps)
             nbytes = 2 * x.numel() * x.element_size()
-            out["%s_%s" % (name, dt)] = {"level": level, "ms": ms, "mdofs": inner / ms / 1e3,
-                                         "gbs": nbytes / ms / 1e6, "hbm_frac": nbytes / ms / 1e6 / peak_gbs}
+            key = "%s_%s" % (name, dt)
+            tr = load_traffic().get(key)
+            out[key] = {"level": level, "ms": ms, "mdofs": inner / ms / 1e3, "gbs": nbytes / ms / 1e6,
+                        "hbm_frac": nbytes / ms / 1e6 / peak_gbs, "bytes": nbytes,
+                        "traffic": tr["bytes_per_launch"] if tr else None}
             del x, y
         del op, mesh
     return out
@@ -308,7 +311,28 @@ def run_n1(hhg, torch, flush, level: int = 7, reps: int = 3):
         y = torch.empty_like(x)
         ms = time_apply(torch, lambda: op.apply(x, out=y), flush, reps)
         out[dt] = {"ms": ms, "mdofs": n_edges_interior / ms / 1e3, "interior_edges": n_edges_interior}
+        if dt == "f64":
+            tr = load_traffic().get("n1_f64")
+            out[dt]["traffic"] = tr["bytes_per_launch"] if tr else None
         del op, x, y
+    return out
+
+
+def run_underint(hhg, torch, flush, level: int = 8, reps: int = 3):
+    """P2 with the analytic coefficient under-integrated by the degree-2 (4-point) rule, the
+    paper's under-integration variant (Section 6.7), reference macro at level 8."""
+    import workloads as W
+    v, t = W.reference_tet()
+    mesh = hhg.Mesh(v, t, level)
+    op = hhg.Operator(mesh, degree=2, coeff=("sin3",), bc="dirichlet", quad_degree=2)
+    tot, inner = mesh.dof_count(2)
+    out = {"workload": "reference macro, level %d, P2, sin3 coefficient at the 4-point degree-2 rule" % level}
+    for dt, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+        x = torch.from_numpy(W.uniform(mesh.vec_size(2), seed=0)).to("cuda", tdt)
+        y = torch.empty_like(x)
+        ms = time_apply(torch, lambda: op.apply(x, out=y), flush, reps)
+        out[dt] = {"ms": ms, "mdofs": inner / ms / 1e3}
+        del x, y
     return out
 
 
@@ -488,6 +512,8 @@ def main():
         extra["epsilon"] = run_eps(hhg, torch, flush)
         torch.cuda.empty_cache()
         extra["n1"] = run_n1(hhg, torch, flush)
+        torch.cuda.empty_cache()
+        extra["under_integration"] = run_underint(hhg, torch, flush)
         torch.cuda.empty_cache()
     fmg = None
     if not args.no_fmg:
