@@ -45,15 +45,17 @@ struct TransferTables {
   int R = 0;
   int npos = 0;
   int* d_pos_cls = nullptr;        // npos
+  int* d_pos_off = nullptr;        // npos x 10: node position in the coarse cube block, q0 | q1 << 4 | q2 << 8
   double* d_pos_w64 = nullptr;     // npos x 10
   float* d_pos_w32 = nullptr;
   int ntypes = 0;
   int* d_st_ptr = nullptr;         // ntypes + 1
-  int* d_st_off = nullptr;         // 3 per entry
+  int* d_st_off = nullptr;         // per entry (dx + 8) | (dy + 8) << 5 | (dz + 8) << 10
   double* d_st_w64 = nullptr;
   float* d_st_w32 = nullptr;
   ~TransferTables() {
     cudaFree(d_pos_cls);
+    cudaFree(d_pos_off);
     cudaFree(d_pos_w64);
     cudaFree(d_pos_w32);
     cudaFree(d_st_ptr);
@@ -141,15 +143,22 @@ static int build_transfer_tables(int R, TransferTables* T) {
             if (R * c[0] + p[0] == C[0] && R * c[1] + p[1] == C[1] && R * c[2] + p[2] == C[2]) wsum += w64[10 * t + node];
           }
           if (std::fabs(wsum) > 1e-14) {
-            st_off.push_back(dx);
-            st_off.push_back(dy);
-            st_off.push_back(dz);
+            st_off.push_back((dx + 8) | ((dy + 8) << 5) | ((dz + 8) << 10));
             st_w.push_back(wsum);
           }
         }
     st_ptr.push_back((int)st_w.size());
   }
   T->ntypes = ntypes;
+  std::vector<int> poff(T->npos * 10, 0);
+  for (int t = 0; t < T->npos; ++t)
+    for (int node = 0; node < nloc; ++node) {
+      int p[3];
+      node_pos(R, cls[t], node, p);
+      poff[10 * t + node] = p[0] | (p[1] << 4) | (p[2] << 8);
+    }
+  HHG_CUDA_TRY(cudaMalloc(&T->d_pos_off, sizeof(int) * poff.size()));
+  HHG_CUDA_TRY(cudaMemcpy(T->d_pos_off, poff.data(), sizeof(int) * poff.size(), cudaMemcpyHostToDevice));
   std::vector<float> w32(w64.begin(), w64.end()), sw32(st_w.begin(), st_w.end());
   HHG_CUDA_TRY(cudaMalloc(&T->d_pos_cls, sizeof(int) * cls.size()));
   HHG_CUDA_TRY(cudaMalloc(&T->d_pos_w64, sizeof(double) * w64.size()));
@@ -201,41 +210,46 @@ struct LevelArgs {
 };
 
 template <typename T, int R>
-__global__ void __launch_bounds__(256) prolongate_kernel(LevelArgs fine, LevelArgs coarse, const MacroGeom* __restrict__ mg,
-                                                          const int* __restrict__ pos_cls, const T* __restrict__ pos_w,
-                                                          const T* __restrict__ xc, T* __restrict__ xf) {
+__global__ void __launch_bounds__(256) prolongate_kernel(LevelArgs fine, LevelArgs coarse, const int* __restrict__ pos_off,
+                                                          const T* __restrict__ pos_w, const T* __restrict__ xc,
+                                                          T* __restrict__ xf) {
   constexpr int W = 2 * R + 1;
+  constexpr int NL = R == 1 ? 4 : 10;
   int i, j, k, p;
   if (!plane_point(fine.N, fine.cta_plane, fine.cta_start, fine.pstart, i, j, k, p)) return;
   const int m = blockIdx.y;
   const int nc = coarse.N / R;            // coarse cubes per edge
-  int c[3] = {i / (2 * R), j / (2 * R), k / (2 * R)};
-  int a[3] = {i - 2 * R * c[0], j - 2 * R * c[1], k - 2 * R * c[2]};
-  if (c[0] + c[1] + c[2] > nc - 1) {
+  int c0 = i / (2 * R), c1 = j / (2 * R), c2 = k / (2 * R);
+  int a0 = i - 2 * R * c0, a1 = j - 2 * R * c1, a2 = k - 2 * R * c2;
+  if (c0 + c1 + c2 > nc - 1) {
     // a coarse vertex on the top face of the macro: take it from the cube below it
-    const int d = c[0] > 0 ? 0 : (c[1] > 0 ? 1 : 2);
-    c[d] -= 1;
-    a[d] += 2 * R;
-  }
-  const int t = a[0] + W * (a[1] + W * a[2]);
-  const int o = __ldg(pos_cls + t);
-  const T* w = pos_w + 10 * t;
-  const T* xm = xc + (int64_t)m * coarse.V;
-  T acc = T(0);
-  const int nloc = R == 1 ? 4 : 10;
-  for (int node = 0; node < nloc; ++node) {
-    int q[3];
-    for (int d = 0; d < 3; ++d) {
-      if (R == 1 || node < 4)
-        q[d] = R * kClassOffsetsD[o][node][d];
-      else
-        q[d] = kClassOffsetsD[o][kP2EdgesD[node - 4][0]][d] + kClassOffsetsD[o][kP2EdgesD[node - 4][1]][d];
+    if (c0 > 0) {
+      c0 -= 1;
+      a0 += 2 * R;
+    } else if (c1 > 0) {
+      c1 -= 1;
+      a1 += 2 * R;
+    } else {
+      c2 -= 1;
+      a2 += 2 * R;
     }
-    const int ci = R * c[0] + q[0], cj = R * c[1] + q[1], ck = R * c[2] + q[2];
-    const T wv = __ldg(w + node);
-    if (wv != T(0)) acc += wv * __ldg(xm + __ldg(coarse.pstart + ck) + rowst32(coarse.N - ck, cj) + ci);
   }
-  (void)mg;
+  const int t = a0 + W * (a1 + W * a2);
+  const T* __restrict__ xm = xc + (int64_t)m * coarse.V;
+  // the nodes of the containing coarse micro-tet lie in the planes R c2 .. R c2 + R
+  int ps[R + 1];
+#pragma unroll
+  for (int dz = 0; dz <= R; ++dz) ps[dz] = __ldg(coarse.pstart + R * c2 + dz);
+  T acc = T(0);
+#pragma unroll
+  for (int node = 0; node < NL; ++node) {
+    const int q = __ldg(pos_off + 10 * t + node);
+    const T wv = __ldg(pos_w + 10 * t + node);
+    const int dz = q >> 8;
+    const int ci = R * c0 + (q & 15), cj = R * c1 + ((q >> 4) & 15), ck = R * c2 + dz;
+    const int pk = (R == 2 && dz == 2) ? ps[R] : (dz >= 1 ? ps[1] : ps[0]);
+    acc += wv * __ldg(xm + pk + rowst32(coarse.N - ck, cj) + ci);
+  }
   xf[(int64_t)m * fine.V + p] = acc;
 }
 
@@ -255,11 +269,11 @@ __global__ void __launch_bounds__(256) restrict_kernel(LevelArgs fine, LevelArgs
   }
   const int type = R == 1 ? 0 : ((i & 1) | ((j & 1) << 1) | ((k & 1) << 2));
   const int Nf = fine.N;
-  const T* rm = rf + (int64_t)m * fine.V;
+  const T* __restrict__ rm = rf + (int64_t)m * fine.V;
   T acc = T(0);
   for (int e = __ldg(st_ptr + type); e < __ldg(st_ptr + type + 1); ++e) {
-    const int fi = 2 * i + __ldg(st_off + 3 * e), fj = 2 * j + __ldg(st_off + 3 * e + 1),
-              fk = 2 * k + __ldg(st_off + 3 * e + 2);
+    const int o = __ldg(st_off + e);
+    const int fi = 2 * i + (o & 31) - 8, fj = 2 * j + ((o >> 5) & 31) - 8, fk = 2 * k + ((o >> 10) & 31) - 8;
     if (fi < 0 || fj < 0 || fk < 0 || fi + fj + fk > Nf) continue;
     if (!((own >> zero_mask(Nf, fi, fj, fk)) & 1u)) continue;   // a copy owned by another macro
     acc += __ldg(st_w + e) * __ldg(rm + __ldg(fine.pstart + fk) + rowst32(Nf - fk, fj) + fi);
@@ -443,9 +457,9 @@ static int do_prolongate(hhg_mesh* mesh, int lf, int degree, const T* xc, T* xf,
   LevelArgs F = level_args(If, degree << lf), C = level_args(Ic, degree << (lf - 1));
   dim3 grid((unsigned)If->ncta, mesh->nmacro());
   if (degree == 1)
-    prolongate_kernel<T, 1><<<grid, 256, 0, s>>>(F, C, mesh->d_macros, TT->d_pos_cls, pos_w<T>(TT), xc, xf);
+    prolongate_kernel<T, 1><<<grid, 256, 0, s>>>(F, C, TT->d_pos_off, pos_w<T>(TT), xc, xf);
   else
-    prolongate_kernel<T, 2><<<grid, 256, 0, s>>>(F, C, mesh->d_macros, TT->d_pos_cls, pos_w<T>(TT), xc, xf);
+    prolongate_kernel<T, 2><<<grid, 256, 0, s>>>(F, C, TT->d_pos_off, pos_w<T>(TT), xc, xf);
   HHG_CUDA_TRY(cudaGetLastError());
   return launch_make_consistent<T>(If, xf, 1, s);
 }

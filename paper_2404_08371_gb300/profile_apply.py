@@ -31,7 +31,8 @@ def main():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
-    ap.add_argument("--op", default="apply", choices=["apply", "adjoint", "diagonal"])
+    ap.add_argument("--op", default="apply", choices=["apply", "adjoint", "diagonal", "mg"])
+    ap.add_argument("--mixed", type=int, default=1, help="--op mg: FP32 cycles inside FP64 refinement (1) or all FP64 (0)")
     args = ap.parse_args()
 
     import torch
@@ -74,6 +75,16 @@ def main():
     mesh.make_consistent(g, args.degree, per_point=ncomp * args.nrhs)
     y = torch.empty_like(x)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    if args.op == "mg":
+        # FMG + V(2,2) solve of the manufactured Poisson problem (the operator must be DIRICHLET diffusion)
+        b = mesh.rhs_sin3_poisson(args.degree)
+        for _ in range(args.warmup):
+            op.mg_solve(b, torch.zeros_like(b), mixed=args.mixed)
+        sts = [op.mg_solve(b, torch.zeros_like(b), mixed=args.mixed)[1] for _ in range(args.reps)]
+        print(json.dumps({"config": vars(args), "solve_ms": [st["solve_ms"] for st in sts],
+                          "iterations": sts[-1]["iterations"], "rel_residual": sts[-1]["rel_residual"]}))
+        return
 
     def once():
         if args.op == "apply":
