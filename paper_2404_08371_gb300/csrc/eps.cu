@@ -34,16 +34,18 @@ __host__ __device__ constexpr int enode(int o, int a, int d) {
   return a < 4 ? 2 * eoff(o, a, d) : eoff(o, eedge(a - 4, 0), d) + eoff(o, eedge(a - 4, 1), d);
 }
 
+// grad_ref u of one component at a quadrature point from its 10 nodal values, and the test
+// y_i += r . grad_ref phi_i, with 4 lambda and 4 lambda - 1 tabulated per point.
 template <typename T>
-__device__ __forceinline__ void ref_grad10(const T* u, const T lam[4], T g[3]) {
+__device__ __forceinline__ void ref_grad10_q(const T* u, const T* L4, const T* L4m1, T g[3]) {
   T s[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) s[a] = u[a] * (T(4) * lam[a] - T(1));
+  for (int a = 0; a < 4; ++a) s[a] = u[a] * L4m1[a];
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
     const int a = eedge(e, 0), b = eedge(e, 1);
-    s[a] += T(4) * u[4 + e] * lam[b];
-    s[b] += T(4) * u[4 + e] * lam[a];
+    s[a] = fma(u[4 + e], L4[b], s[a]);
+    s[b] = fma(u[4 + e], L4[a], s[b]);
   }
   g[0] = s[1] - s[0];
   g[1] = s[2] - s[0];
@@ -51,14 +53,14 @@ __device__ __forceinline__ void ref_grad10(const T* u, const T lam[4], T g[3]) {
 }
 
 template <typename T>
-__device__ __forceinline__ void ref_test10(const T r[3], const T lam[4], T* y) {
+__device__ __forceinline__ void ref_test10_q(const T r[3], const T* L4, const T* L4m1, T* y) {
   const T rho[4] = {-(r[0] + r[1] + r[2]), r[0], r[1], r[2]};
 #pragma unroll
-  for (int a = 0; a < 4; ++a) y[a] += (T(4) * lam[a] - T(1)) * rho[a];
+  for (int a = 0; a < 4; ++a) y[a] = fma(L4m1[a], rho[a], y[a]);
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
     const int a = eedge(e, 0), b = eedge(e, 1);
-    y[4 + e] += T(4) * (lam[a] * rho[b] + lam[b] * rho[a]);
+    y[4 + e] = fma(L4[a], rho[b], fma(L4[b], rho[a], y[4 + e]));
   }
 }
 
@@ -116,12 +118,13 @@ __global__ void __launch_bounds__(256) eps_color_kernel(const OpConst<T>* __rest
       dmu[a] = T(0);
     }
     for (int q = 0; q < c.nq; ++q) {
-      const T lam[4] = {c.lam[q][0], c.lam[q][1], c.lam[q][2], c.lam[q][3]};
+      const T* L4 = c.lam4[q];
+      const T* L4m1 = c.lam4m1[q];
       T G[3][3];
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) {
         T gh[3];
-        ref_grad10<T>(u[cc], lam, gh);
+        ref_grad10_q<T>(u[cc], L4, L4m1, gh);
         phys_grad<T>(Ji, gh, G[cc]);
       }
       if (MODE == 0) {
@@ -137,14 +140,14 @@ __global__ void __launch_bounds__(256) eps_color_kernel(const OpConst<T>* __rest
           for (int d = 0; d < 3; ++d) Sc[d] = s * (G[cc][d] + G[d][cc]);
 #pragma unroll
           for (int e = 0; e < 3; ++e) rr[e] = Ji[e * 3 + 0] * Sc[0] + Ji[e * 3 + 1] * Sc[1] + Ji[e * 3 + 2] * Sc[2];
-          ref_test10<T>(rr, lam, y[cc]);
+          ref_test10_q<T>(rr, L4, L4m1, y[cc]);
         }
       } else {
         T Gg[3][3];
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
           T gh[3];
-          ref_grad10<T>(gv[cc], lam, gh);
+          ref_grad10_q<T>(gv[cc], L4, L4m1, gh);
           phys_grad<T>(Ji, gh, Gg[cc]);
         }
         T tq = T(0);

@@ -147,6 +147,8 @@ struct alignas(16) OpConst {
   int nq;
   T w[kMaxQ];
   T lam[kMaxQ][4];
+  T lam4[kMaxQ][4];      // 4 lambda_a and 4 lambda_a - 1 at the points (P2 gradients)
+  T lam4m1[kMaxQ][4];
   T psi[kMaxQ][10];
   T cs[6][kMaxQ][3][2];
   T qoff[6][kMaxQ][3];   // physical offset delta of point q of class o from the cube origin

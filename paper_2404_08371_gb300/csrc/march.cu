@@ -70,33 +70,33 @@ __device__ __forceinline__ T shfl_down(T v) {
   return __shfl_down_sync(0xffffffffu, v, 1);
 }
 
-// grad_ref u at quadrature point q from the 10 P2 nodal values.
+// grad_ref u at a quadrature point from the 10 P2 nodal values, and y_i += r . grad_ref phi_i, with
+// 4 lambda and 4 lambda - 1 tabulated per quadrature point (19 FP64 operations each).
 template <typename T>
-__device__ __forceinline__ void p2_ref_grad(const T* u, const T lam[4], T g[3]) {
+__device__ __forceinline__ void p2_ref_grad_q(const T* u, const T* L4, const T* L4m1, T g[3]) {
   T s[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) s[a] = u[a] * (T(4) * lam[a] - T(1));
+  for (int a = 0; a < 4; ++a) s[a] = u[a] * L4m1[a];
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
     const int a = edge_end(e, 0), b = edge_end(e, 1);
-    s[a] += T(4) * u[4 + e] * lam[b];
-    s[b] += T(4) * u[4 + e] * lam[a];
+    s[a] = fma(u[4 + e], L4[b], s[a]);
+    s[b] = fma(u[4 + e], L4[a], s[b]);
   }
   g[0] = s[1] - s[0];
   g[1] = s[2] - s[0];
   g[2] = s[3] - s[0];
 }
 
-// y_i += r . grad_ref phi_i at the point with barycentric coordinates lam.
 template <typename T>
-__device__ __forceinline__ void p2_ref_test(const T r[3], const T lam[4], T* y) {
+__device__ __forceinline__ void p2_ref_test_q(const T r[3], const T* L4, const T* L4m1, T* y) {
   const T rho[4] = {-(r[0] + r[1] + r[2]), r[0], r[1], r[2]};   // r . grad lambda_a
 #pragma unroll
-  for (int a = 0; a < 4; ++a) y[a] += (T(4) * lam[a] - T(1)) * rho[a];
+  for (int a = 0; a < 4; ++a) y[a] = fma(L4m1[a], rho[a], y[a]);
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
     const int a = edge_end(e, 0), b = edge_end(e, 1);
-    y[4 + e] += T(4) * (lam[a] * rho[b] + lam[b] * rho[a]);
+    y[4 + e] = fma(L4[a], rho[b], fma(L4[b], rho[a], y[4 + e]));
   }
 }
 
@@ -337,7 +337,6 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
           const T* M = c.M[o];
 #pragma unroll 2
           for (int q = 0; q < c.nq; ++q) {
-            const T lam[4] = {c.lam[q][0], c.lam[q][1], c.lam[q][2], c.lam[q][3]};
             T kq;
             if (COEF == HHG_COEFF_SIN3) {
               T sv[3];
@@ -351,13 +350,13 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
             }
             if (MODE == MODE_APPLY) {
               T gr[3], r[3];
-              p2_ref_grad<T>(ul, lam, gr);
+              p2_ref_grad_q<T>(ul, c.lam4[q], c.lam4m1[q], gr);
               metric<T>(M, gr, r);
               const T s = kq * c.w[q];
               r[0] *= s;
               r[1] *= s;
               r[2] *= s;
-              p2_ref_test<T>(r, lam, yl);
+              p2_ref_test_q<T>(r, c.lam4[q], c.lam4m1[q], yl);
             } else if (MODE == MODE_DIAG) {
               // grad_ref phi_a . M grad_ref phi_a for every node a
               const T s = kq * c.w[q];
@@ -367,14 +366,14 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
 #pragma unroll
                 for (int b = 0; b < 10; ++b) e[b] = T(a == b ? 1 : 0);
                 T gr[3], r[3];
-                p2_ref_grad<T>(e, lam, gr);
+                p2_ref_grad_q<T>(e, c.lam4[q], c.lam4m1[q], gr);
                 metric<T>(M, gr, r);
                 yl[a] += s * (gr[0] * r[0] + gr[1] * r[1] + gr[2] * r[2]);
               }
             } else {
               T gu[3], gg[3], r[3];
-              p2_ref_grad<T>(ul, lam, gu);
-              p2_ref_grad<T>(gl, lam, gg);
+              p2_ref_grad_q<T>(ul, c.lam4[q], c.lam4m1[q], gu);
+              p2_ref_grad_q<T>(gl, c.lam4[q], c.lam4m1[q], gg);
               metric<T>(M, gu, r);
               const T t = c.w[q] * (gg[0] * r[0] + gg[1] * r[1] + gg[2] * r[2]);
 #pragma unroll

@@ -135,6 +135,8 @@ static void build_const(hhg_op* op) {
       c.w[q] = rq.w[q];
       for (int a = 0; a < 4; ++a) {
         c.lam[q][a] = lam[a];
+        c.lam4[q][a] = 4.0 * lam[a];
+        c.lam4m1[q][a] = 4.0 * lam[a] - 1.0;
         c.psi[q][a] = lam[a] * (2.0 * lam[a] - 1.0);
       }
       for (int e = 0; e < 6; ++e) c.psi[q][4 + e] = 4.0 * lam[kP2Edges[e][0]] * lam[kP2Edges[e][1]];
@@ -225,7 +227,11 @@ static OpConst<T> convert_const(const OpConst<double>& c) {
   o.nq = c.nq;
   for (int q = 0; q < kMaxQ; ++q) {
     o.w[q] = (T)c.w[q];
-    for (int a = 0; a < 4; ++a) o.lam[q][a] = (T)c.lam[q][a];
+    for (int a = 0; a < 4; ++a) {
+      o.lam[q][a] = (T)c.lam[q][a];
+      o.lam4[q][a] = (T)c.lam4[q][a];
+      o.lam4m1[q][a] = (T)c.lam4m1[q][a];
+    }
     for (int m = 0; m < 10; ++m) o.psi[q][m] = (T)c.psi[q][m];
     for (int cl = 0; cl < 6; ++cl)
       for (int d = 0; d < 3; ++d) {
