@@ -71,7 +71,8 @@ __device__ __forceinline__ T shfl_down(T v) {
 }
 
 // grad_ref u at a quadrature point from the 10 P2 nodal values, and y_i += r . grad_ref phi_i, with
-// 4 lambda and 4 lambda - 1 tabulated per quadrature point (19 FP64 operations each).
+// 4 lambda and 4 lambda - 1 tabulated per quadrature point (19 FP64 operations each); used for rules
+// of few points, where the per-element set-up of the affine form below does not pay.
 template <typename T>
 __device__ __forceinline__ void p2_ref_grad_q(const T* u, const T* L4, const T* L4m1, T g[3]) {
   T s[4];
@@ -100,6 +101,100 @@ __device__ __forceinline__ void p2_ref_test_q(const T r[3], const T* L4, const T
   }
 }
 
+// The reference gradient of a P2 function is affine in the barycentric coordinates:
+// grad_ref u(lambda) = W0 + lambda_1 W1 + lambda_2 W2 + lambda_3 W3, with W formed once per
+// micro-tet from W'_c = 4 u_c g_c + 4 sum_{edges (c, b)} u_(c,b) g_b - sum_a u_a g_a (g_a = grad_ref
+// lambda_a), W0 = W'_0 and Wc = W'_c - W'_0; a quadrature point then costs 9 FMA.
+template <int B, typename T>
+__device__ __forceinline__ void add_gref(T v[3], T f) {
+  if (B == 0) {
+    v[0] -= f;
+    v[1] -= f;
+    v[2] -= f;
+  } else {
+    v[B - 1] += f;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void p2_grad_affine(const T* u, T W[4][3]) {
+  const T U[3] = {u[1] - u[0], u[2] - u[0], u[3] - u[0]};
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) W[a][d] = -U[d];
+  add_gref<0>(W[0], T(4) * u[0]);
+  add_gref<1>(W[1], T(4) * u[1]);
+  add_gref<2>(W[2], T(4) * u[2]);
+  add_gref<3>(W[3], T(4) * u[3]);
+  // edges (0,1) (0,2) (0,3) (1,2) (1,3) (2,3): W'_a += 4 u_e g_b, W'_b += 4 u_e g_a
+  {
+    const T f = T(4) * u[4];
+    add_gref<1>(W[0], f);
+    add_gref<0>(W[1], f);
+  }
+  {
+    const T f = T(4) * u[5];
+    add_gref<2>(W[0], f);
+    add_gref<0>(W[2], f);
+  }
+  {
+    const T f = T(4) * u[6];
+    add_gref<3>(W[0], f);
+    add_gref<0>(W[3], f);
+  }
+  {
+    const T f = T(4) * u[7];
+    add_gref<2>(W[1], f);
+    add_gref<1>(W[2], f);
+  }
+  {
+    const T f = T(4) * u[8];
+    add_gref<3>(W[1], f);
+    add_gref<1>(W[3], f);
+  }
+  {
+    const T f = T(4) * u[9];
+    add_gref<3>(W[2], f);
+    add_gref<2>(W[3], f);
+  }
+#pragma unroll
+  for (int c = 1; c < 4; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) W[c][d] -= W[0][d];
+}
+
+template <typename T>
+__device__ __forceinline__ void p2_grad_at(const T W[4][3], T l1, T l2, T l3, T g[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) g[d] = fma(l3, W[3][d], fma(l2, W[2][d], fma(l1, W[1][d], W[0][d])));
+}
+
+// Testing against the P2 basis over all quadrature points through the moments
+// S_ab = sum_q lambda_b rho_a and R_a = sum_q rho_a of rho_a = r . g_a (a, b = 1..3 accumulated):
+// y_a += 4 S_aa - R_a for a vertex, y_(a,b) += 4 (S_ab + S_ba) for an edge.
+template <typename T>
+__device__ __forceinline__ void p2_test_moments(const T S3[3][3], const T R3[3], T* y) {
+  T S[4][4], R[4];
+#pragma unroll
+  for (int a = 1; a < 4; ++a) {
+    R[a] = R3[a - 1];
+#pragma unroll
+    for (int b = 1; b < 4; ++b) S[a][b] = S3[a - 1][b - 1];
+    S[a][0] = R[a] - S[a][1] - S[a][2] - S[a][3];   // lambda_0 = 1 - lambda_1 - lambda_2 - lambda_3
+  }
+  R[0] = -(R[1] + R[2] + R[3]);                      // g_0 = -(g_1 + g_2 + g_3)
+#pragma unroll
+  for (int b = 0; b < 4; ++b) S[0][b] = -(S[1][b] + S[2][b] + S[3][b]);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) y[a] += T(4) * S[a][a] - R[a];
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const int a = edge_end(e, 0), b = edge_end(e, 1);
+    y[4 + e] += T(4) * (S[a][b] + S[b][a]);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void metric(const T* M, const T g[3], T r[3]) {
   r[0] = M[0] * g[0] + M[3] * g[1] + M[4] * g[2];
@@ -118,7 +213,9 @@ __device__ __forceinline__ void sincos2pi<float>(float x, float* s, float* c) {
   sincospif(2.0f * x, s, c);
 }
 
-template <typename T, int R, int COEF, int MODE, bool DIR>
+// AFF (P2, variable coefficient, APPLY): affine gradient + moment test (rules of many points) or the
+// tabulated direct form (rules of few points).
+template <typename T, int R, int COEF, int MODE, bool DIR, bool AFF = true>
 __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __restrict__ cst,
                                                             const int4* __restrict__ tasks, int kChunk,
                                                             const T* __restrict__ x, const T* __restrict__ g,
@@ -335,6 +432,19 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
             for (int a = 0; a < 10; ++a) gl[a] = gb[node_slot<R>(o, a)];
           }
           const T* M = c.M[o];
+          constexpr bool affine = AFF;
+          T Wu[4][3], Wg[4][3];
+          T S3[3][3], R3[3];
+          if ((MODE == MODE_APPLY && affine) || MODE == MODE_ADJ) {
+            p2_grad_affine<T>(ul, Wu);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              R3[a] = T(0);
+#pragma unroll
+              for (int b = 0; b < 3; ++b) S3[a][b] = T(0);
+            }
+          }
+          if (MODE == MODE_ADJ) p2_grad_affine<T>(gl, Wg);
 #pragma unroll 2
           for (int q = 0; q < c.nq; ++q) {
             T kq;
@@ -348,7 +458,7 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
 #pragma unroll
               for (int m = 0; m < 10; ++m) kq += c.psi[q][m] * kb[node_slot<R>(o, m)];
             }
-            if (MODE == MODE_APPLY) {
+            if (MODE == MODE_APPLY && !affine) {
               T gr[3], r[3];
               p2_ref_grad_q<T>(ul, c.lam4[q], c.lam4m1[q], gr);
               metric<T>(M, gr, r);
@@ -357,6 +467,20 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
               r[1] *= s;
               r[2] *= s;
               p2_ref_test_q<T>(r, c.lam4[q], c.lam4m1[q], yl);
+            } else if (MODE == MODE_APPLY) {
+              const T l1 = c.lam[q][1], l2 = c.lam[q][2], l3 = c.lam[q][3];
+              T gr[3], r[3];
+              p2_grad_at<T>(Wu, l1, l2, l3, gr);
+              metric<T>(M, gr, r);
+              const T s = kq * c.w[q];
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                const T ra = r[a] * s;
+                R3[a] += ra;
+                S3[a][0] = fma(l1, ra, S3[a][0]);
+                S3[a][1] = fma(l2, ra, S3[a][1]);
+                S3[a][2] = fma(l3, ra, S3[a][2]);
+              }
             } else if (MODE == MODE_DIAG) {
               // grad_ref phi_a . M grad_ref phi_a for every node a
               const T s = kq * c.w[q];
@@ -372,14 +496,15 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
               }
             } else {
               T gu[3], gg[3], r[3];
-              p2_ref_grad_q<T>(ul, c.lam4[q], c.lam4m1[q], gu);
-              p2_ref_grad_q<T>(gl, c.lam4[q], c.lam4m1[q], gg);
+              p2_grad_at<T>(Wu, c.lam[q][1], c.lam[q][2], c.lam[q][3], gu);
+              p2_grad_at<T>(Wg, c.lam[q][1], c.lam[q][2], c.lam[q][3], gg);
               metric<T>(M, gu, r);
               const T t = c.w[q] * (gg[0] * r[0] + gg[1] * r[1] + gg[2] * r[2]);
 #pragma unroll
               for (int m = 0; m < 10; ++m) yl[m] += c.psi[q][m] * t;
             }
           }
+          if (MODE == MODE_APPLY && affine) p2_test_moments<T>(S3, R3, yl);
         }
 #pragma unroll
         for (int a = 0; a < NL; ++a) acc[node_slot<R>(o, a)] += yl[a];
@@ -433,17 +558,17 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
   }
 }
 
-template <typename T, int R, int COEF, int MODE>
+template <typename T, int R, int COEF, int MODE, bool AFF = true>
 static int launch_march_t(const hhg_op* op, const OpConst<T>* cst, const T* x, const T* g, const T* kf, T* out,
                           cudaStream_t s, N1Args<T> n1a = N1Args<T>()) {
   const Interface* I = op->itf;
   const unsigned grid = (unsigned)I->n_march_tasks;
   if (op->bc == HHG_DIRICHLET)
-    march_kernel<T, R, COEF, MODE, true><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x, g, kf,
-                                                                       out, n1a);
+    march_kernel<T, R, COEF, MODE, true, AFF><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x, g,
+                                                                            kf, out, n1a);
   else
-    march_kernel<T, R, COEF, MODE, false><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x, g,
-                                                                        kf, out, n1a);
+    march_kernel<T, R, COEF, MODE, false, AFF><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x,
+                                                                             g, kf, out, n1a);
   HHG_CUDA_TRY(cudaGetLastError());
   return HHG_OK;
 }
@@ -461,8 +586,15 @@ int launch_march(const hhg_op* op, const OpConst<T>* cst, int mode, const T* x, 
   HHG_MARCH_CASE(1, HHG_COEFF_FIELD_P1, MODE_DIAG)
   HHG_MARCH_CASE(1, HHG_COEFF_FIELD_P1, MODE_ADJ)
   HHG_MARCH_CASE(2, HHG_COEFF_CONST, MODE_APPLY)
-  HHG_MARCH_CASE(2, HHG_COEFF_SIN3, MODE_APPLY)
-  HHG_MARCH_CASE(2, HHG_COEFF_FIELD_P2, MODE_APPLY)
+  // P2 variable coefficient: the affine form pays from about 7 quadrature points on
+  if (op->degree == 2 && mode == MODE_APPLY && (ct == HHG_COEFF_SIN3 || ct == HHG_COEFF_FIELD_P2)) {
+    const bool aff = op->rule.nq() > 6;
+    if (ct == HHG_COEFF_SIN3)
+      return aff ? launch_march_t<T, 2, HHG_COEFF_SIN3, MODE_APPLY, true>(op, cst, x, g, kf, out, s)
+                 : launch_march_t<T, 2, HHG_COEFF_SIN3, MODE_APPLY, false>(op, cst, x, g, kf, out, s);
+    return aff ? launch_march_t<T, 2, HHG_COEFF_FIELD_P2, MODE_APPLY, true>(op, cst, x, g, kf, out, s)
+               : launch_march_t<T, 2, HHG_COEFF_FIELD_P2, MODE_APPLY, false>(op, cst, x, g, kf, out, s);
+  }
   HHG_MARCH_CASE(2, HHG_COEFF_SIN3, MODE_DIAG)
   HHG_MARCH_CASE(2, HHG_COEFF_FIELD_P2, MODE_DIAG)
   HHG_MARCH_CASE(2, HHG_COEFF_FIELD_P2, MODE_ADJ)
