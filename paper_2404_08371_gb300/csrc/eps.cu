@@ -29,38 +29,83 @@ __host__ __device__ constexpr int eedge(int e, int s) {
   constexpr int t[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
   return t[e][s];
 }
-// Doubled-lattice offset of P2 node `a` of class o from 2 * (cube origin).
+// Doubled-lattice offset of P2 node `a` of class o from 2 * (cube origin); in kernels, where o is a
+// run-time value uniform over the warp, from the constant-memory class table.
+__device__ __forceinline__ int enode_d(int o, int a, int d) {
+  return a < 4 ? 2 * kClassOffsetsD[o][a][d]
+               : kClassOffsetsD[o][eedge(a - 4, 0)][d] + kClassOffsetsD[o][eedge(a - 4, 1)][d];
+}
+// The same at compile time.
 __host__ __device__ constexpr int enode(int o, int a, int d) {
   return a < 4 ? 2 * eoff(o, a, d) : eoff(o, eedge(a - 4, 0), d) + eoff(o, eedge(a - 4, 1), d);
 }
 
-// grad_ref u of one component at a quadrature point from its 10 nodal values, and the test
-// y_i += r . grad_ref phi_i, with 4 lambda and 4 lambda - 1 tabulated per point.
-template <typename T>
-__device__ __forceinline__ void ref_grad10_q(const T* u, const T* L4, const T* L4m1, T g[3]) {
-  T s[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) s[a] = u[a] * L4m1[a];
-#pragma unroll
-  for (int e = 0; e < 6; ++e) {
-    const int a = eedge(e, 0), b = eedge(e, 1);
-    s[a] = fma(u[4 + e], L4[b], s[a]);
-    s[b] = fma(u[4 + e], L4[a], s[b]);
+// The reference gradient of a P2 component is affine in the barycentric coordinates:
+// grad_ref u(lambda) = W0 + lambda_1 W1 + lambda_2 W2 + lambda_3 W3, formed once per micro-tet from
+// W'_c = 4 u_c g_c + 4 sum_{edges (c, b)} u_(c,b) g_b - sum_a u_a g_a (g_a = grad_ref lambda_a),
+// W0 = W'_0, Wc = W'_c - W'_0.
+template <int B, typename T>
+__device__ __forceinline__ void eps_add_g(T v[3], T f) {
+  if (B == 0) {
+    v[0] -= f;
+    v[1] -= f;
+    v[2] -= f;
+  } else {
+    v[B - 1] += f;
   }
-  g[0] = s[1] - s[0];
-  g[1] = s[2] - s[0];
-  g[2] = s[3] - s[0];
 }
 
 template <typename T>
-__device__ __forceinline__ void ref_test10_q(const T r[3], const T* L4, const T* L4m1, T* y) {
-  const T rho[4] = {-(r[0] + r[1] + r[2]), r[0], r[1], r[2]};
+__device__ __forceinline__ void eps_grad_affine(const T* u, T W[4][3]) {
+  const T U[3] = {u[1] - u[0], u[2] - u[0], u[3] - u[0]};
 #pragma unroll
-  for (int a = 0; a < 4; ++a) y[a] = fma(L4m1[a], rho[a], y[a]);
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) W[a][d] = -U[d];
+  eps_add_g<0>(W[0], T(4) * u[0]);
+  eps_add_g<1>(W[1], T(4) * u[1]);
+  eps_add_g<2>(W[2], T(4) * u[2]);
+  eps_add_g<3>(W[3], T(4) * u[3]);
+  // edges (0,1) (0,2) (0,3) (1,2) (1,3) (2,3): W'_a += 4 u_e g_b, W'_b += 4 u_e g_a
+  eps_add_g<1>(W[0], T(4) * u[4]);
+  eps_add_g<0>(W[1], T(4) * u[4]);
+  eps_add_g<2>(W[0], T(4) * u[5]);
+  eps_add_g<0>(W[2], T(4) * u[5]);
+  eps_add_g<3>(W[0], T(4) * u[6]);
+  eps_add_g<0>(W[3], T(4) * u[6]);
+  eps_add_g<2>(W[1], T(4) * u[7]);
+  eps_add_g<1>(W[2], T(4) * u[7]);
+  eps_add_g<3>(W[1], T(4) * u[8]);
+  eps_add_g<1>(W[3], T(4) * u[8]);
+  eps_add_g<3>(W[2], T(4) * u[9]);
+  eps_add_g<2>(W[3], T(4) * u[9]);
+#pragma unroll
+  for (int c = 1; c < 4; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) W[c][d] -= W[0][d];
+}
+
+// Testing over all quadrature points through the moments S_ab = sum_q lambda_b rho_a and
+// R_a = sum_q rho_a (a, b = 1..3 given): y_a += 4 S_aa - R_a, y_(a,b) += 4 (S_ab + S_ba).
+template <typename T>
+__device__ __forceinline__ void eps_test_moments(const T S3[3][3], const T R3[3], T* y) {
+  T S[4][4], R[4];
+#pragma unroll
+  for (int a = 1; a < 4; ++a) {
+    R[a] = R3[a - 1];
+#pragma unroll
+    for (int b = 1; b < 4; ++b) S[a][b] = S3[a - 1][b - 1];
+    S[a][0] = R[a] - S[a][1] - S[a][2] - S[a][3];
+  }
+  R[0] = -(R[1] + R[2] + R[3]);
+#pragma unroll
+  for (int b = 0; b < 4; ++b) S[0][b] = -(S[1][b] + S[2][b] + S[3][b]);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) y[a] += T(4) * S[a][a] - R[a];
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
     const int a = eedge(e, 0), b = eedge(e, 1);
-    y[4 + e] = fma(L4[a], rho[b], fma(L4[b], rho[a], y[4 + e]));
+    y[4 + e] += T(4) * (S[a][b] + S[b][a]);
   }
 }
 
@@ -97,7 +142,7 @@ __global__ void __launch_bounds__(256) eps_color_kernel(const OpConst<T>* __rest
     T u[3][10], gv[3][10], m[10];
 #pragma unroll
     for (int a = 0; a < 10; ++a) {
-      const int pi = 2 * ci + enode(o, a, 0), pj = 2 * cj + enode(o, a, 1), pk = 2 * ck + enode(o, a, 2);
+      const int pi = 2 * ci + enode_d(o, a, 0), pj = 2 * cj + enode_d(o, a, 1), pk = 2 * ck + enode_d(o, a, 2);
       idx[a] = tet_ok ? packed_index(N, pi, pj, pk) : 0;
       const bool masked = !tet_ok || (DIR && on_dirichlet(c.bnd_table, N, pi, pj, pk));
 #pragma unroll
@@ -117,39 +162,80 @@ __global__ void __launch_bounds__(256) eps_color_kernel(const OpConst<T>* __rest
       y[0][a] = y[1][a] = y[2][a] = T(0);
       dmu[a] = T(0);
     }
-    for (int q = 0; q < c.nq; ++q) {
-      const T* L4 = c.lam4[q];
-      const T* L4m1 = c.lam4m1[q];
-      T G[3][3];
+    // physical gradients of the components, affine in lambda: G_c = P[c][0] + sum_b lambda_b P[c][b]
+    T P[3][4][3];
 #pragma unroll
-      for (int cc = 0; cc < 3; ++cc) {
-        T gh[3];
-        ref_grad10_q<T>(u[cc], L4, L4m1, gh);
-        phys_grad<T>(Ji, gh, G[cc]);
-      }
-      if (MODE == 0) {
+    for (int cc = 0; cc < 3; ++cc) {
+      T W[4][3];
+      eps_grad_affine<T>(u[cc], W);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) phys_grad<T>(Ji, W[t], P[cc][t]);
+    }
+    if (MODE == 0) {
+      // physical moments of the stress: Q[c][0] = sum_q S_c, Q[c][b] = sum_q lambda_b S_c
+      T Q[3][4][3];
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) Q[cc][t][d] = T(0);
+      for (int q = 0; q < c.nq; ++q) {
+        const T l1 = c.lam[q][1], l2 = c.lam[q][2], l3 = c.lam[q][3];
+        T G[3][3];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            G[cc][d] = fma(l3, P[cc][3][d], fma(l2, P[cc][2][d], fma(l1, P[cc][1][d], P[cc][0][d])));
         T muq = T(0);
 #pragma unroll
         for (int a = 0; a < 10; ++a) muq += c.psi[q][a] * m[a];
         const T s = muq * c.w[q] * wdet;
-        // S = s (G + G^T) = 2 mu eps(u) w |det J|;  y_c += (J^{-1} S_c) . grad_ref phi
+        // S = s (G + G^T) = 2 mu eps(u) w |det J|
 #pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          T Sc[3], rr[3];
+        for (int cc = 0; cc < 3; ++cc)
 #pragma unroll
-          for (int d = 0; d < 3; ++d) Sc[d] = s * (G[cc][d] + G[d][cc]);
+          for (int d = 0; d < 3; ++d) {
+            const T Sd = s * (G[cc][d] + G[d][cc]);
+            Q[cc][0][d] += Sd;
+            Q[cc][1][d] = fma(l1, Sd, Q[cc][1][d]);
+            Q[cc][2][d] = fma(l2, Sd, Q[cc][2][d]);
+            Q[cc][3][d] = fma(l3, Sd, Q[cc][3][d]);
+          }
+      }
+      // y_c += sum_q (J^{-1} S_c) . grad_ref phi: map the moments back once, then test
 #pragma unroll
-          for (int e = 0; e < 3; ++e) rr[e] = Ji[e * 3 + 0] * Sc[0] + Ji[e * 3 + 1] * Sc[1] + Ji[e * 3 + 2] * Sc[2];
-          ref_test10_q<T>(rr, L4, L4m1, y[cc]);
+      for (int cc = 0; cc < 3; ++cc) {
+        T R3[3], S3[3][3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          R3[e] = Ji[e * 3 + 0] * Q[cc][0][0] + Ji[e * 3 + 1] * Q[cc][0][1] + Ji[e * 3 + 2] * Q[cc][0][2];
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+            S3[e][b] = Ji[e * 3 + 0] * Q[cc][b + 1][0] + Ji[e * 3 + 1] * Q[cc][b + 1][1] + Ji[e * 3 + 2] * Q[cc][b + 1][2];
         }
-      } else {
-        T Gg[3][3];
+        eps_test_moments<T>(S3, R3, y[cc]);
+      }
+    } else {
+      T Pg[3][4][3];
 #pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          T gh[3];
-          ref_grad10_q<T>(gv[cc], L4, L4m1, gh);
-          phys_grad<T>(Ji, gh, Gg[cc]);
-        }
+      for (int cc = 0; cc < 3; ++cc) {
+        T W[4][3];
+        eps_grad_affine<T>(gv[cc], W);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) phys_grad<T>(Ji, W[t], Pg[cc][t]);
+      }
+      for (int q = 0; q < c.nq; ++q) {
+        const T l1 = c.lam[q][1], l2 = c.lam[q][2], l3 = c.lam[q][3];
+        T G[3][3], Gg[3][3];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            G[cc][d] = fma(l3, P[cc][3][d], fma(l2, P[cc][2][d], fma(l1, P[cc][1][d], P[cc][0][d])));
+            Gg[cc][d] = fma(l3, Pg[cc][3][d], fma(l2, Pg[cc][2][d], fma(l1, Pg[cc][1][d], Pg[cc][0][d])));
+          }
         T tq = T(0);
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc)
