@@ -281,6 +281,29 @@ __device__ __noinline__ T p1_face_point(const OpConst<T>& c, const int* __restri
   return acc;
 }
 
+// Row of a P1 point on a macro face: Dirichlet points keep x; a point inside one face uses that
+// face's stencil (neighbours outside the macro drop out); a point on a macro edge or vertex sums its
+// incident micro-tets that exist.
+template <typename T, bool DIRICHLET>
+__device__ __forceinline__ T p1_face_value(const OpConst<T>& c, const int* __restrict__ pstart, const T* __restrict__ xm,
+                                           int i, int j, int k) {
+  const int N = c.N;
+  const uint32_t table = c.bnd_table;
+  if (DIRICHLET && on_dirichlet(table, N, i, j, k)) return xm[__ldg(pstart + k) + row32(N - k, j) + i];
+  const int z = zero_mask(N, i, j, k);
+  if (__popc(z) != 1) return p1_face_point<T, DIRICHLET>(c, pstart, xm, i, j, k);
+  const T* Sf = c.Sface[__ffs(z) - 1];
+  T acc = T(0);
+#pragma unroll
+  for (int d = 0; d < 15; ++d) {
+    const int pi = i + kStencilD[d][0], pj = j + kStencilD[d][1], pkk = k + kStencilD[d][2];
+    if (!inside(N, pi, pj, pkk)) continue;
+    if (DIRICHLET && on_dirichlet(table, N, pi, pj, pkk)) continue;
+    acc += Sf[d] * __ldg(xm + __ldg(pstart + pkk) + row32(N - pkk, pj) + pi);
+  }
+  return acc;
+}
+
 // P1 constant-coefficient apply, one thread per output point (gather).  A CTA covers 256
 // consecutive points of one plane k; the plane of each CTA and the first packed position of each
 // plane come from per-level tables, so the index arithmetic is 32-bit and free of divisions.
@@ -348,27 +371,41 @@ __global__ void __launch_bounds__(256) p1_gather_kernel(const OpConst<T>* __rest
 #pragma unroll
     for (int d = 0; d < 15; ++d) acc += c.S[d] * v[d];
   } else {
-    if (DIRICHLET && on_dirichlet(table, N, i, j, k)) {
-      ym[p] = xm[p];
-      return;
-    }
-    const int z = zero_mask(N, i, j, k);
-    if (__popc(z) == 1) {
-      // inside one macro face: the face's own stencil; neighbours outside the macro drop out
-      const T* Sf = c.Sface[__ffs(z) - 1];
-#pragma unroll
-      for (int d = 0; d < 15; ++d) {
-        const int pi = i + kStencilD[d][0], pj = j + kStencilD[d][1], pkk = k + kStencilD[d][2];
-        if (!inside(N, pi, pj, pkk)) continue;
-        if (DIRICHLET && on_dirichlet(table, N, pi, pj, pkk)) continue;
-        acc += Sf[d] * __ldg(xm + __ldg(pstart + pkk) + row32(N - pkk, pj) + pi);
-      }
-    } else {
-      // on a macro edge or vertex: sum the incident micro-tets that exist
-      acc = p1_face_point<T, DIRICHLET>(c, pstart, xm, i, j, k);
-    }
+    acc = p1_face_value<T, DIRICHLET>(c, pstart, xm, i, j, k);
   }
   ym[p] = acc;
+}
+
+// Points on the faces of the macros for the plane-tile kernel (which writes only the points off the
+// faces), one thread each: face a of the macro has the points (a, b) with a + b <= N of its
+// triangle; a point on several faces is written by the lowest.
+template <typename T, bool DIRICHLET>
+__global__ void __launch_bounds__(256) p1_face_kernel(const OpConst<T>* __restrict__ cst, const int* __restrict__ pstart,
+                                                      const T* __restrict__ x, T* __restrict__ y) {
+  const int macro = blockIdx.z, f = blockIdx.y;
+  const OpConst<T>& c = cst[macro];
+  const int N = c.N;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tri(N)) return;
+  const float bq = 2.0f * N + 3.0f;
+  int b = (int)(0.5f * (bq - sqrtf(fmaxf(bq * bq - 8.0f * (float)t, 0.0f))));
+  b = max(0, min(b, N));
+  if (b < N && row32(N, b + 1) <= t) ++b;
+  if (b > 0 && row32(N, b) > t) --b;
+  const int a = t - row32(N, b);
+  int i, j, k;
+  if (f == 0) {
+    i = 0; j = a; k = b;
+  } else if (f == 1) {
+    i = a; j = 0; k = b;
+  } else if (f == 2) {
+    i = a; j = b; k = 0;
+  } else {
+    i = N - a - b; j = a; k = b;
+  }
+  if ((f >= 1 && i == 0) || (f >= 2 && j == 0) || (f == 3 && k == 0)) return;
+  const T* __restrict__ xm = x + c.base;
+  y[c.base + __ldg(pstart + k) + row32(N - k, j) + i] = p1_face_value<T, DIRICHLET>(c, pstart, xm, i, j, k);
 }
 
 
@@ -600,16 +637,6 @@ __device__ __forceinline__ float2 p1_pair_stencil(const float* W, const float* p
   return acc;
 }
 
-// Scalar stencil of the point at column cc (used next to the macro faces).
-__device__ __forceinline__ float p1_point_stencil(const float* W, const float* pm, const float* p0, const float* pp,
-                                                  int r, int cc) {
-  const int o = r * kPairW + cc;
-  return W[0] * p0[o] + W[1] * p0[o + 1] + W[2] * p0[o - 1] + W[3] * p0[o + kPairW] + W[4] * p0[o - kPairW] +
-         W[5] * pp[o] + W[6] * pm[o] + W[7] * p0[o - kPairW + 1] + W[8] * p0[o + kPairW - 1] + W[9] * pm[o + 1] +
-         W[10] * pp[o - 1] + W[11] * pm[o + kPairW] + W[12] * pp[o - kPairW] + W[13] * pp[o - kPairW + 1] +
-         W[14] * pm[o + kPairW - 1];
-}
-
 template <bool DIRICHLET>
 __global__ void __launch_bounds__(256, 3) p1_tile_f32_kernel(const OpConst<float>* __restrict__ cst,
                                                               const int4* __restrict__ tasks, int kch,
@@ -638,7 +665,10 @@ __global__ void __launch_bounds__(256, 3) p1_tile_f32_kernel(const OpConst<float
     cp_async_commit();
   }
   cp_async_wait<kTileDepth - 1>();
-  if (DIRICHLET) {
+  // a staged plane can hold points of a macro face only if the tile touches i = 0, j = 0, k = 0 or
+  // reaches i + j + k = N; only then are its Dirichlet points looked for (uniform over the CTA)
+  const bool edge_tile = i0 == 0 || j0 == 0 || i0 + kTileI + j0 + kTileJ + k_end + 1 >= N;
+  if (DIRICHLET && (edge_tile || k0 <= 1)) {
     p1_mask_plane_f32(buf, N, table, i0, j0, k0 - 1);
     p1_mask_plane_f32(buf + kPairSlot, N, table, i0, j0, k0);
   }
@@ -647,7 +677,7 @@ __global__ void __launch_bounds__(256, 3) p1_tile_f32_kernel(const OpConst<float
     const int s0 = sm + 1 == kTileRing ? 0 : sm + 1;
     const int sp = s0 + 1 == kTileRing ? 0 : s0 + 1;
     cp_async_wait<kTileDepth - 2>();
-    if (DIRICHLET) p1_mask_plane_f32(buf + sp * kPairSlot, N, table, i0, j0, k + 1);
+    if (DIRICHLET && edge_tile) p1_mask_plane_f32(buf + sp * kPairSlot, N, table, i0, j0, k + 1);
     __syncthreads();
     {
       const int kn = k + kTileDepth;
@@ -660,33 +690,18 @@ __global__ void __launch_bounds__(256, 3) p1_tile_f32_kernel(const OpConst<float
     const float* p0 = buf + s0 * kPairSlot;
     const float* pp = buf + sp * kPairSlot;
     const int len = N - j - k + 1;
-    if (len > 0) {
+    // rows j = 0 and planes k = 0 hold only points on macro faces (written by p1_face_kernel)
+    if (j > 0 && k > 0 && len > 0 && i0 < len) {
       float* __restrict__ yrow = ym + __ldg(pstart + k) + row32(N - k, j);
-      const bool rowface = (j == 0) | (k == 0);
 #pragma unroll
       for (int v = 0; v < kTileI / 64; ++v) {
         const int p2 = lane + 32 * v;
         const int ii = i0 + 2 * p2;
         if (ii >= len) continue;
-        // packed stencil of the pair; points on a macro face are patched below
-        const float2 acc = rowface ? make_float2(0.0f, 0.0f) : p1_pair_stencil(S, pm, p0, pp, r, 2 * p2 + 2);
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int ie = ii + e;
-          if (ie >= len) break;
-          float val = e == 0 ? acc.x : acc.y;
-          const int z = (ie == len - 1) | ((ie == 0) << 1) | ((j == 0) << 2) | ((k == 0) << 3);
-          if (z != 0) {
-            const int cc = 2 * p2 + 2 + e;
-            if (DIRICHLET && ((table >> z) & 1u))
-              val = __ldg(xm + (yrow - ym) + ie);
-            else if (__popc(z) == 1)
-              val = p1_point_stencil(c.Sface[__ffs(z) - 1], pm, p0, pp, r, cc);
-            else
-              val = p1_face_point<float, DIRICHLET>(c, pstart, xm, ie, j, k);
-          }
-          yrow[ie] = val;
-        }
+        const float2 acc = p1_pair_stencil(S, pm, p0, pp, r, 2 * p2 + 2);
+        // only the points off the macro faces (0 < i < len - 1)
+        if (ii > 0 && ii < len - 1) yrow[ii] = acc.x;
+        if (ii + 1 < len - 1) yrow[ii + 1] = acc.y;
       }
     }
     sm = s0;
@@ -906,7 +921,10 @@ __global__ void __launch_bounds__(256) p2_tile_kernel(const OpConst<T>* __restri
     cp_async_commit();
   }
   cp_async_wait<kP2Ahead>();   // planes k0-2 .. k0+1 have arrived
-  if (DIRICHLET) {
+  // a staged plane can hold points of a macro face only if the tile touches i = 0, j = 0, k = 0 or
+  // reaches i + j + k = N; only then are its Dirichlet points looked for (uniform over the CTA)
+  const bool edge_tile = i0 == 0 || j0 == 0 || i0 + TI + 1 + j0 + kP2TileJ + 1 + k_end + 2 >= N;
+  if (DIRICHLET && (edge_tile || k0 <= 2)) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) p2_mask_plane<T, TI>(buf + q * SLOT, N, table, i0, j0, k0 - 2 + q);
   }
@@ -915,7 +933,7 @@ __global__ void __launch_bounds__(256) p2_tile_kernel(const OpConst<T>* __restri
   for (int k = k0; k <= k_end; ++k) {
     const int q = k - k0;   // plane kk sits in ring slot (kk - k0 + 2) mod kP2Ring
     cp_async_wait<kP2Ahead - 1>();   // plane k+2 has arrived
-    if (DIRICHLET) p2_mask_plane<T, TI>(buf + ((q + 4) % kP2Ring) * SLOT, N, table, i0, j0, k + 2);
+    if (DIRICHLET && edge_tile) p2_mask_plane<T, TI>(buf + ((q + 4) % kP2Ring) * SLOT, N, table, i0, j0, k + 2);
     __syncthreads();
     {
       const int kn = k + 2 + kP2Ahead;   // into the slot of plane k-3, read for the last time in step k-1
@@ -1212,12 +1230,16 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
     const unsigned grid = (unsigned)I->tile[0].n;
     const size_t smem = p1_tile_f32_smem();
     const OpConst<float>* cf = (const OpConst<float>*)op->d_const32;
-    if (op->bc == HHG_DIRICHLET)
+    const dim3 fgrid((unsigned)((tri_host(op->N) + 255) / 256), 4, nm);
+    if (op->bc == HHG_DIRICHLET) {
       p1_tile_f32_kernel<true><<<grid, 256, smem, s>>>(cf, I->tile[0].d, I->tile[0].kchunk, I->d_pstart,
                                                        (const float*)x, (float*)y);
-    else
+      p1_face_kernel<float, true><<<fgrid, 256, 0, s>>>(cf, I->d_pstart, (const float*)x, (float*)y);
+    } else {
       p1_tile_f32_kernel<false><<<grid, 256, smem, s>>>(cf, I->tile[0].d, I->tile[0].kchunk, I->d_pstart,
                                                         (const float*)x, (float*)y);
+      p1_face_kernel<float, false><<<fgrid, 256, 0, s>>>(cf, I->d_pstart, (const float*)x, (float*)y);
+    }
     HHG_CUDA_TRY(cudaGetLastError());
     return HHG_OK;
   }
