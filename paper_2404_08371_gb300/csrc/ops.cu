@@ -1245,7 +1245,11 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
   }
   // P2 constant coefficient: stencil rows (28.75 FMA per point against about 74 in element form)
   // from shared-memory plane tiles; 128-point tiles in FP32, 64-point tiles in FP64
-  if (op->kind == HHG_DIFFUSION && op->degree == 2 && op->coeff.type == HHG_COEFF_CONST && op->d_p2st64) {
+  // (small lattices in FP32, the coarse levels of mixed-precision multigrid, run one marching launch
+  // instead: there a launch costs more than the work; in FP64 the few CTAs of a small march would
+  // leave the FP64 pipes of most SMs idle)
+  if (op->kind == HHG_DIFFUSION && op->degree == 2 && op->coeff.type == HHG_COEFF_CONST && op->d_p2st64 &&
+      (sizeof(T) == 8 || op->N > 32)) {
     const Interface* I = op->itf;
     const P2Stencil<T>* st = (const P2Stencil<T>*)(sizeof(T) == 8 ? op->d_p2st64 : op->d_p2st32);
     constexpr int TI = sizeof(T) == 8 ? 64 : 128;
