@@ -139,8 +139,9 @@ int hhg_op_set_field(hhg_op_t* op, const void* field, int field_dtype);
 
 /* y = A x (Eq. 4.1, Algorithm 1 summed over all micro-tets).  x, y: packed
  * vectors of the op's space (ncomp = 3 for EPSILON), nrhs right-hand sides
- * (nrhs >= 1; > 1 only for EPSILON).  y is overwritten; x and y must not
- * overlap.  The apply computes every local matrix on the fly. */
+ * (nrhs >= 1; > 1 only for EPSILON, at most 256, else HHG_E_UNSUPPORTED).
+ * y is overwritten; x and y must not overlap.  The apply computes every
+ * local matrix on the fly. */
 int hhg_op_apply(hhg_op_t* op, const void* x, void* y, int dtype, int nrhs, void* stream);
 
 /* Adjoint in the coefficient of a FIELD operator (A is linear in k):

@@ -13,6 +13,9 @@
 // each (cubes of equal parity share no point, so plain read-modify-write accumulation is race
 // free), one thread per (cube, right-hand side) with the right-hand side fastest so that loads of
 // the [point][component][rhs] layout coalesce.
+#include <algorithm>
+#include <vector>
+
 #include "hhg_internal.h"
 #include "lattice.cuh"
 
@@ -117,20 +120,24 @@ __device__ __forceinline__ void phys_grad(const T* Ji, const T gh[3], T G[3]) {
 }
 
 // MODE 0: out += A u (all right-hand sides); MODE 2: out_m += sum_r g_r^T (dA/dmu_m) u_r.
+// One CTA per task of its colour: up to cpb consecutive cubes of one row (cj, ck) of one macro,
+// times the right-hand sides.
 template <typename T, int MODE, bool FIELD, bool DIR>
-__global__ void __launch_bounds__(256) eps_color_kernel(const OpConst<T>* __restrict__ cst, int color, int nz,
+__global__ void __launch_bounds__(256) eps_color_kernel(const OpConst<T>* __restrict__ cst,
+                                                         const int4* __restrict__ tasks, int color, int cpb,
                                                          int nrhs, T mu_const, const T* __restrict__ x,
                                                          const T* __restrict__ g, const T* __restrict__ mu,
                                                          T* __restrict__ out) {
-  const int macro = blockIdx.z / nz;
+  const int4 task = tasks[blockIdx.x];
+  const int macro = task.w;
   const OpConst<T>& c = cst[macro];
   const int n = c.n, N = c.N;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = threadIdx.x;
   const int r = t % nrhs;
-  const int ci = 2 * (t / nrhs) + (color & 1);
-  const int cj = 2 * blockIdx.y + ((color >> 1) & 1);
-  const int ck = 2 * (blockIdx.z - macro * nz) + ((color >> 2) & 1);
-  const bool live = ci + cj + ck <= n - 1;
+  const int ci = 2 * (task.x + t / nrhs) + (color & 1);
+  const int cj = 2 * task.y + ((color >> 1) & 1);
+  const int ck = 2 * task.z + ((color >> 2) & 1);
+  const bool live = t / nrhs < cpb && ci + cj + ck <= n - 1;
   if (MODE == 0 && !live) return;
   if (MODE == 2 && __all_sync(0xffffffffu, !live)) return;
   const int64_t base = c.base;
@@ -291,11 +298,41 @@ int launch_eps(const hhg_op* op, const OpConst<T>* cst, int mode, int nrhs, cons
   const T muc = (T)(op->coeff.type == HHG_COEFF_CONST ? op->coeff.value : 1.0);
   if (mode == 2 && (nrhs > 32 || (32 % nrhs) != 0))
     return fail(HHG_E_UNSUPPORTED, "epsilon adjoint: nrhs must divide 32");
+  if (nrhs > 256) return fail(HHG_E_UNSUPPORTED, "epsilon: at most 256 right-hand sides per call");
+  // tasks of live cubes per colour (cached in the operator for this number of cubes per CTA)
+  const int cpb = 256 / nrhs;
+  if (op->eps_cpb != cpb) {
+    std::vector<int4> tv;
+    int64_t off[9];
+    for (int color = 0; color < 8; ++color) {
+      off[color] = (int64_t)tv.size();
+      const int px = color & 1, py = (color >> 1) & 1, pz = (color >> 2) & 1;
+      for (int m = 0; m < nm; ++m)
+        for (int kz = 0; kz < nz; ++kz)
+          for (int jy = 0; jy < nh; ++jy) {
+            const int rem = n - 1 - (2 * jy + py) - (2 * kz + pz) - px;   // room left for 2 ci'
+            if (rem < 0) continue;
+            const int len = rem / 2 + 1;                                   // live cubes of the row
+            for (int st = 0; st < len; st += cpb) tv.push_back(int4{st, jy, kz, m});
+          }
+    }
+    off[8] = (int64_t)tv.size();
+    cudaFree(op->d_eps_tasks);
+    op->d_eps_tasks = nullptr;
+    op->eps_cpb = 0;
+    HHG_CUDA_TRY(cudaMalloc(&op->d_eps_tasks, sizeof(int4) * std::max<size_t>(tv.size(), 1)));
+    if (!tv.empty())
+      HHG_CUDA_TRY(cudaMemcpy(op->d_eps_tasks, tv.data(), sizeof(int4) * tv.size(), cudaMemcpyHostToDevice));
+    for (int c = 0; c < 9; ++c) op->eps_off[c] = off[c];
+    op->eps_cpb = cpb;
+  }
   const size_t bytes = sizeof(T) * (size_t)op->npts * (mode == 0 ? 3 * nrhs : 1);
   HHG_CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));
-  dim3 grid((unsigned)((nh * nrhs + 255) / 256), (unsigned)nh, (unsigned)(nz * nm));
   for (int color = 0; color < 8; ++color) {
-#define HHG_EPS(M, F, D) eps_color_kernel<T, M, F, D><<<grid, 256, 0, s>>>(cst, color, nz, nrhs, muc, x, g, mu, out)
+    const unsigned grid = (unsigned)(op->eps_off[color + 1] - op->eps_off[color]);
+    if (grid == 0) continue;
+    const int4* tk = op->d_eps_tasks + op->eps_off[color];
+#define HHG_EPS(M, F, D) eps_color_kernel<T, M, F, D><<<grid, 256, 0, s>>>(cst, tk, color, cpb, nrhs, muc, x, g, mu, out)
     const bool dir = op->bc == HHG_DIRICHLET;
     if (mode == 0) {
       if (field) {

@@ -226,6 +226,11 @@ struct hhg_op {
   void* d_p2st64 = nullptr;  // P2Stencil<double>[nmacro] (P2 constant-coefficient diffusion)
   void* d_p2st32 = nullptr;
   void* d_p2idx = nullptr;   // P2StencilIndex (structural neighbour lists)
+  // epsilon operator: per colour, the CTAs of live cubes (ci/2 start, cj/2, ck/2, macro), built on
+  // first use for eps_cpb cubes per CTA
+  mutable int4* d_eps_tasks = nullptr;
+  mutable int64_t eps_off[9] = {0};
+  mutable int eps_cpb = 0;
   void* d_n1_64 = nullptr;   // N1Const<double>[nmacro]
   void* d_n1_32 = nullptr;
   int N = 0, n = 0;

@@ -437,6 +437,15 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
           T S3[3][3], R3[3];
           if ((MODE == MODE_APPLY && affine) || MODE == MODE_ADJ) {
             p2_grad_affine<T>(ul, Wu);
+            // the metric is linear too: M grad_ref u = M W0 + sum_b lambda_b M Wb
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              T mw[3];
+              metric<T>(M, Wu[t], mw);
+              Wu[t][0] = mw[0];
+              Wu[t][1] = mw[1];
+              Wu[t][2] = mw[2];
+            }
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
               R3[a] = T(0);
@@ -469,9 +478,8 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
               p2_ref_test_q<T>(r, c.lam4[q], c.lam4m1[q], yl);
             } else if (MODE == MODE_APPLY) {
               const T l1 = c.lam[q][1], l2 = c.lam[q][2], l3 = c.lam[q][3];
-              T gr[3], r[3];
-              p2_grad_at<T>(Wu, l1, l2, l3, gr);
-              metric<T>(M, gr, r);
+              T r[3];
+              p2_grad_at<T>(Wu, l1, l2, l3, r);   // M grad_ref u at the point
               const T s = kq * c.w[q];
 #pragma unroll
               for (int a = 0; a < 3; ++a) {
@@ -495,10 +503,9 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
                 yl[a] += s * (gr[0] * r[0] + gr[1] * r[1] + gr[2] * r[2]);
               }
             } else {
-              T gu[3], gg[3], r[3];
-              p2_grad_at<T>(Wu, c.lam[q][1], c.lam[q][2], c.lam[q][3], gu);
+              T gg[3], r[3];
+              p2_grad_at<T>(Wu, c.lam[q][1], c.lam[q][2], c.lam[q][3], r);   // M grad_ref u
               p2_grad_at<T>(Wg, c.lam[q][1], c.lam[q][2], c.lam[q][3], gg);
-              metric<T>(M, gu, r);
               const T t = c.w[q] * (gg[0] * r[0] + gg[1] * r[1] + gg[2] * r[2]);
 #pragma unroll
               for (int m = 0; m < 10; ++m) yl[m] += c.psi[q][m] * t;

@@ -1302,6 +1302,7 @@ hhg_op::~hhg_op() {
   cudaFree(d_p2st64);
   cudaFree(d_p2st32);
   cudaFree(d_p2idx);
+  cudaFree(d_eps_tasks);
 }
 
 static int check_dtype(int dtype) {

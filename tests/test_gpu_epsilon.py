@@ -78,3 +78,22 @@ def test_epsilon_rigid_body_modes_neumann():
     K = OA.epsilon_matrix(c.S, ("field", c.S, mu), 4, "neumann")
     scale = abs(K).max() * np.abs(X).max()
     assert np.abs(y).max() <= 1e-12 * scale * 10
+
+
+def test_epsilon_batch_sizes_on_one_operator():
+    """One operator applied with 3, 16 and again 3 right-hand sides (the per-launch task lists are
+    rebuilt when the batch size changes); more than 256 right-hand sides are refused."""
+    import paper_2404_08371_gb300 as hhg
+    from gpu_helpers import rel_err
+    c, mu = _case("cube6", 1)
+    op = hhg.Operator(c.mesh, kind="epsilon", degree=2, coeff=("field_p2", c.packed(mu)), bc="dirichlet",
+                      quad_degree=4)
+    K = OA.epsilon_matrix(c.S, ("field", c.S, mu), 4, "dirichlet")
+    for nrhs in (3, 16, 3):
+        X = np.stack([W.uniform(3 * c.S.ndof, seed=40 + s) for s in range(nrhs)], axis=1)
+        xp = torch.tensor(OL.to_packed(c.S, X.reshape(c.S.ndof, 3, nrhs), 3, nrhs), device="cuda")
+        got = OL.from_packed(c.S, op.apply(xp, nrhs=nrhs).cpu().numpy(), 3, nrhs).reshape(c.S.ndof, 3, nrhs)
+        assert rel_err(got, (K @ X).reshape(c.S.ndof, 3, nrhs)) <= 1e-12
+    xb = torch.zeros(c.mesh.vec_size(2) * 3 * 257, dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError, match="256"):
+        op.apply(xb, nrhs=257)
