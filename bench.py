@@ -16,6 +16,7 @@ needs no data from other GPUs); value = DoFs of all ranks / max rank time.
 from __future__ import annotations
 
 import argparse
+import itertools
 import json
 import os
 import statistics
@@ -461,13 +462,33 @@ def main():
         d2h += L["hy"].numel() * L["esize"]
     # End to end: every step copies each leg's x from pinned host memory and its y back, through the
     # public apply.  Copies run on their own streams, ordered by events around each apply, so they
-    # overlap the other legs' applies; the leg with the smallest input goes first, the one with the
-    # smallest output (of the rest) last, the others by decreasing apply time.
-    first = min(legs, key=lambda L: L["hx"].numel() * L["esize"])
-    rest = [L for L in legs if L is not first]
-    last = min(rest, key=lambda L: L["hy"].numel() * L["esize"])
-    mid = sorted([L for L in rest if L is not last], key=lambda L: -statistics.mean(L["ms"]))
-    order = [first] + mid + [last]
+    # overlap the other legs' applies.  The leg order is the one with the shortest modelled step
+    # (copies in order on one stream per direction at the rates measured here, applies in order).
+    big = max(legs, key=lambda L: L["hx"].numel())
+    nbig = big["hx"].numel() * big["esize"]
+
+    def copy_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    h2d_rate = nbig / copy_ms(lambda: big["x"].copy_(big["hx"], non_blocking=True))   # bytes per ms
+    d2h_rate = nbig / copy_ms(lambda: big["hy"].copy_(big["y"], non_blocking=True))
+
+    def modelled_ms(order):
+        th = tc = td = 0.0
+        for L in order:
+            th += L["hx"].numel() * L["esize"] / h2d_rate
+            tc = max(tc, th) + statistics.mean(L["ms"])
+            td = max(td, tc) + L["hy"].numel() * L["esize"] / d2h_rate
+        return td
+
+    order = list(min(itertools.permutations(legs), key=modelled_ms))
     comp = torch.cuda.current_stream()
     h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
     e2e_ms = []
