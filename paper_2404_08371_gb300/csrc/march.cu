@@ -374,14 +374,14 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
           // ---- P1: A_T = kbar_T A0_o with A0_o the hoisted constant matrix ----
           T kbar = T(1);
           if (COEF == HHG_COEFF_SIN3) {
-            kbar = T(0);
+            // k_T = 1 + sum_q 3 w_q prod_d sin(2 pi x_q,d), the factor 3 w_q in the x table
+            kbar = T(1);
             for (int q = 0; q < c.nq; ++q) {
               T sv[3];
 #pragma unroll
               for (int d = 0; d < 3; ++d) sv[d] = so[d] * c.cs[o][q][d][0] + co[d] * c.cs[o][q][d][1];
-              kbar += c.w[q] * (T(1) + T(0.5) * sv[0] * sv[1] * sv[2]);
+              kbar = fma(sv[0] * sv[1], sv[2], kbar);
             }
-            kbar *= T(6);   // sum_q w_q = 1/6
           } else if (COEF == HHG_COEFF_FIELD_P1) {
             kbar = T(0.25) * (kb[node_slot<R>(o, 0)] + kb[node_slot<R>(o, 1)] + kb[node_slot<R>(o, 2)] +
                               kb[node_slot<R>(o, 3)]);
@@ -456,23 +456,25 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
           if (MODE == MODE_ADJ) p2_grad_affine<T>(gl, Wg);
 #pragma unroll 2
           for (int q = 0; q < c.nq; ++q) {
-            T kq;
+            // s = w_q k(x_q): analytic, w_q + 0.5 w_q prod_d sin(2 pi x_q,d) with the factor 0.5 w_q
+            // in the x table; P2 field, w_q sum_m k_m psi_m(x_q)
+            T s;
             if (COEF == HHG_COEFF_SIN3) {
               T sv[3];
 #pragma unroll
               for (int d = 0; d < 3; ++d) sv[d] = so[d] * c.cs[o][q][d][0] + co[d] * c.cs[o][q][d][1];
-              kq = T(1) + T(0.5) * sv[0] * sv[1] * sv[2];
+              s = fma(sv[0] * sv[1], sv[2], c.w[q]);
             } else {
-              kq = T(0);
+              T kq = T(0);
 #pragma unroll
               for (int m = 0; m < 10; ++m) kq += c.psi[q][m] * kb[node_slot<R>(o, m)];
+              s = kq * c.w[q];
             }
             if (MODE == MODE_APPLY && !affine) {
               T gr[3], r[3];
               p2_ref_grad_q<T>(ul, c.lam4[q], c.lam4m1[q], gr);
               metric<T>(M, gr, r);
-              const T s = kq * c.w[q];
-              r[0] *= s;
+                            r[0] *= s;
               r[1] *= s;
               r[2] *= s;
               p2_ref_test_q<T>(r, c.lam4[q], c.lam4m1[q], yl);
@@ -480,8 +482,7 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
               const T l1 = c.lam[q][1], l2 = c.lam[q][2], l3 = c.lam[q][3];
               T r[3];
               p2_grad_at<T>(Wu, l1, l2, l3, r);   // M grad_ref u at the point
-              const T s = kq * c.w[q];
-#pragma unroll
+              #pragma unroll
               for (int a = 0; a < 3; ++a) {
                 const T ra = r[a] * s;
                 R3[a] += ra;
@@ -491,8 +492,7 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
               }
             } else if (MODE == MODE_DIAG) {
               // grad_ref phi_a . M grad_ref phi_a for every node a
-              const T s = kq * c.w[q];
-#pragma unroll
+              #pragma unroll
               for (int a = 0; a < 10; ++a) {
                 T e[10];
 #pragma unroll

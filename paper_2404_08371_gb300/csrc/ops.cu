@@ -147,11 +147,16 @@ static void build_const(hhg_op* op) {
           ref[a] = kClassOffsets[o][0][a];
           for (int b = 0; b < 3; ++b) ref[a] += (kClassOffsets[o][b + 1][a] - kClassOffsets[o][0][a]) * xi[b];
         }
+        // the first coordinate's entries carry the point's factor of the analytic coefficient:
+        // P1 element mean k_T = 1 + sum_q 3 w_q prod_d sin(2 pi x_d) (sum_q w_q = 1/6), P2 point
+        // weight w_q k_q = w_q + 0.5 w_q prod_d sin(2 pi x_d)
+        const double fq = op->degree == 1 ? 3.0 * rq.w[q] : 0.5 * rq.w[q];
         for (int d = 0; d < 3; ++d) {
           double delta = 0;
           for (int a = 0; a < 3; ++a) delta += c.h[a][d] * ref[a];
-          c.cs[o][q][d][0] = std::cos(2.0 * M_PI * delta);
-          c.cs[o][q][d][1] = std::sin(2.0 * M_PI * delta);
+          const double f = d == 0 ? fq : 1.0;
+          c.cs[o][q][d][0] = f * std::cos(2.0 * M_PI * delta);
+          c.cs[o][q][d][1] = f * std::sin(2.0 * M_PI * delta);
           c.qoff[o][q][d] = delta;
         }
       }
