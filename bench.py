@@ -337,6 +337,37 @@ def run_underint(hhg, torch, flush, level: int = 8, reps: int = 3):
     return out
 
 
+def run_precomputed(hhg, torch, flush, level: int = 8, reps: int = 3):
+    """The precomputed variant against the matrix-free apply: local matrices of the sin3 legs
+    integrated once and stored (set-up timed separately), reference macro at level 8."""
+    import workloads as W
+    v, t = W.reference_tet()
+    mesh = hhg.Mesh(v, t, level)
+    out = {"workload": "reference macro, level %d, sin3 coefficient: stored local matrices vs matrix-free" % level}
+    for deg, qd in ((2, 4), (1, 2)):
+        tot, inner = mesh.dof_count(deg)
+        for dt, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+            op = hhg.Operator(mesh, degree=deg, coeff=("sin3",), bc="dirichlet", quad_degree=qd)
+            x = torch.from_numpy(W.uniform(mesh.vec_size(deg), seed=0)).to("cuda", tdt)
+            y = torch.empty_like(x)
+            free = time_apply(torch, lambda: op.apply(x, out=y), flush, reps)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            op.store_element_matrices(tdt)
+            e1.record()
+            torch.cuda.synchronize()
+            setup = e0.elapsed_time(e1)
+            stored = time_apply(torch, lambda: op.apply(x, out=y), flush, reps)
+            nbytes = len(t) * 6 * (55 if deg == 2 else 1) * (2 ** level) * (2 ** level + 1) * (2 ** level + 2) // 6 * \
+                (8 if dt == "f64" else 4)
+            out["p%d_sin3_%s" % (deg, dt)] = {"matrix_free_ms": free, "stored_ms": stored, "setup_ms": setup,
+                                              "stored_mdofs": inner / stored / 1e3, "stored_bytes": nbytes,
+                                              "break_even_applies": setup / (free - stored) if free > stored else None}
+            del op, x, y
+            torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -557,6 +588,8 @@ def main():
         extra["n1"] = run_n1(hhg, torch, flush)
         torch.cuda.empty_cache()
         extra["under_integration"] = run_underint(hhg, torch, flush)
+        torch.cuda.empty_cache()
+        extra["precomputed"] = run_precomputed(hhg, torch, flush)
         torch.cuda.empty_cache()
     fmg = None
     if not args.no_fmg:

@@ -183,6 +183,16 @@ class Operator:
                                              nrhs, _stream()), "hhg_op_apply_adjoint_coeff")
         return out
 
+    def store_element_matrices(self, dtype=torch.float64) -> "Operator":
+        """Precomputed variant: integrate the local matrices once; applies in ``dtype`` read them."""
+        check(lib.hhg_op_store_element_matrices(self.handle, HHG_F64 if dtype == torch.float64 else HHG_F32,
+                                                _stream()), "hhg_op_store_element_matrices")
+        return self
+
+    def drop_element_matrices(self) -> "Operator":
+        check(lib.hhg_op_drop_element_matrices(self.handle), "hhg_op_drop_element_matrices")
+        return self
+
     def diagonal(self, dtype=torch.float64) -> torch.Tensor:
         d = self.mesh.empty(self.degree, dtype, self.level)
         check(lib.hhg_op_diagonal(self.handle, _dev_ptr(d), dtype_code(d), _stream()), "hhg_op_diagonal")

@@ -55,6 +55,8 @@ SIGNATURES = {
     "hhg_op_apply": ([_vp, _vp, _vp, _i, _i, _vp], _i),
     "hhg_op_apply_adjoint_coeff": ([_vp, _vp, _vp, _vp, _i, _i, _vp], _i),
     "hhg_op_diagonal": ([_vp, _vp, _i, _vp], _i),
+    "hhg_op_store_element_matrices": ([_vp, _i, _vp], _i),
+    "hhg_op_drop_element_matrices": ([_vp], _i),
     "hhg_vec_coordinates": ([_vp, _i, _i, _vp, _vp], _i),
     "hhg_vec_make_consistent": ([_vp, _i, _i, _vp, _i, _i, _vp], _i),
     "hhg_vec_dot": ([_vp, _i, _i, _vp, _vp, _i, _i, ctypes.POINTER(_d), _vp], _i),

@@ -168,6 +168,11 @@ template <typename T>
 int launch_make_consistent(const Interface* itf, T* x, int per_point, cudaStream_t s);
 // Element-centric kernels (march.cu); mode 0 apply, 1 diagonal, 2 coefficient adjoint,
 // 3 load vector of f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z).
+// Precomputed variant (march.cu): local matrices of all micro-tets into elem, and applies from them.
+template <typename T>
+int launch_elem_store(const struct ::hhg_op* op, T* elem, cudaStream_t s);
+template <typename T>
+int launch_march_stored(const struct ::hhg_op* op, const T* x, T* y, cudaStream_t s);
 template <typename T>
 int launch_march(const struct ::hhg_op* op, const OpConst<T>* cst, int mode, const T* x, const T* g, const T* kf,
                  T* out, cudaStream_t s);
@@ -226,6 +231,10 @@ struct hhg_op {
   void* d_p2st64 = nullptr;  // P2Stencil<double>[nmacro] (P2 constant-coefficient diffusion)
   void* d_p2st32 = nullptr;
   void* d_p2idx = nullptr;   // P2StencilIndex (structural neighbour lists)
+  // stored local matrices (hhg_op_store_element_matrices): [macro][class][entry][cube], cube =
+  // packed index of its origin in the lattice of resolution 2^level - 1; entries 55 (P2) or 1 (P1)
+  void* d_elem = nullptr;
+  int elem_dtype = -1;
   // epsilon operator: per colour, the CTAs of live cubes (ci/2 start, cj/2, ck/2, macro), built on
   // first use for eps_cpb cubes per CTA
   mutable int4* d_eps_tasks = nullptr;

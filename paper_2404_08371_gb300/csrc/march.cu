@@ -52,6 +52,11 @@ __host__ __device__ constexpr int edge_end(int e, int s) {
   return t[e][s];
 }
 __host__ __device__ constexpr int class_shrink(int o) { return o == 0 ? 0 : (o == 5 ? 2 : 1); }
+
+// Coefficient tag of the precomputed variant: local matrices read from device memory (kf points to
+// them, layout [macro][class][entry][cube]); entries of the symmetric 10 x 10 P2 matrix a <= b.
+constexpr int kCoefStored = 4;
+__host__ __device__ constexpr int p2_sym(int a, int b) { return a * 10 - a * (a - 1) / 2 + (b - a); }
 // Position (0..R per axis) of local node `node` of class o inside the cube block, linearised.
 template <int R>
 __host__ __device__ constexpr int node_slot(int o, int node) {
@@ -315,6 +320,13 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
           cb[cn] = n1a.beta ? (in ? __ldg(n1a.beta + vidx) : T(0)) : n1a.beta_c;
         }
       }
+      // precomputed variant: the cube's entries in the stored local matrices
+      const T* __restrict__ elem = nullptr;
+      int64_t ncubes = 0;
+      if constexpr (COEF == kCoefStored) {
+        ncubes = dV(n - 1);
+        elem = kf + (int64_t)macro * 6 * (R == 1 ? 1 : 55) * ncubes + packed_index(n - 1, ci, cj, ck);
+      }
       // analytic coefficient in FP32: sin / cos of 2 pi x at the cube origin, per coordinate
       if (COEF == HHG_COEFF_SIN3 && !kRotate) {
 #pragma unroll
@@ -385,6 +397,8 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
           } else if (COEF == HHG_COEFF_FIELD_P1) {
             kbar = T(0.25) * (kb[node_slot<R>(o, 0)] + kb[node_slot<R>(o, 1)] + kb[node_slot<R>(o, 2)] +
                               kb[node_slot<R>(o, 3)]);
+          } else if (COEF == kCoefStored) {
+            kbar = __ldg(elem + (int64_t)o * ncubes);
           }
           if (MODE == MODE_APPLY) {
 #pragma unroll
@@ -409,6 +423,19 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
             }
 #pragma unroll
             for (int a = 0; a < 4; ++a) yl[a] = T(0.25) * t;
+          }
+        } else if (COEF == kCoefStored) {
+          // ---- P2 precomputed: the micro-tet's stored symmetric matrix ----
+          const T* __restrict__ E = elem + (int64_t)o * 55 * ncubes;
+          T Ae[55];
+#pragma unroll
+          for (int e = 0; e < 55; ++e) Ae[e] = __ldg(E + (int64_t)e * ncubes);
+#pragma unroll
+          for (int a = 0; a < 10; ++a) {
+            T s = T(0);
+#pragma unroll
+            for (int b = 0; b < 10; ++b) s = fma(Ae[a <= b ? p2_sym(a, b) : p2_sym(b, a)], ul[b], s);
+            yl[a] = s;
           }
         } else if (COEF == HHG_COEFF_CONST) {
           // ---- P2 constant: hoisted 10x10 matrix ----
@@ -579,6 +606,135 @@ static int launch_march_t(const hhg_op* op, const OpConst<T>* cst, const T* x, c
   HHG_CUDA_TRY(cudaGetLastError());
   return HHG_OK;
 }
+
+// Local matrices of all micro-tets by quadrature, for the precomputed variant: one thread per
+// (cube, class).  P2: A_T[a][b] = sum_q w_q k(x_q) gref_a(xi_q)^T M_o gref_b(xi_q), a <= b, summed per
+// quadrature point into the thread's row of shared memory; P1: the element mean of k.  Classes that
+// do not exist at the cube are skipped (never read).
+constexpr int kElemThreads = 64;
+
+template <typename T, int R, int COEF>
+__global__ void __launch_bounds__(kElemThreads) elem_store_kernel(const OpConst<T>* __restrict__ cst,
+                                                                  const T* __restrict__ kf, T* __restrict__ elem) {
+  constexpr int NE = R == 1 ? 1 : 55;
+  __shared__ T acc[kElemThreads][R == 1 ? 1 : 56];
+  const int macro = blockIdx.y;
+  const OpConst<T>& c = cst[macro];
+  const int n = c.n, N = c.N;
+  const int64_t ncubes = dV(n - 1);
+  const int64_t t = (int64_t)blockIdx.x * kElemThreads + threadIdx.x;
+  if (t >= 6 * ncubes) return;
+  const int o = (int)(t % 6);
+  const int64_t p = t / 6;
+  int ci, cj, ck;
+  decode_point(p, n - 1, ci, cj, ck);
+  if (ci + cj + ck > n - 1 - class_shrink(o)) return;
+  T* __restrict__ out = elem + ((int64_t)macro * 6 + o) * NE * ncubes + p;
+  T so[3] = {T(0), T(0), T(0)}, co[3] = {T(0), T(0), T(0)};
+  if (COEF == HHG_COEFF_SIN3) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T xd = c.X0[d] + T(ci) * c.H[0][d] + T(cj) * c.H[1][d] + T(ck) * c.H[2][d];
+      sincos2pi<T>(xd, &so[d], &co[d]);
+    }
+  }
+  constexpr int NL = R == 1 ? 4 : 10;
+  T kb[NL];
+  if (COEF == HHG_COEFF_FIELD_P1 || COEF == HHG_COEFF_FIELD_P2) {
+#pragma unroll
+    for (int a = 0; a < NL; ++a) {
+      const int s = node_slot<R>(o, a), cx = s % (R + 1), cy = (s / (R + 1)) % (R + 1), cz = s / ((R + 1) * (R + 1));
+      kb[a] = __ldg(kf + c.kbase + packed_index(N, R * ci + cx, R * cj + cy, R * ck + cz));
+    }
+  }
+  if constexpr (R == 1) {
+    T kbar = T(1);
+    if (COEF == HHG_COEFF_SIN3) {
+      for (int q = 0; q < c.nq; ++q) {
+        T sv[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sv[d] = so[d] * c.cs[o][q][d][0] + co[d] * c.cs[o][q][d][1];
+        kbar = fma(sv[0] * sv[1], sv[2], kbar);   // factor 3 w_q in the x table
+      }
+    } else {
+      kbar = T(0.25) * (kb[0] + kb[1] + kb[2] + kb[3]);
+    }
+    out[0] = kbar;
+  } else {
+    T* a_row = acc[threadIdx.x];
+    for (int e = 0; e < NE; ++e) a_row[e] = T(0);
+    const T* M = c.M[o];
+    const T g0[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};   // grad_ref lambda_a
+    for (int q = 0; q < c.nq; ++q) {
+      T sq;
+      if (COEF == HHG_COEFF_SIN3) {
+        T sv[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sv[d] = so[d] * c.cs[o][q][d][0] + co[d] * c.cs[o][q][d][1];
+        sq = fma(sv[0] * sv[1], sv[2], c.w[q]);   // factor 0.5 w_q in the x table
+      } else {
+        T kq = T(0);
+#pragma unroll
+        for (int m = 0; m < 10; ++m) kq += c.psi[q][m] * kb[m];
+        sq = kq * c.w[q];
+      }
+      // reference gradients of the 10 basis functions at the point
+      T G[10][3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) G[a][d] = c.lam4m1[q][a] * g0[a][d];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        const int a = edge_end(e, 0), b = edge_end(e, 1);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) G[4 + e][d] = c.lam4[q][a] * g0[b][d] + c.lam4[q][b] * g0[a][d];
+      }
+#pragma unroll
+      for (int b = 0; b < 10; ++b) {
+        T mg[3];
+        metric<T>(M, G[b], mg);
+        mg[0] *= sq;
+        mg[1] *= sq;
+        mg[2] *= sq;
+#pragma unroll
+        for (int a = 0; a <= b; ++a) a_row[p2_sym(a, b)] += G[a][0] * mg[0] + G[a][1] * mg[1] + G[a][2] * mg[2];
+      }
+    }
+    for (int e = 0; e < NE; ++e) out[(int64_t)e * ncubes] = a_row[e];
+  }
+}
+
+template <typename T>
+int launch_elem_store(const hhg_op* op, T* elem, cudaStream_t s) {
+  const int nm = op->mesh->nmacro();
+  const int64_t ncubes = (int64_t)op->n * (op->n + 1) * (op->n + 2) / 6;   // V(n - 1)
+  const dim3 grid((unsigned)((6 * ncubes + kElemThreads - 1) / kElemThreads), nm);
+  const OpConst<T>* cst = (const OpConst<T>*)(sizeof(T) == 8 ? op->d_const64 : op->d_const32);
+  const T* kf = (op->coeff.type == HHG_COEFF_FIELD_P1 || op->coeff.type == HHG_COEFF_FIELD_P2)
+                    ? (const T*)op->coeff.field : nullptr;
+#define HHG_ELEM(RR, CC) elem_store_kernel<T, RR, CC><<<grid, kElemThreads, 0, s>>>(cst, kf, elem)
+  if (op->degree == 1 && op->coeff.type == HHG_COEFF_SIN3) HHG_ELEM(1, HHG_COEFF_SIN3);
+  else if (op->degree == 1 && op->coeff.type == HHG_COEFF_FIELD_P1) HHG_ELEM(1, HHG_COEFF_FIELD_P1);
+  else if (op->degree == 2 && op->coeff.type == HHG_COEFF_SIN3) HHG_ELEM(2, HHG_COEFF_SIN3);
+  else if (op->degree == 2 && op->coeff.type == HHG_COEFF_FIELD_P2) HHG_ELEM(2, HHG_COEFF_FIELD_P2);
+  else return fail(HHG_E_UNSUPPORTED, "store_element_matrices: needs a SIN3 or FIELD coefficient of the op's degree");
+#undef HHG_ELEM
+  HHG_CUDA_TRY(cudaGetLastError());
+  return HHG_OK;
+}
+template int launch_elem_store<double>(const hhg_op*, double*, cudaStream_t);
+template int launch_elem_store<float>(const hhg_op*, float*, cudaStream_t);
+
+// Apply with the stored local matrices.
+template <typename T>
+int launch_march_stored(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
+  const OpConst<T>* cst = (const OpConst<T>*)(sizeof(T) == 8 ? op->d_const64 : op->d_const32);
+  if (op->degree == 1) return launch_march_t<T, 1, kCoefStored, MODE_APPLY>(op, cst, x, nullptr, (const T*)op->d_elem, y, s);
+  return launch_march_t<T, 2, kCoefStored, MODE_APPLY>(op, cst, x, nullptr, (const T*)op->d_elem, y, s);
+}
+template int launch_march_stored<double>(const hhg_op*, const double*, double*, cudaStream_t);
+template int launch_march_stored<float>(const hhg_op*, const float*, float*, cudaStream_t);
 
 // Dispatch on (degree, coefficient, mode).  Returns HHG_E_UNSUPPORTED for other combinations.
 template <typename T>

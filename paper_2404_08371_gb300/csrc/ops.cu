@@ -1217,6 +1217,8 @@ template <typename T>
 int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
   const int64_t V = lattice_size(op->N);
   const int nm = op->mesh->nmacro();
+  // precomputed variant: local matrices stored in this dtype
+  if (op->d_elem && op->elem_dtype == (sizeof(T) == 8 ? HHG_F64 : HHG_F32)) return launch_march_stored<T>(op, x, y, s);
   if (op->kind == HHG_DIFFUSION && op->degree == 1 && op->coeff.type == HHG_COEFF_CONST) {
     (void)V;
     const Interface* I = op->itf;
@@ -1308,6 +1310,7 @@ hhg_op::~hhg_op() {
   cudaFree(d_p2st32);
   cudaFree(d_p2idx);
   cudaFree(d_eps_tasks);
+  cudaFree(d_elem);
 }
 
 static int check_dtype(int dtype) {
@@ -1491,6 +1494,49 @@ extern "C" int hhg_op_destroy(hhg_op_t* op) {
   return HHG_OK;
 }
 
+extern "C" int hhg_op_drop_element_matrices(hhg_op_t* op) {
+  clear_error();
+  if (!op) return fail(HHG_E_ARG, "drop_element_matrices: null op");
+  if (op->d_elem) {
+    HHG_CUDA_TRY(cudaDeviceSynchronize());   // no apply in flight may still read them
+    cudaFree(op->d_elem);
+  }
+  op->d_elem = nullptr;
+  op->elem_dtype = -1;
+  return HHG_OK;
+}
+
+extern "C" int hhg_op_store_element_matrices(hhg_op_t* op, int dtype, void* stream) {
+  clear_error();
+  if (!op) return fail(HHG_E_ARG, "store_element_matrices: null op");
+  HHG_TRY(check_dtype(dtype));
+  if (op->kind != HHG_DIFFUSION || !(op->coeff.type == HHG_COEFF_SIN3 ||
+                                     (op->coeff.type == HHG_COEFF_FIELD_P1 && op->degree == 1) ||
+                                     (op->coeff.type == HHG_COEFF_FIELD_P2 && op->degree == 2)))
+    return fail(HHG_E_UNSUPPORTED, "store_element_matrices: needs a DIFFUSION op with a SIN3 or FIELD coefficient");
+  if ((op->coeff.type == HHG_COEFF_FIELD_P1 || op->coeff.type == HHG_COEFF_FIELD_P2) && op->coeff.field_dtype != dtype)
+    return fail(HHG_E_ARG, "store_element_matrices: the coefficient field must have the stored dtype");
+  HHG_TRY(hhg_op_drop_element_matrices(op));
+  const int64_t ncubes = (int64_t)op->n * (op->n + 1) * (op->n + 2) / 6;   // V(2^level - 1)
+  const size_t bytes = (size_t)op->mesh->nmacro() * 6 * (op->degree == 1 ? 1 : 55) * ncubes *
+                       (dtype == HHG_F64 ? 8 : 4);
+  if (cudaMalloc(&op->d_elem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    op->d_elem = nullptr;
+    return fail(HHG_E_OOM, "store_element_matrices: %zu bytes of device memory", bytes);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int rc = dtype == HHG_F64 ? launch_elem_store<double>(op, (double*)op->d_elem, s)
+                                  : launch_elem_store<float>(op, (float*)op->d_elem, s);
+  if (rc != HHG_OK) {
+    cudaFree(op->d_elem);
+    op->d_elem = nullptr;
+    return rc;
+  }
+  op->elem_dtype = dtype;
+  return HHG_OK;
+}
+
 extern "C" int hhg_op_set_field(hhg_op_t* op, const void* field, int field_dtype) {
   clear_error();
   if (!op) return fail(HHG_E_ARG, "op_set_field: null op");
@@ -1499,6 +1545,7 @@ extern "C" int hhg_op_set_field(hhg_op_t* op, const void* field, int field_dtype
   HHG_TRY(check_dtype(field_dtype));
   op->coeff.field = field;
   op->coeff.field_dtype = field_dtype;
+  HHG_TRY(hhg_op_drop_element_matrices(op));   // they were integrated with the old field
   return HHG_OK;
 }
 

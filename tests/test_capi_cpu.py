@@ -68,6 +68,8 @@ def test_null_arguments_rejected(lib):
     assert lib.hhg_op_apply(None, None, None, 1, 1, None) == _lib.HHG_E_ARG
     assert lib.hhg_vec_size(None, 0, 1, None) == _lib.HHG_E_ARG
     assert lib.hhg_mg_default_opts(None) == _lib.HHG_E_ARG
+    assert lib.hhg_op_store_element_matrices(None, _lib.HHG_F64, None) == _lib.HHG_E_ARG
+    assert lib.hhg_op_drop_element_matrices(None) == _lib.HHG_E_ARG
     o = _lib.hhg_mg_opts_t()
     assert lib.hhg_mg_default_opts(ctypes.byref(o)) == 0
     assert (o.nu1, o.nu2, o.cheb_order, o.power_iters, o.tol) == (2, 2, 2, 15, 1e-10)

@@ -165,3 +165,35 @@ def test_p2_under_integration_parity(meshname, level, kind, qd, dtype):
     ref = OA.diffusion_matrix(c.S, oc, qd, "dirichlet") @ xg
     got, spread = c.unpack(y)
     assert rel_err(got, ref) <= TOL[dtype] and spread == 0.0
+
+
+@pytest.mark.parametrize("meshname,level", [("reference_tet", 0), ("reference_tet", 3), ("cube6", 2), ("cuboid36", 1)])
+@pytest.mark.parametrize("degree,kind", [(1, "sin3"), (1, "field"), (2, "sin3"), (2, "field")])
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_stored_element_matrices_parity(meshname, level, degree, kind, bc, dtype):
+    """Precomputed variant: local matrices integrated once and stored, then applied; the same
+    operator as the matrix-free apply (oracle parity), other dtypes keep the matrix-free path."""
+    from gpu_helpers import Case, rel_err
+    import paper_2404_08371_gb300 as hhg
+    c = Case(meshname, level, degree)
+    lc, oc = _coeff(c, kind, dtype)
+    op = hhg.Operator(c.mesh, degree=degree, coeff=lc, bc=bc, quad_degree=QD[degree])
+    xg = W.uniform(c.S.ndof, seed=5)
+    if dtype == torch.float32:
+        xg = xg.astype(np.float32).astype(np.float64)
+    xp = c.packed(xg, dtype)
+    y_free = op.apply(xp)
+    op.store_element_matrices(dtype)
+    y = op.apply(xp)
+    ref = OA.diffusion_matrix(c.S, oc, QD[degree], bc) @ xg
+    got, spread = c.unpack(y)
+    assert rel_err(got, ref) <= TOL[dtype], rel_err(got, ref)
+    assert spread == 0.0
+    assert torch.allclose(y, y_free, rtol=0, atol=(1e-13 if dtype == torch.float64 else 2e-6) * y_free.abs().max().item())
+    other = torch.float32 if dtype == torch.float64 else torch.float64
+    if kind == "sin3":   # the other dtype still takes the matrix-free path
+        y_other = op.apply(xp.to(other))
+        assert rel_err(c.unpack(y_other)[0], ref) <= 1e-5
+    op.drop_element_matrices()
+    assert torch.equal(op.apply(xp), y_free)
