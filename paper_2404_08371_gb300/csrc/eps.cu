@@ -21,26 +21,16 @@
 
 namespace hhg {
 
-__host__ __device__ constexpr int eoff(int o, int v, int d) {
-  constexpr int t[6][4][3] = {
-      {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, {{0, 1, 0}, {1, 0, 1}, {1, 0, 0}, {1, 1, 0}},
-      {{0, 1, 0}, {1, 0, 1}, {1, 1, 0}, {0, 1, 1}}, {{0, 1, 0}, {1, 0, 1}, {0, 1, 1}, {0, 0, 1}},
-      {{0, 1, 0}, {1, 0, 1}, {0, 0, 1}, {1, 0, 0}}, {{1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}}};
-  return t[o][v][d];
-}
 __host__ __device__ constexpr int eedge(int e, int s) {
   constexpr int t[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
   return t[e][s];
 }
+
 // Doubled-lattice offset of P2 node `a` of class o from 2 * (cube origin); in kernels, where o is a
 // run-time value uniform over the warp, from the constant-memory class table.
 __device__ __forceinline__ int enode_d(int o, int a, int d) {
   return a < 4 ? 2 * kClassOffsetsD[o][a][d]
                : kClassOffsetsD[o][eedge(a - 4, 0)][d] + kClassOffsetsD[o][eedge(a - 4, 1)][d];
-}
-// The same at compile time.
-__host__ __device__ constexpr int enode(int o, int a, int d) {
-  return a < 4 ? 2 * eoff(o, a, d) : eoff(o, eedge(a - 4, 0), d) + eoff(o, eedge(a - 4, 1), d);
 }
 
 // The reference gradient of a P2 component is affine in the barycentric coordinates:

@@ -20,14 +20,6 @@
 
 namespace hhg {
 
-__host__ __device__ constexpr int cls_off(int o, int v, int d) {
-  constexpr int t[6][4][3] = {
-      {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, {{0, 1, 0}, {1, 0, 1}, {1, 0, 0}, {1, 1, 0}},
-      {{0, 1, 0}, {1, 0, 1}, {1, 1, 0}, {0, 1, 1}}, {{0, 1, 0}, {1, 0, 1}, {0, 1, 1}, {0, 0, 1}},
-      {{0, 1, 0}, {1, 0, 1}, {0, 0, 1}, {1, 0, 0}}, {{1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}}};
-  return t[o][v][d];
-}
-
 // Coarse-cube block position (0..R per axis) of local node `node` of class o.
 static void node_pos(int R, int o, int node, int p[3]) {
   for (int d = 0; d < 3; ++d) {
