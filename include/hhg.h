@@ -158,13 +158,14 @@ int hhg_op_apply_adjoint_coeff(hhg_op_t* op, const void* u, const void* g, void*
 int hhg_op_diagonal(hhg_op_t* op, void* d, int dtype, void* stream);
 
 /* Precomputed variant of Eq. 4.1 for a variable-coefficient DIFFUSION op
- * (HHG_COEFF_SIN3 or a FIELD of the op's degree): the local matrices A_T of
- * all micro-tets are integrated once with the op's rule and kept in device
- * memory owned by the op (P2: the 55 entries of the symmetric 10 x 10 matrix,
- * P1: the element mean of k, A_T = mean(k) A0); later hhg_op_apply calls in
+ * (HHG_COEFF_SIN3 or a FIELD of the op's degree) or a CURLCURL op (Eq. N1):
+ * the local matrices A_T of all micro-tets are integrated once with the op's
+ * rule and kept in device memory owned by the op (P2: the 55 entries of the
+ * symmetric 10 x 10 matrix, P1: the element mean of k, A_T = mean(k) A0, N1:
+ * the 21 entries of the symmetric 6 x 6 matrix); later hhg_op_apply calls in
  * `dtype` read them instead of integrating (the paper's precomputed element
- * matrices, Section 6.6).  Memory: 6 V(2^level - 1) (55 for P2, 1 for P1)
- * entries per macro of `dtype`.  Applies in the other dtype, the diagonal and
+ * matrices, Section 6.6).  Memory: 6 V(2^level - 1) (55 for P2, 1 for P1, 21
+ * for N1) entries per macro of `dtype`; coefficient fields must have `dtype`.  Applies in the other dtype, the diagonal and
  * the adjoint keep the matrix-free path.  hhg_op_set_field drops the stored
  * matrices.  Errors: HHG_E_UNSUPPORTED (other kinds or coefficients),
  * HHG_E_ARG, HHG_E_OOM, HHG_E_CUDA. */

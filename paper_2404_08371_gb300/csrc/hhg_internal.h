@@ -174,6 +174,8 @@ int launch_elem_store(const struct ::hhg_op* op, T* elem, cudaStream_t s);
 template <typename T>
 int launch_march_stored(const struct ::hhg_op* op, const T* x, T* y, cudaStream_t s);
 template <typename T>
+int launch_elem_store_n1(const struct ::hhg_op* op, T* elem, cudaStream_t s);
+template <typename T>
 int launch_march(const struct ::hhg_op* op, const OpConst<T>* cst, int mode, const T* x, const T* g, const T* kf,
                  T* out, cudaStream_t s);
 // Nedelec curl-curl + mass apply (march.cu, R = 2 traversal of the doubled lattice).

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
           }
       // Nedelec coefficients: P1 alpha / beta at the eight cube corners (inside the macro)
       T ca[MODE == MODE_N1 ? 8 : 1], cb[MODE == MODE_N1 ? 8 : 1];
-      if constexpr (MODE == MODE_N1) {
+      if constexpr (MODE == MODE_N1 && COEF != kCoefStored) {
 #pragma unroll
         for (int cn = 0; cn < 8; ++cn) {
           const int vi = ci + (cn & 1), vj = cj + ((cn >> 1) & 1), vk = ck + (cn >> 2);
@@ -325,7 +325,8 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
       int64_t ncubes = 0;
       if constexpr (COEF == kCoefStored) {
         ncubes = dV(n - 1);
-        elem = kf + (int64_t)macro * 6 * (R == 1 ? 1 : 55) * ncubes + packed_index(n - 1, ci, cj, ck);
+        elem = kf + (int64_t)macro * 6 * (MODE == MODE_N1 ? kN1Sym : (R == 1 ? 1 : 55)) * ncubes +
+               packed_index(n - 1, ci, cj, ck);
       }
       // analytic coefficient in FP32: sin / cos of 2 pi x at the cube origin, per coordinate
       if (COEF == HHG_COEFF_SIN3 && !kRotate) {
@@ -349,19 +350,24 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
           // A_T = mean(alpha) C_o + sum_v beta_v M_o^v (symmetric, canonical orientation), formed
           // once per micro-tet and applied to the six edge values.
           if constexpr (R == 2) {
-            T av[4], bv[4];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              const int cn = coff(o, v, 0) + 2 * coff(o, v, 1) + 4 * coff(o, v, 2);
-              av[v] = ca[cn];
-              bv[v] = cb[cn];
-            }
-            const T abar = T(0.25) * (av[0] + av[1] + av[2] + av[3]);
             T A[kN1Sym];
+            if constexpr (COEF == kCoefStored) {
 #pragma unroll
-            for (int t = 0; t < kN1Sym; ++t)
-              A[t] = abar * n1c.C[o][t] + bv[0] * n1c.M[o][0][t] + bv[1] * n1c.M[o][1][t] +
-                     bv[2] * n1c.M[o][2][t] + bv[3] * n1c.M[o][3][t];
+              for (int t = 0; t < kN1Sym; ++t) A[t] = __ldg(elem + ((int64_t)o * kN1Sym + t) * ncubes);
+            } else {
+              T av[4], bv[4];
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                const int cn = coff(o, v, 0) + 2 * coff(o, v, 1) + 4 * coff(o, v, 2);
+                av[v] = ca[cn];
+                bv[v] = cb[cn];
+              }
+              const T abar = T(0.25) * (av[0] + av[1] + av[2] + av[3]);
+#pragma unroll
+              for (int t = 0; t < kN1Sym; ++t)
+                A[t] = abar * n1c.C[o][t] + bv[0] * n1c.M[o][0][t] + bv[1] * n1c.M[o][1][t] +
+                       bv[2] * n1c.M[o][2][t] + bv[3] * n1c.M[o][3][t];
+            }
 #pragma unroll
             for (int e = 0; e < 6; ++e) {
               T s = T(0);
@@ -831,8 +837,65 @@ int launch_l2_error(const hhg_op* op, const double* uh, double* partial, cudaStr
   return HHG_OK;
 }
 
+// Local matrices of the Nedelec operator for the precomputed variant: one thread per (cube, class),
+// A_T = mean(alpha) C_o + sum_v beta_v M_o^v (21 entries, canonical orientation).
+template <typename T>
+__global__ void __launch_bounds__(kElemThreads) elem_store_n1_kernel(const N1Const<T>* __restrict__ n1, N1Args<T> a,
+                                                                     T* __restrict__ elem) {
+  const int macro = blockIdx.y;
+  const int n = a.n;
+  const int64_t ncubes = dV(n - 1);
+  const int64_t t = (int64_t)blockIdx.x * kElemThreads + threadIdx.x;
+  if (t >= 6 * ncubes) return;
+  const int o = (int)(t % 6);
+  const int64_t p = t / 6;
+  int ci, cj, ck;
+  decode_point(p, n - 1, ci, cj, ck);
+  if (ci + cj + ck > n - 1 - class_shrink(o)) return;
+  const N1Const<T>& q = n1[macro];
+  T av[4], bv[4];
+  for (int v = 0; v < 4; ++v) {
+    const int64_t vidx = q.vbase + packed_index(n, ci + coff(o, v, 0), cj + coff(o, v, 1), ck + coff(o, v, 2));
+    av[v] = a.alpha ? __ldg(a.alpha + vidx) : a.alpha_c;
+    bv[v] = a.beta ? __ldg(a.beta + vidx) : a.beta_c;
+  }
+  const T abar = T(0.25) * (av[0] + av[1] + av[2] + av[3]);
+  T* __restrict__ out = elem + ((int64_t)macro * 6 + o) * kN1Sym * ncubes + p;
+  for (int e = 0; e < kN1Sym; ++e)
+    out[(int64_t)e * ncubes] = abar * q.C[o][e] + bv[0] * q.M[o][0][e] + bv[1] * q.M[o][1][e] +
+                               bv[2] * q.M[o][2][e] + bv[3] * q.M[o][3][e];
+}
+
+template <typename T>
+static N1Args<T> n1_args(const hhg_op* op) {
+  N1Args<T> a;
+  a.n1 = (const N1Const<T>*)(sizeof(T) == 8 ? op->d_n1_64 : op->d_n1_32);
+  a.alpha = op->coeff.type == HHG_COEFF_FIELD_P1 ? (const T*)op->coeff.field : nullptr;
+  a.beta = op->coeff2.type == HHG_COEFF_FIELD_P1 ? (const T*)op->coeff2.field : nullptr;
+  a.alpha_c = (T)op->coeff.value;
+  a.beta_c = (T)op->coeff2.value;
+  a.n = op->n;
+  return a;
+}
+
+template <typename T>
+int launch_elem_store_n1(const hhg_op* op, T* elem, cudaStream_t s) {
+  const int64_t ncubes = (int64_t)op->n * (op->n + 1) * (op->n + 2) / 6;
+  const dim3 grid((unsigned)((6 * ncubes + kElemThreads - 1) / kElemThreads), op->mesh->nmacro());
+  const N1Args<T> a = n1_args<T>(op);
+  elem_store_n1_kernel<T><<<grid, kElemThreads, 0, s>>>(a.n1, a, elem);
+  HHG_CUDA_TRY(cudaGetLastError());
+  return HHG_OK;
+}
+template int launch_elem_store_n1<double>(const hhg_op*, double*, cudaStream_t);
+template int launch_elem_store_n1<float>(const hhg_op*, float*, cudaStream_t);
+
 template <typename T>
 int launch_n1(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
+  if (op->d_elem && op->elem_dtype == (sizeof(T) == 8 ? HHG_F64 : HHG_F32)) {
+    const OpConst<T>* cst = (const OpConst<T>*)(sizeof(T) == 8 ? op->d_const64 : op->d_const32);
+    return launch_march_t<T, 2, kCoefStored, MODE_N1>(op, cst, x, nullptr, (const T*)op->d_elem, y, s, n1_args<T>(op));
+  }
   N1Args<T> a;
   a.n1 = (const N1Const<T>*)(sizeof(T) == 8 ? op->d_n1_64 : op->d_n1_32);
   a.alpha = op->coeff.type == HHG_COEFF_FIELD_P1 ? (const T*)op->coeff.field : nullptr;

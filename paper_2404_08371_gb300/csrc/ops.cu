@@ -1510,24 +1510,30 @@ extern "C" int hhg_op_store_element_matrices(hhg_op_t* op, int dtype, void* stre
   clear_error();
   if (!op) return fail(HHG_E_ARG, "store_element_matrices: null op");
   HHG_TRY(check_dtype(dtype));
-  if (op->kind != HHG_DIFFUSION || !(op->coeff.type == HHG_COEFF_SIN3 ||
-                                     (op->coeff.type == HHG_COEFF_FIELD_P1 && op->degree == 1) ||
-                                     (op->coeff.type == HHG_COEFF_FIELD_P2 && op->degree == 2)))
-    return fail(HHG_E_UNSUPPORTED, "store_element_matrices: needs a DIFFUSION op with a SIN3 or FIELD coefficient");
-  if ((op->coeff.type == HHG_COEFF_FIELD_P1 || op->coeff.type == HHG_COEFF_FIELD_P2) && op->coeff.field_dtype != dtype)
-    return fail(HHG_E_ARG, "store_element_matrices: the coefficient field must have the stored dtype");
+  const bool n1 = op->kind == HHG_CURLCURL;
+  if (!n1 && (op->kind != HHG_DIFFUSION || !(op->coeff.type == HHG_COEFF_SIN3 ||
+                                             (op->coeff.type == HHG_COEFF_FIELD_P1 && op->degree == 1) ||
+                                             (op->coeff.type == HHG_COEFF_FIELD_P2 && op->degree == 2))))
+    return fail(HHG_E_UNSUPPORTED, "store_element_matrices: needs a CURLCURL op or a DIFFUSION op with a SIN3 or FIELD "
+                                   "coefficient");
+  for (const hhg_coeff_t* cf : {&op->coeff, &op->coeff2})
+    if ((cf->type == HHG_COEFF_FIELD_P1 || cf->type == HHG_COEFF_FIELD_P2) && cf->field_dtype != dtype &&
+        (cf == &op->coeff || n1))
+      return fail(HHG_E_ARG, "store_element_matrices: the coefficient fields must have the stored dtype");
   HHG_TRY(hhg_op_drop_element_matrices(op));
   const int64_t ncubes = (int64_t)op->n * (op->n + 1) * (op->n + 2) / 6;   // V(2^level - 1)
-  const size_t bytes = (size_t)op->mesh->nmacro() * 6 * (op->degree == 1 ? 1 : 55) * ncubes *
-                       (dtype == HHG_F64 ? 8 : 4);
+  const int ne = n1 ? kN1Sym : (op->degree == 1 ? 1 : 55);
+  const size_t bytes = (size_t)op->mesh->nmacro() * 6 * ne * ncubes * (dtype == HHG_F64 ? 8 : 4);
   if (cudaMalloc(&op->d_elem, bytes) != cudaSuccess) {
     cudaGetLastError();
     op->d_elem = nullptr;
     return fail(HHG_E_OOM, "store_element_matrices: %zu bytes of device memory", bytes);
   }
   cudaStream_t s = (cudaStream_t)stream;
-  const int rc = dtype == HHG_F64 ? launch_elem_store<double>(op, (double*)op->d_elem, s)
-                                  : launch_elem_store<float>(op, (float*)op->d_elem, s);
+  const int rc = n1 ? (dtype == HHG_F64 ? launch_elem_store_n1<double>(op, (double*)op->d_elem, s)
+                                       : launch_elem_store_n1<float>(op, (float*)op->d_elem, s))
+                    : (dtype == HHG_F64 ? launch_elem_store<double>(op, (double*)op->d_elem, s)
+                                        : launch_elem_store<float>(op, (float*)op->d_elem, s));
   if (rc != HHG_OK) {
     cudaFree(op->d_elem);
     op->d_elem = nullptr;

@@ -65,3 +65,31 @@ def test_n1_gradients_in_kernel_level3():
     y = op.apply(torch.tensor(OL.n1_to_packed(S, gp), device="cuda")).cpu().numpy()
     K = OA.n1_matrix(S, ("const", 1.0), ("const", 0.0), 4, "neumann")
     assert np.abs(OL.n1_from_packed(S, y)).max() <= 1e-12 * abs(K).max() * np.abs(gp).max() * 10
+
+
+@pytest.mark.parametrize("meshname,level", [("reference_tet", 3), ("cube6", 2), ("cuboid36", 1)])
+@pytest.mark.parametrize("kind", ["const", "field"])
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_n1_stored_element_matrices_parity(meshname, level, kind, bc, dtype):
+    """Precomputed variant of the Nedelec operator: the 21 entries per micro-tet stored once, then
+    applied; the same operator as the matrix-free apply."""
+    import paper_2404_08371_gb300 as hhg
+    from gpu_helpers import rel_err
+    v, t = getattr(W, meshname)()
+    mesh = hhg.Mesh(v, t, level)
+    S = OA.EdgeSpace(OM.MacroMesh(v, t), level)
+    la, lb, oa, ob = _coeffs(S, kind, dtype)
+    op = hhg.CurlCurl(mesh, la, lb, bc=bc)
+    xg = W.uniform(S.ndof, seed=2)
+    if dtype == torch.float32:
+        xg = xg.astype(np.float32).astype(np.float64)
+    xp = torch.tensor(OL.n1_to_packed(S, xg), dtype=dtype, device="cuda")
+    y_free = op.apply(xp)
+    op.store_element_matrices(dtype)
+    y = op.apply(xp)
+    ref = OA.n1_matrix(S, oa, ob, 4, bc) @ xg
+    assert rel_err(OL.n1_from_packed(S, y.double().cpu().numpy()), ref) <= TOL[dtype]
+    assert torch.allclose(y, y_free, rtol=0, atol=(1e-13 if dtype == torch.float64 else 2e-6) * y_free.abs().max().item())
+    op.drop_element_matrices()
+    assert torch.equal(op.apply(xp), y_free)
