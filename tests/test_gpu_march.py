@@ -197,3 +197,41 @@ def test_stored_element_matrices_parity(meshname, level, degree, kind, bc, dtype
         assert rel_err(c.unpack(y_other)[0], ref) <= 1e-5
     op.drop_element_matrices()
     assert torch.equal(op.apply(xp), y_free)
+
+
+def _sampled_points(N, n, rng, count=300):
+    """Sampled packed positions of a single-macro lattice of resolution N (plus points next to every
+    face and the first / last positions) and their lattice points."""
+    from oracle import mesh as OM
+    pts = OM.lattice_points(N)
+    near = np.nonzero((pts.min(axis=1) == 1) | (pts.sum(axis=1) == N - 1))[0]
+    sample = np.unique(np.concatenate([rng.choice(n, count, replace=False), rng.choice(near, 100, replace=False),
+                                       [0, n - 1, n // 2]]))
+    return sample, pts[sample]
+
+
+@pytest.mark.parametrize("degree,coeff,level,stored", [(1, "sin3", 8, False), (2, "sin3", 8, False),
+                                                        (1, "const", 9, False), (2, "const", 8, False),
+                                                        (2, "sin3", 8, True), (1, "sin3", 8, True)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_bench_legs_full_size_sampled(degree, coeff, level, stored, dtype):
+    """The bench's legs at full size, in the launch configuration it times (single macro, Dirichlet,
+    the leg's rule; constant-coefficient legs at their levels 8 / 9; the precomputed variant):
+    sampled rows against the oracle's per-point sums."""
+    import paper_2404_08371_gb300 as hhg
+    v, t = W.reference_tet()
+    mesh = hhg.Mesh(v, t, level)
+    lc = ("sin3",) if coeff == "sin3" else ("const", 1.0)
+    op = hhg.Operator(mesh, degree=degree, coeff=lc, bc="dirichlet", quad_degree=QD[degree])
+    if stored:
+        op.store_element_matrices(dtype)
+    N = degree * 2 ** level
+    n = mesh.vec_size(degree)
+    xp = W.uniform(n, seed=3)
+    if dtype == torch.float32:
+        xp = xp.astype(np.float32).astype(np.float64)
+    y = op.apply(torch.tensor(xp, dtype=dtype, device="cuda")).double().cpu().numpy()
+    sample, pts = _sampled_points(N, n, np.random.default_rng(level + 10 * degree))
+    ref = OA.sampled_diffusion_rows(v[t[0]], level, degree, lc, QD[degree], "dirichlet", xp, pts)
+    tol = 1e-12 if dtype == torch.float64 else 1e-5
+    assert np.abs(y[sample] - ref).max() <= tol * np.abs(y).max(), np.abs(y[sample] - ref).max() / np.abs(y).max()
