@@ -45,7 +45,7 @@ FALLBACK_LEGS = {
     "p1_sin3_f32": ("p1_const_f32", 1, ("const", 1.0), 2, "f32"),
 }
 
-# Algorithmic FLOPs per micro-tet of each apply variant ("algorithmic work").
+# Algorithmic FLOPs per unit (point or micro-tet) of each apply variant.
 def flops_per_unit(name: str, degree: int, nq: int):
     if name.startswith("p1_const"):
         return ("dof", 30.0)                       # 15-point stencil: 15 FMA per point
