@@ -77,7 +77,7 @@ struct Interface {
   int64_t n_march_tasks = 0;
   int march_kchunk = 32;
   // task lists of the plane-tile kernels: (i-chunk, row group, k-chunk, macro), heaviest first;
-  // tile[0] for chunks of 128 points along i, tile[1] for chunks of 64 (degree 2 only)
+  // tile[0] for chunks of 128 points along i, tile[1] for chunks of 64
   TileTasks tile[2];
   ~Interface();
 };

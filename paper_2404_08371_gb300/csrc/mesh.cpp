@@ -555,11 +555,8 @@ int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
     HHG_CUDA_TRY(cudaMemcpy(I->d_march_tasks, tv.data(), sizeof(int4) * tv.size(), cudaMemcpyHostToDevice));
   }
   // plane-tile kernel tasks: (i-chunk, row group, k-chunk), sorted by their number of points
-  if (degree == 1) HHG_TRY(build_tile_tasks(N, 32 * kStencilV, kStencilWarps, &I->tile[0]));
-  if (degree == 2) {
-    HHG_TRY(build_tile_tasks(N, 128, kStencilWarps, &I->tile[0]));
-    HHG_TRY(build_tile_tasks(N, 64, kStencilWarps, &I->tile[1]));
-  }
+  HHG_TRY(build_tile_tasks(N, 128, kStencilWarps, &I->tile[0]));
+  HHG_TRY(build_tile_tasks(N, 64, kStencilWarps, &I->tile[1]));
   I->h_ptr = ptr;
   I->h_idx = idx;
   I->h_bnd = bnd;

@@ -381,36 +381,77 @@ __global__ void __launch_bounds__(256) p1_gather_kernel(const OpConst<T>* __rest
   ym[p] = acc;
 }
 
-// Points on the faces of the macros for the plane-tile kernel (which writes only the points off the
-// faces), one thread each: face a of the macro has the points (a, b) with a + b <= N of its
-// triangle; a point on several faces is written by the lowest.
+// The register-climbing P1 FP32 kernel (p1_climb_f32_kernel) stops below the top kP1ClimbTop - 1
+// planes, where rows are too short for its unchecked windows; p1_face_slice writes those points.
+constexpr int kP1ClimbTop = 10;
+
+// Point off the macro faces: the 15-point stencil with the Dirichlet columns dropped.
 template <typename T, bool DIRICHLET>
-__global__ void __launch_bounds__(256) p1_face_kernel(const OpConst<T>* __restrict__ cst, const int* __restrict__ pstart,
-                                                      const T* __restrict__ x, T* __restrict__ y) {
-  const int macro = blockIdx.z, f = blockIdx.y;
-  const OpConst<T>& c = cst[macro];
+__device__ __forceinline__ T p1_interior_value(const OpConst<T>& c, const int* __restrict__ pstart,
+                                               const T* __restrict__ xm, int i, int j, int k) {
   const int N = c.N;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= tri(N)) return;
-  const float bq = 2.0f * N + 3.0f;
-  int b = (int)(0.5f * (bq - sqrtf(fmaxf(bq * bq - 8.0f * (float)t, 0.0f))));
-  b = max(0, min(b, N));
-  if (b < N && row32(N, b + 1) <= t) ++b;
-  if (b > 0 && row32(N, b) > t) --b;
-  const int a = t - row32(N, b);
-  int i, j, k;
-  if (f == 0) {
-    i = 0; j = a; k = b;
-  } else if (f == 1) {
-    i = a; j = 0; k = b;
-  } else if (f == 2) {
-    i = a; j = b; k = 0;
-  } else {
-    i = N - a - b; j = a; k = b;
+  T acc = T(0);
+#pragma unroll
+  for (int d = 0; d < 15; ++d) {
+    const int pi = i + kStencilD[d][0], pj = j + kStencilD[d][1], pkk = k + kStencilD[d][2];
+    if (DIRICHLET && on_dirichlet(c.bnd_table, N, pi, pj, pkk)) continue;
+    acc += c.S[d] * __ldg(xm + __ldg(pstart + pkk) + row32(N - pkk, pj) + pi);
   }
-  if ((f >= 1 && i == 0) || (f >= 2 && j == 0) || (f == 3 && k == 0)) return;
+  return acc;
+}
+
+// Points of the P1 FP32 apply that the climbing part of p1_climb_f32_kernel does not write, one
+// thread each (thread t of slice f).  Slices
+// 0-3: face a of the macro, the points (a, b) with a + b <= N of its triangle (a point on several
+// faces is written by the lowest).  Slices 4 and 5: the points off the faces in row j = 1 and in
+// plane k = 1.  Slice 6: the points off the faces with j >= 2 on the top planes k > N - kP1ClimbTop
+// (all planes k >= 2 when N < kP1ClimbTop + 2).
+template <typename T, bool DIRICHLET>
+__device__ __forceinline__ void p1_face_slice(const OpConst<T>& c, const int* __restrict__ pstart,
+                                              const T* __restrict__ x, T* __restrict__ y, int f, int t) {
+  const int N = c.N;
+  int i, j, k;
+  if (f <= 5) {
+    if (t >= tri(N)) return;
+    const float bq = 2.0f * N + 3.0f;
+    int b = (int)(0.5f * (bq - sqrtf(fmaxf(bq * bq - 8.0f * (float)t, 0.0f))));
+    b = max(0, min(b, N));
+    if (b < N && row32(N, b + 1) <= t) ++b;
+    if (b > 0 && row32(N, b) > t) --b;
+    const int a = t - row32(N, b);
+    if (f == 0) {
+      i = 0; j = a; k = b;
+    } else if (f == 1) {
+      i = a; j = 0; k = b;
+    } else if (f == 2) {
+      i = a; j = b; k = 0;
+    } else if (f == 3) {
+      i = N - a - b; j = a; k = b;
+    } else if (f == 4) {
+      i = a; j = 1; k = b;
+    } else {
+      i = a; j = b; k = 1;
+    }
+  } else {
+    // lattice of the top planes k >= kt (at most V(kP1ClimbTop - 1) points), plane by plane
+    const int kt = max(2, N - kP1ClimbTop + 1);
+    const int m = N - kt;
+    if (m < 0 || t >= (m + 1) * (m + 2) * (m + 3) / 6) return;
+    int rem = t, kk = 0;
+    while (rem >= tri(m - kk)) rem -= tri(m - kk++);
+    int jj = 0;
+    while (rem >= m - kk - jj + 1) rem -= m - kk - jj++ + 1;
+    i = rem; j = jj; k = kt + kk;
+  }
   const T* __restrict__ xm = x + c.base;
-  y[c.base + __ldg(pstart + k) + row32(N - k, j) + i] = p1_face_value<T, DIRICHLET>(c, pstart, xm, i, j, k);
+  if (f <= 3) {
+    if ((f >= 1 && i == 0) || (f >= 2 && j == 0) || (f == 3 && k == 0)) return;
+    y[c.base + __ldg(pstart + k) + row32(N - k, j) + i] = p1_face_value<T, DIRICHLET>(c, pstart, xm, i, j, k);
+    return;
+  }
+  const bool off_faces = i >= 1 && j >= 1 && k >= 1 && i + j + k <= N - 1;
+  if (!off_faces || (f >= 5 && j < 2)) return;
+  y[c.base + __ldg(pstart + k) + row32(N - k, j) + i] = p1_interior_value<T, DIRICHLET>(c, pstart, xm, i, j, k);
 }
 
 
@@ -513,19 +554,7 @@ struct P2UCell {
   static constexpr int ib = p2_union_list(PA).ib[C];
 };
 
-// P1 constant-coefficient apply in FP32 from shared-memory plane tiles.  A CTA owns rows
-// j0..j0+7 and points i0..i0+kTileI-1 of a k-chunk (task list of the stencil kernel) and climbs
-// its planes.  Each plane of the tile plus a one-point halo is staged with cp.async into a ring of
-// shared-memory planes, kTileDepth planes ahead of the plane being computed (one global load per
-// staged value; Dirichlet points zeroed after arrival); each thread evaluates the 15-point
-// stencil of its pairs of points from three staged planes with packed FMA.
-constexpr int kTileI = 32 * kStencilV;           // points along i (kStencilV per lane)
-constexpr int kTileJ = kStencilWarps;            // 8 rows
-constexpr int kTileH = kTileJ + 2;               // staged rows
-
-constexpr int kTileDepth = 4;                      // planes staged ahead of the one being computed
-constexpr int kTileRing = kTileDepth + 3;          // planes k-2 .. k+kTileDepth: one barrier per plane
-
+// cp.async helpers of the plane-tile kernels.
 __device__ __forceinline__ void cp_async_zfill(void* smem, const void* gmem, int bytes, bool valid) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   const int src = valid ? bytes : 0;   // src-size 0: the destination is zero-filled, nothing is read
@@ -540,181 +569,207 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(NPENDING));
 }
 
-// FP32 variant with packed FMA (Blackwell fma.rn.f32x2): each thread owns the pairs of points
-// (i, i+1), i = i0 + 2 (lane + 32 v), v < kTileI / 64.  Staged column c holds point i = i0 - 2 + c, so every
-// pair starts at an even column and a stencil row needs two or three 8-byte shared loads per pair.
-constexpr int kPairW = kTileI + 4;                 // staged columns (1 .. kTileI + 2 used)
-constexpr int kPairSlot = kTileH * kPairW;
 
-__device__ __forceinline__ void p1_issue_plane_f32(float* slot, const float* __restrict__ xm,
-                                                   const int* __restrict__ pstart, int N, int i0, int j0, int kk) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// P1 constant-coefficient apply in FP32 with the planes carried in registers.  A CTA takes a tile
+// task (rows j0..j0+7, points i0..i0+32 PT-1 of a k-chunk); warp w owns row j = j0 + w and the
+// points i = i0 + lane + 32 t (t < PT) and climbs k.  The 15-point stencil of row (j, k) reads seven
+// rows: (j, k) at i-1, i, i+1; (j+1, k) and (j+1, k-1) at i-1, i; (j-1, k) and (j-1, k+1) at i,
+// i+1; (j, k+1) at i-1, i; (j, k-1) at i, i+1.  A row j' = j+1 serves the warp in two consecutive
+// steps, a row j' = j in three and a row j' = j-1 in two, so each step reads three new rows from
+// global memory (through L1, where the warps of rows j-1 and j+1 find them again): (j+1, k+1),
+// (j-1, k+2), (j, k+2), one step before they are needed.  The rows live in register rings of
+// 3, 4 and 3 slots; the k loop is unrolled by 12, the least common multiple, so that every slot
+// index is a compile-time constant.  No shared memory, no barriers.
+//
+// The kernel writes the points with 1 <= i <= N-j-k-1, j >= 2 and 2 <= k <= N - kP1ClimbTop; the
+// other points off the macro faces (rows j = 1, planes k = 1 and the top planes) and the face points
+// are written by p1_face_slice.  Every row it reads then exists, and a row is read without bounds
+// checks: positions before its first or after its last point fall inside the macro's array (on
+// these planes at least V(8) = 165 points follow every row, more than a window reaches past it) and
+// feed only points that are not written.  With rows j, k >= 2 the only neighbours on a macro face are
+// the points i = 0 (face i = 0, for the point i = 1) and the points on the face i + j + k = N (for
+// the point i = N-j-k-1), each lying on that face alone; their four terms are summed apart and
+// dropped when the face is Dirichlet.
+
+template <int SLO, int SHI, int PT>
+__device__ __forceinline__ void p1_climb_row(float (&v)[SHI - SLO + 1][PT], const float* __restrict__ at) {
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int r = warp + kTileJ * h;
-    if (r >= kTileH) break;
-    const int jr = j0 - 1 + r;
-    const int len = N - jr - kk + 1;
-    const bool rowok = jr >= 0 && kk >= 0 && kk <= N && len > 0;
-    const float* __restrict__ row = rowok ? xm + __ldg(pstart + kk) + row32(N - kk, jr) : xm;
+  for (int s = SLO; s <= SHI; ++s)
 #pragma unroll
-    for (int t = 0; t < (kTileI + 2 + 31) / 32; ++t) {
-      const int col = 1 + lane + 32 * t;
-      if (col > kTileI + 2) break;
-      const int ii = i0 - 2 + col;
-      const bool ok = rowok && ii >= 0 && ii < len;
-      cp_async_zfill(slot + r * kPairW + col, ok ? row + ii : xm, 4, ok);
+    for (int t = 0; t < PT; ++t) v[s - SLO][t] = __ldg(at + 32 * t + s);
+}
+
+// The loads of a row are issued one step before its first use, which alone does not cover the
+// DRAM latency: the three rows that step k + kClimbAhead loads are prefetched into L2 at step k
+// (0 or 1: no prefetch).  The window [ib-1, ib+32 PT] spans at most PT + 2 lines of 32 floats;
+// lane l <= PT + 1 touches the line at offset min(32 l, 32 PT + 1).
+constexpr int kClimbAhead = 3;
+
+__device__ __forceinline__ void p1_climb_prefetch(const float* a) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
+// points per lane of the climbing kernel (its tile tasks are 32 * kClimbPT points wide)
+constexpr int kClimbPT = 2;
+
+template <int PT>
+struct P1Climb {
+  float P[3][2][PT];   // rows j+1 at i-1, i
+  float Z[4][3][PT];   // rows j at i-1, i, i+1
+  float M[3][2][PT];   // rows j-1 at i, i+1
+  // running offsets (from point ib + lane of the macro) of the rows loaded next, (j+1, k+1),
+  // (j-1, k+2), (j, k+2), of the same rows kClimbAhead planes higher (prefetch, at the lane's line
+  // offset), and of y at (j, k); a row advances by start(jr, kr + 1) = start(jr, kr) + tri(N - kr) - jr
+  int ap, am, az, fp, fm, fz, ay;
+  int t0;              // tri(N - k)
+  int ta;              // tri(N - k - kClimbAhead)
+};
+
+// Step U (mod 12) of the climb: row (j, k).  Slots: row j+1 of plane k in P[(U+1)%3], row j of
+// plane k in Z[(U+1)%4], row j-1 of plane k in M[U%3].
+template <int U, int PT, bool DIRICHLET>
+__device__ __forceinline__ void p1_climb_step(P1Climb<PT>& R, const float (&S)[15], const float* __restrict__ xb,
+                                              float* __restrict__ yb, int N, bool dir_i0, bool dir_diag, int ib,
+                                              int j, int k, int ke) {
+  constexpr int pm = U % 3, p0 = (U + 1) % 3, pn = (U + 2) % 3;
+  constexpr int zm = U % 4, z0 = (U + 1) % 4, zp = (U + 2) % 4, zn = (U + 3) % 4;
+  constexpr int m0 = U % 3, mp = (U + 1) % 3, mn = (U + 2) % 3;
+  const int lane = threadIdx.x & 31;
+  if (k < ke) {
+    p1_climb_row<-1, 0, PT>(R.P[pn], xb + R.ap);
+    p1_climb_row<0, 1, PT>(R.M[mn], xb + R.am);
+    p1_climb_row<-1, 1, PT>(R.Z[zn], xb + R.az);
+  }
+  if (kClimbAhead > 1 && k + kClimbAhead < ke && lane <= PT + 1) {   // rows of step k + kClimbAhead
+    p1_climb_prefetch(xb + R.fp);
+    p1_climb_prefetch(xb + R.fm);
+    p1_climb_prefetch(xb + R.fz);
+  }
+  const int len = N - j - k + 1;
+  float mid[PT], lft[PT], rgt[PT];
+#pragma unroll
+  for (int t = 0; t < PT; ++t) {
+    float a = S[0] * R.Z[z0][1][t];
+    a = fmaf(S[4], R.M[m0][0][t], a);     // ( 0,-1, 0)
+    a = fmaf(S[7], R.M[m0][1][t], a);     // ( 1,-1, 0)
+    a = fmaf(S[6], R.Z[zm][1][t], a);     // ( 0, 0,-1)
+    a = fmaf(S[9], R.Z[zm][2][t], a);     // ( 1, 0,-1)
+    a = fmaf(S[11], R.P[pm][1][t], a);    // ( 0, 1,-1)
+    a = fmaf(S[12], R.M[mp][0][t], a);    // ( 0,-1, 1)
+    mid[t] = a;
+    // neighbours with i-1 (on face i = 0 for the point i = 1)
+    float l = S[2] * R.Z[z0][0][t];       // (-1, 0, 0)
+    l = fmaf(S[8], R.P[p0][0][t], l);     // (-1, 1, 0)
+    l = fmaf(S[10], R.Z[zp][0][t], l);    // (-1, 0, 1)
+    l = fmaf(S[14], R.P[pm][0][t], l);    // (-1, 1,-1)
+    lft[t] = l;
+    // neighbours one step nearer the face i + j + k = N (on it for the point i = N-j-k-1)
+    float r = S[1] * R.Z[z0][2][t];       // ( 1, 0, 0)
+    r = fmaf(S[3], R.P[p0][1][t], r);     // ( 0, 1, 0)
+    r = fmaf(S[5], R.Z[zp][1][t], r);     // ( 0, 0, 1)
+    r = fmaf(S[13], R.M[mp][1][t], r);    // ( 1,-1, 1)
+    rgt[t] = r;
+  }
+  if (DIRICHLET) {
+    if (dir_i0 && ib == 0 && lane == 1) lft[0] = 0.0f;
+    const int q = len - 2 - ib;           // the point i = N-j-k-1, relative to the window
+    if (dir_diag && q >= 0 && q < 32 * PT) {
+#pragma unroll
+      for (int t = 0; t < PT; ++t)
+        if (lane + 32 * t == q) rgt[t] = 0.0f;
     }
   }
-}
-
-// After plane kk has arrived: zero the staged Dirichlet points.  Off the faces j = 0 and k = 0
-// only the two row ends i = 0 and i = len - 1 can be Dirichlet points; the thread that staged a
-// position zeroes it.
-__device__ __forceinline__ void p1_mask_plane_f32(float* slot, int N, uint32_t table, int i0, int j0, int kk) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lo = 1 - ib - lane, hi = len - 2 - ib - lane;   // 32 t in [lo, hi]: a point to write
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int r = warp + kTileJ * h;
-    if (r >= kTileH) break;
-    const int jr = j0 - 1 + r;
-    const int len = N - jr - kk + 1;
-    if (!(jr >= 0 && kk >= 0 && kk <= N && len > 0)) continue;
-    if (jr == 0 || kk == 0) {
-#pragma unroll
-      for (int t = 0; t < (kTileI + 2 + 31) / 32; ++t) {
-        const int col = 1 + lane + 32 * t;
-        if (col > kTileI + 2) break;
-        const int ii = i0 - 2 + col;
-        if (ii >= 0 && ii < len && on_dirichlet(table, N, ii, jr, kk)) slot[r * kPairW + col] = 0.0f;
-      }
-    } else {
-      const int cand[2] = {2 - i0, len + 1 - i0};   // columns of i = 0 and i = len - 1
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int col = cand[e];
-        if (col >= 1 && col <= kTileI + 2 && ((col - 1) & 31) == lane) {
-          const int ii = i0 - 2 + col;
-          if (on_dirichlet(table, N, ii, jr, kk)) slot[r * kPairW + col] = 0.0f;
-        }
-      }
-    }
+  for (int t = 0; t < PT; ++t)
+    if (32 * t >= lo && 32 * t <= hi) yb[R.ay + 32 * t] = mid[t] + lft[t] + rgt[t];
+  // next plane
+  const int s = N - k;
+  const int t1 = R.t0 - (s + 1), t2 = t1 - s;   // tri(s - 1), tri(s - 2)
+  R.ay += R.t0 - j;
+  R.ap += t1 - (j + 1);
+  R.am += t2 - (j - 1);
+  R.az += t2 - j;
+  R.t0 = t1;
+  if (kClimbAhead > 1) {
+    const int sa = s - kClimbAhead;
+    const int a1 = R.ta - (sa + 1), a2 = a1 - sa;
+    R.fp += a1 - (j + 1);
+    R.fm += a2 - (j - 1);
+    R.fz += a2 - j;
+    R.ta = a1;
   }
 }
 
-__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
-__device__ __forceinline__ float2 fma2(float w, float2 v, float2 acc) { return __ffma2_rn(make_float2(w, w), v, acc); }
-
-// Stencil of the point pair at even column b of staged row r (planes k-1, k, k+1).
-__device__ __forceinline__ float2 p1_pair_stencil(const float* W, const float* pm, const float* p0, const float* pp,
-                                                  int r, int b) {
-  const int o = r * kPairW + b;
-  // centre row: columns b-2 .. b+3
-  const float2 c0 = ld2(p0 + o - 2), c1 = ld2(p0 + o), c2 = ld2(p0 + o + 2);
-  float2 acc = make_float2(0.0f, 0.0f);
-  acc = fma2(W[0], c1, acc);                                  // (0,0,0)
-  acc = fma2(W[1], make_float2(c1.y, c2.x), acc);             // (1,0,0)
-  acc = fma2(W[2], make_float2(c0.y, c1.x), acc);             // (-1,0,0)
-  // rows needing i-1, i: (j+1,k) [3: (0,1,0), 8: (-1,1,0)], (j,k+1) [5, 10], (j+1,k-1) [11, 14]
-  {
-    const float2 a0 = ld2(p0 + o + kPairW - 2), a1 = ld2(p0 + o + kPairW);
-    acc = fma2(W[3], a1, acc);
-    acc = fma2(W[8], make_float2(a0.y, a1.x), acc);
-    const float2 b0 = ld2(pp + o - 2), b1 = ld2(pp + o);
-    acc = fma2(W[5], b1, acc);
-    acc = fma2(W[10], make_float2(b0.y, b1.x), acc);
-    const float2 d0 = ld2(pm + o + kPairW - 2), d1 = ld2(pm + o + kPairW);
-    acc = fma2(W[11], d1, acc);
-    acc = fma2(W[14], make_float2(d0.y, d1.x), acc);
+// One launch does both parts: blocks below ntasks climb (tile tasks, heaviest first), the blocks after
+// them write the other points (p1_face_slice: per macro, slices 0-5 of nfb blocks each and one block
+// for the top planes), so that those fill the SMs that the last climbing tasks leave idle.
+template <int PT, bool DIRICHLET>
+__global__ void __launch_bounds__(256, PT == 4 ? 2 : 3) p1_climb_f32_kernel(const OpConst<float>* __restrict__ cst,
+                                                                             const int4* __restrict__ tasks,
+                                                                             int ntasks, int kch, int nfb,
+                                                                             const int* __restrict__ pstart,
+                                                                             const float* __restrict__ x,
+                                                                             float* __restrict__ y) {
+  if ((int)blockIdx.x >= ntasks) {
+    const int b = blockIdx.x - ntasks;
+    const int per_macro = 6 * nfb + 1;
+    const int macro = b / per_macro, r = b - macro * per_macro;
+    const int f = min(r / nfb, 6);
+    p1_face_slice<float, DIRICHLET>(cst[macro], pstart, x, y, f, (r - f * nfb) * 256 + threadIdx.x);
+    return;
   }
-  // rows needing i, i+1: (j-1,k) [4: (0,-1,0), 7: (1,-1,0)], (j-1,k+1) [12, 13], (j,k-1) [6, 9]
-  {
-    const float2 a1 = ld2(p0 + o - kPairW), a2 = ld2(p0 + o - kPairW + 2);
-    acc = fma2(W[4], a1, acc);
-    acc = fma2(W[7], make_float2(a1.y, a2.x), acc);
-    const float2 b1 = ld2(pp + o - kPairW), b2 = ld2(pp + o - kPairW + 2);
-    acc = fma2(W[12], b1, acc);
-    acc = fma2(W[13], make_float2(b1.y, b2.x), acc);
-    const float2 d1 = ld2(pm + o), d2 = ld2(pm + o + 2);
-    acc = fma2(W[6], d1, acc);
-    acc = fma2(W[9], make_float2(d1.y, d2.x), acc);
-  }
-  return acc;
-}
-
-template <bool DIRICHLET>
-__global__ void __launch_bounds__(256, 3) p1_tile_f32_kernel(const OpConst<float>* __restrict__ cst,
-                                                              const int4* __restrict__ tasks, int kch,
-                                                              const int* __restrict__ pstart,
-                                                              const float* __restrict__ x, float* __restrict__ y) {
-  extern __shared__ __align__(16) unsigned char tile_smem[];
-  float* buf = reinterpret_cast<float*>(tile_smem);
   const int4 task = tasks[blockIdx.x];
   const OpConst<float>& c = cst[task.w];
   const int N = c.N;
-  const uint32_t table = c.bnd_table;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = task.x * kTileI, j0 = task.y * kTileJ, k0 = task.z * kch;
-  const int k_end = min(k0 + kch - 1, N - j0 - i0);
-  if (k_end < k0) return;
-  const float* __restrict__ xm = x + c.base;
-  float* __restrict__ ym = y + c.base;
+  const int lane = threadIdx.x & 31;
+  const int j = task.y * kStencilWarps + (threadIdx.x >> 5);
+  const int ib = task.x * 32 * PT;
+  const int k0 = task.z * kch;
+  const int kb = max(k0, 2);
+  // row (j, k) holds a point i >= max(ib, 1) off the macro faces iff ib <= N - j - k - 1
+  const int ke = min(min(k0 + kch - 1, N - j - ib - 1), N - kP1ClimbTop);
+  if (j < 2 || ke < kb) return;   // whole warps only; the kernel has no barrier
+  // faces i = 0 and i + j + k = N: zero sets {i} and {i+j+k = N} of the boundary table
+  const bool dir_i0 = DIRICHLET && ((c.bnd_table >> 2) & 1u);
+  const bool dir_diag = DIRICHLET && ((c.bnd_table >> 1) & 1u);
+  const float* __restrict__ xb = x + c.base + ib + lane;
+  float* __restrict__ yb = y + c.base + ib + lane;
   float S[15];
 #pragma unroll
   for (int d = 0; d < 15; ++d) S[d] = c.S[d];
-  const int j = j0 + warp;
-  const int r = warp + 1;
-  for (int q = 0; q <= kTileDepth; ++q) {
-    const int kk = k0 - 1 + q;
-    if (kk <= k_end + 1) p1_issue_plane_f32(buf + q * kPairSlot, xm, pstart, N, i0, j0, kk);
-    cp_async_commit();
+  P1Climb<PT> R;
+  auto at = [&](int jr, int kr) { return __ldg(pstart + kr) + row32(N - kr, jr); };
+  // planes kb-1 .. kb+1 for step 0 (slots of U = 0)
+  p1_climb_row<-1, 0, PT>(R.P[0], xb + at(j + 1, kb - 1));
+  p1_climb_row<-1, 0, PT>(R.P[1], xb + at(j + 1, kb));
+  p1_climb_row<-1, 1, PT>(R.Z[0], xb + at(j, kb - 1));
+  p1_climb_row<-1, 1, PT>(R.Z[1], xb + at(j, kb));
+  p1_climb_row<-1, 1, PT>(R.Z[2], xb + at(j, kb + 1));
+  p1_climb_row<0, 1, PT>(R.M[0], xb + at(j - 1, kb));
+  p1_climb_row<0, 1, PT>(R.M[1], xb + at(j - 1, kb + 1));
+  R.ap = at(j + 1, kb + 1);
+  R.am = at(j - 1, kb + 2);
+  R.az = at(j, kb + 2);
+  R.ay = at(j, kb);
+  R.t0 = tri(N - kb);
+  if (kClimbAhead > 1) {
+    // planes up to kb + kClimbAhead + 2 <= N - kP1ClimbTop + kClimbAhead + 2 < N
+    const int off = min(32 * lane, 32 * PT + 1) - 1 - lane;
+    R.fp = at(j + 1, kb + kClimbAhead + 1) + off;
+    R.fm = at(j - 1, kb + kClimbAhead + 2) + off;
+    R.fz = at(j, kb + kClimbAhead + 2) + off;
+    R.ta = tri(N - kb - kClimbAhead);
   }
-  cp_async_wait<kTileDepth - 1>();
-  // a staged plane can hold points of a macro face only if the tile touches i = 0, j = 0, k = 0 or
-  // reaches i + j + k = N; only then are its Dirichlet points looked for (uniform over the CTA)
-  const bool edge_tile = i0 == 0 || j0 == 0 || i0 + kTileI + j0 + kTileJ + k_end + 1 >= N;
-  if (DIRICHLET && (edge_tile || k0 <= 1)) {
-    p1_mask_plane_f32(buf, N, table, i0, j0, k0 - 1);
-    p1_mask_plane_f32(buf + kPairSlot, N, table, i0, j0, k0);
+  for (int k = kb; k <= ke; k += 12) {
+#define HHG_CLIMB_STEP(U)                                                                                     \
+  if (k + U > ke) break;                                                                                      \
+  p1_climb_step<U, PT, DIRICHLET>(R, S, xb, yb, N, dir_i0, dir_diag, ib, j, k + U, ke);
+    HHG_CLIMB_STEP(0) HHG_CLIMB_STEP(1) HHG_CLIMB_STEP(2) HHG_CLIMB_STEP(3) HHG_CLIMB_STEP(4) HHG_CLIMB_STEP(5)
+    HHG_CLIMB_STEP(6) HHG_CLIMB_STEP(7) HHG_CLIMB_STEP(8) HHG_CLIMB_STEP(9) HHG_CLIMB_STEP(10) HHG_CLIMB_STEP(11)
+#undef HHG_CLIMB_STEP
   }
-  int sm = 0;
-  for (int k = k0; k <= k_end; ++k) {
-    const int s0 = sm + 1 == kTileRing ? 0 : sm + 1;
-    const int sp = s0 + 1 == kTileRing ? 0 : s0 + 1;
-    cp_async_wait<kTileDepth - 2>();
-    if (DIRICHLET && edge_tile) p1_mask_plane_f32(buf + sp * kPairSlot, N, table, i0, j0, k + 1);
-    __syncthreads();
-    {
-      const int kn = k + kTileDepth;
-      int sn = sm + kTileDepth + 1;
-      if (sn >= kTileRing) sn -= kTileRing;
-      if (kn <= k_end + 1) p1_issue_plane_f32(buf + sn * kPairSlot, xm, pstart, N, i0, j0, kn);
-      cp_async_commit();
-    }
-    const float* pm = buf + sm * kPairSlot;
-    const float* p0 = buf + s0 * kPairSlot;
-    const float* pp = buf + sp * kPairSlot;
-    const int len = N - j - k + 1;
-    // rows j = 0 and planes k = 0 hold only points on macro faces (written by p1_face_kernel)
-    if (j > 0 && k > 0 && len > 0 && i0 < len) {
-      float* __restrict__ yrow = ym + __ldg(pstart + k) + row32(N - k, j);
-#pragma unroll
-      for (int v = 0; v < kTileI / 64; ++v) {
-        const int p2 = lane + 32 * v;
-        const int ii = i0 + 2 * p2;
-        if (ii >= len) continue;
-        const float2 acc = p1_pair_stencil(S, pm, p0, pp, r, 2 * p2 + 2);
-        // only the points off the macro faces (0 < i < len - 1)
-        if (ii > 0 && ii < len - 1) yrow[ii] = acc.x;
-        if (ii + 1 < len - 1) yrow[ii + 1] = acc.y;
-      }
-    }
-    sm = s0;
-  }
-  cp_async_wait<0>();
 }
-
-constexpr size_t p1_tile_f32_smem() { return sizeof(float) * kTileRing * kPairSlot; }
 
 // ---------------------------------------------------------------------------
 // P2 constant-coefficient apply from shared-memory plane tiles.  A CTA owns rows j0..j0+7 and
@@ -1234,19 +1289,18 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
       HHG_CUDA_TRY(cudaGetLastError());
       return HHG_OK;
     }
-    const unsigned grid = (unsigned)I->tile[0].n;
-    const size_t smem = p1_tile_f32_smem();
+    const TileTasks& tt = I->tile[kClimbPT == 4 ? 0 : 1];
     const OpConst<float>* cf = (const OpConst<float>*)op->d_const32;
-    const dim3 fgrid((unsigned)((tri_host(op->N) + 255) / 256), 4, nm);
-    if (op->bc == HHG_DIRICHLET) {
-      p1_tile_f32_kernel<true><<<grid, 256, smem, s>>>(cf, I->tile[0].d, I->tile[0].kchunk, I->d_pstart,
-                                                       (const float*)x, (float*)y);
-      p1_face_kernel<float, true><<<fgrid, 256, 0, s>>>(cf, I->d_pstart, (const float*)x, (float*)y);
-    } else {
-      p1_tile_f32_kernel<false><<<grid, 256, smem, s>>>(cf, I->tile[0].d, I->tile[0].kchunk, I->d_pstart,
-                                                        (const float*)x, (float*)y);
-      p1_face_kernel<float, false><<<fgrid, 256, 0, s>>>(cf, I->d_pstart, (const float*)x, (float*)y);
-    }
+    // face blocks: slices 0-5 need tri(N) threads each, the top planes at most V(kP1ClimbTop - 1) <= 256
+    static_assert(kP1ClimbTop * (kP1ClimbTop + 1) * (kP1ClimbTop + 2) / 6 <= 256, "top planes exceed one block");
+    const int nfb = (int)((tri_host(op->N) + 255) / 256);
+    const unsigned grid = (unsigned)(tt.n + (int64_t)nm * (6 * nfb + 1));
+    if (op->bc == HHG_DIRICHLET)
+      p1_climb_f32_kernel<kClimbPT, true><<<grid, 256, 0, s>>>(cf, tt.d, (int)tt.n, tt.kchunk, nfb, I->d_pstart,
+                                                               (const float*)x, (float*)y);
+    else
+      p1_climb_f32_kernel<kClimbPT, false><<<grid, 256, 0, s>>>(cf, tt.d, (int)tt.n, tt.kchunk, nfb, I->d_pstart,
+                                                                (const float*)x, (float*)y);
     HHG_CUDA_TRY(cudaGetLastError());
     return HHG_OK;
   }

@@ -113,3 +113,19 @@ def test_coordinates(meshname, level, degree):
     xyz = c.mesh.coordinates(degree).cpu().numpy()
     ref = np.concatenate([OM.physical(c.v[c.t[m]], c.S.pts, c.S.N) for m in range(len(c.t))])
     assert np.abs(xyz - ref).max() <= 1e-15
+
+
+@pytest.mark.parametrize("level", [7, 8])
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_p1_const_f32_matches_f64_full_vector(level, bc):
+    """Every point of the FP32 apply (register-climbing kernel + face kernel) at sizes with rows
+    longer than one tile, against the FP64 apply of the same FP32-representable input."""
+    import paper_2404_08371_gb300 as hhg
+    v, t = W.reference_tet()
+    mesh = hhg.Mesh(v, t, level)
+    op = hhg.Operator(mesh, degree=1, coeff=("const", 1.3), bc=bc)
+    x32 = torch.tensor(W.uniform(mesh.vec_size(1), seed=4), device="cuda").float()
+    y32 = op.apply(x32).double()
+    y64 = op.apply(x32.double())
+    assert torch.isfinite(y32).all()
+    assert (y32 - y64).abs().max().item() <= 1e-5 * y64.abs().max().item()
