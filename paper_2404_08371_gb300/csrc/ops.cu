@@ -779,7 +779,8 @@ __global__ void __launch_bounds__(256, PT == 4 ? 2 : 3) p1_climb_f32_kernel(cons
 // arrival.  A lane evaluates the points i0 + 64 v + 2 lane + {0, 1}: both node parities of its row,
 // so a warp never diverges between stencils, with offsets known at compile time.  Even and odd
 // staged columns are kept apart (column c at (c & 1) W/2 + c/2), so the 32 lanes of a warp read 32
-// consecutive words.  The tile writes the points off the macro faces; p2_face_kernel the rest.
+// consecutive words.  The tile writes the points off the macro faces; p2_face_point the rest (extra
+// blocks of the same launch).
 constexpr int kP2TileJ = 8;
 constexpr int kP2TileH = kP2TileJ + 4;
 constexpr int kP2Ahead = 2;
@@ -920,7 +921,7 @@ __device__ __forceinline__ void p2_tile_pair(const typename P2W<T>::type* w, con
 }
 
 // Interior points of one tile row (row parity PA): the second half of a 128-point tile only when
-// the row reaches into it.  Points on macro faces are left to p2_face_kernel.
+// the row reaches into it.  Points on macro faces are left to p2_face_point.
 template <typename T, int W, int NV, int PA>
 __device__ __forceinline__ void p2_tile_row(const typename P2W<T>::type* w, const T* const (&pl)[5], int ob, int i0,
                                             int len, T* __restrict__ yrow) {
@@ -945,16 +946,83 @@ __device__ __forceinline__ void p2_tile_row(const typename P2W<T>::type* w, cons
   }
 }
 
+// Points on the faces of the macros (zero mask z != 0), one thread each (thread t of face f): face a
+// of the macro has the points (a, b) with a + b <= N of its triangle; a point on several faces is
+// written by the lowest.  Its row comes from the face table (zero weights outside the macro); x is
+// read from global memory.  offs / starts: the stencil offsets and class starts, staged in shared
+// memory by the caller.
+template <typename T, bool DIRICHLET>
+__device__ __forceinline__ void p2_face_point(const OpConst<T>& c, const P2Stencil<T>& stm, const int* offs,
+                                              const int* starts, const int* __restrict__ pstart,
+                                              const T* __restrict__ x, T* __restrict__ y, int f, int t) {
+  const int N = c.N;
+  if (t >= tri(N)) return;
+  const float bq = 2.0f * N + 3.0f;
+  int b = (int)(0.5f * (bq - sqrtf(fmaxf(bq * bq - 8.0f * (float)t, 0.0f))));
+  b = max(0, min(b, N));
+  if (b < N && row32(N, b + 1) <= t) ++b;
+  if (b > 0 && row32(N, b) > t) --b;
+  const int a = t - row32(N, b);
+  int i, j, k;
+  if (f == 0) {
+    i = 0; j = a; k = b;
+  } else if (f == 1) {
+    i = a; j = 0; k = b;
+  } else if (f == 2) {
+    i = a; j = b; k = 0;
+  } else {
+    i = N - a - b; j = a; k = b;
+  }
+  if ((f >= 1 && i == 0) || (f >= 2 && j == 0) || (f == 3 && k == 0)) return;
+  const T* __restrict__ xm = x + c.base;
+  T* __restrict__ ym = y + c.base;
+  const uint32_t table = c.bnd_table;
+  const int p = __ldg(pstart + k) + row32(N - k, j) + i;
+  if (DIRICHLET && on_dirichlet(table, N, i, j, k)) {
+    ym[p] = xm[p];
+    return;
+  }
+  const int z = zero_mask(N, i, j, k);
+  const T* __restrict__ wz = stm.w[z];
+  const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+  T acc = T(0);
+  const int d1 = starts[par + 1];
+  for (int d = starts[par]; d < d1; ++d) {
+    const T w = __ldg(wz + d);
+    if (w == T(0)) continue;   // no micro-tet of the macro couples the two points
+    const int o = offs[d];
+    const int ii = i + (o & 15) - 2, jj = j + ((o >> 4) & 15) - 2, kk = k + ((o >> 8) & 15) - 2;
+    if (DIRICHLET && on_dirichlet(table, N, ii, jj, kk)) continue;
+    acc += w * __ldg(xm + __ldg(pstart + kk) + row32(N - kk, jj) + ii);
+  }
+  ym[p] = acc;
+}
+
 template <typename T, int TI, bool DIRICHLET>
 __global__ void __launch_bounds__(256) p2_tile_kernel(const OpConst<T>* __restrict__ cst,
                                                       const P2Stencil<T>* __restrict__ st,
-                                                      const int4* __restrict__ tasks, int kch,
+                                                      const P2StencilIndex* __restrict__ sidx,
+                                                      const int4* __restrict__ tasks, int ntasks, int kch, int nfb,
                                                       const int* __restrict__ pstart, const T* __restrict__ x,
                                                       T* __restrict__ y) {
   constexpr int W = TI + 4;
   constexpr int SLOT = W * kP2TileH;
   constexpr int NV = TI / 64;
   extern __shared__ __align__(16) unsigned char p2_tile_smem_raw[];
+  if ((int)blockIdx.x >= ntasks) {
+    // blocks after the tile tasks write the face points (4 faces x nfb blocks per macro), filling the
+    // SMs that the last tiles leave idle
+    int* offs = reinterpret_cast<int*>(p2_tile_smem_raw);
+    int* starts = offs + kP2StTotal;
+    for (int t = threadIdx.x; t < kP2StTotal; t += blockDim.x) offs[t] = sidx->off[t];
+    if (threadIdx.x < 9) starts[threadIdx.x] = sidx->start[threadIdx.x];
+    __syncthreads();
+    const int b = blockIdx.x - ntasks;
+    const int macro = b / (4 * nfb), r = b - macro * 4 * nfb;
+    const int f = r / nfb;
+    p2_face_point<T, DIRICHLET>(cst[macro], st[macro], offs, starts, pstart, x, y, f, (r - f * nfb) * 256 + threadIdx.x);
+    return;
+  }
   using WT = typename P2W<T>::type;
   T* buf = reinterpret_cast<T*>(p2_tile_smem_raw);
   WT* w0 = reinterpret_cast<WT*>(buf + kP2Ring * SLOT);
@@ -1018,65 +1086,6 @@ __global__ void __launch_bounds__(256) p2_tile_kernel(const OpConst<T>* __restri
   cp_async_wait<0>();
 }
 
-// Points on the faces of the macros (zero mask z != 0), one thread each: face a of the macro has the
-// points (a, b) with a + b <= N of its triangle; a point on several faces is written by the lowest.
-// Its row comes from the face table (zero weights outside the macro); x is read from global memory.
-template <typename T, bool DIRICHLET>
-__global__ void __launch_bounds__(256) p2_face_kernel(const OpConst<T>* __restrict__ cst,
-                                                      const P2Stencil<T>* __restrict__ st,
-                                                      const P2StencilIndex* __restrict__ sidx,
-                                                      const int* __restrict__ pstart, const T* __restrict__ x,
-                                                      T* __restrict__ y) {
-  __shared__ int offs[kP2StTotal];
-  __shared__ int starts[9];
-  for (int t = threadIdx.x; t < kP2StTotal; t += blockDim.x) offs[t] = sidx->off[t];
-  if (threadIdx.x < 9) starts[threadIdx.x] = sidx->start[threadIdx.x];
-  __syncthreads();
-  const int macro = blockIdx.z, f = blockIdx.y;
-  const OpConst<T>& c = cst[macro];
-  const int N = c.N;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= tri(N)) return;
-  const float bq = 2.0f * N + 3.0f;
-  int b = (int)(0.5f * (bq - sqrtf(fmaxf(bq * bq - 8.0f * (float)t, 0.0f))));
-  b = max(0, min(b, N));
-  if (b < N && row32(N, b + 1) <= t) ++b;
-  if (b > 0 && row32(N, b) > t) --b;
-  const int a = t - row32(N, b);
-  int i, j, k;
-  if (f == 0) {
-    i = 0; j = a; k = b;
-  } else if (f == 1) {
-    i = a; j = 0; k = b;
-  } else if (f == 2) {
-    i = a; j = b; k = 0;
-  } else {
-    i = N - a - b; j = a; k = b;
-  }
-  if ((f >= 1 && i == 0) || (f >= 2 && j == 0) || (f == 3 && k == 0)) return;
-  const T* __restrict__ xm = x + c.base;
-  T* __restrict__ ym = y + c.base;
-  const uint32_t table = c.bnd_table;
-  const int p = __ldg(pstart + k) + row32(N - k, j) + i;
-  if (DIRICHLET && on_dirichlet(table, N, i, j, k)) {
-    ym[p] = xm[p];
-    return;
-  }
-  const int z = zero_mask(N, i, j, k);
-  const T* __restrict__ wz = st[macro].w[z];
-  const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-  T acc = T(0);
-  const int d1 = starts[par + 1];
-  for (int d = starts[par]; d < d1; ++d) {
-    const T w = __ldg(wz + d);
-    if (w == T(0)) continue;   // no micro-tet of the macro couples the two points
-    const int o = offs[d];
-    const int ii = i + (o & 15) - 2, jj = j + ((o >> 4) & 15) - 2, kk = k + ((o >> 8) & 15) - 2;
-    if (DIRICHLET && on_dirichlet(table, N, ii, jj, kk)) continue;
-    acc += w * __ldg(xm + __ldg(pstart + kk) + row32(N - kk, jj) + ii);
-  }
-  ym[p] = acc;
-}
 
 // diag(A) for the constant-coefficient operators: sum of A_T[a][a] over the incident micro-tets.
 template <typename T>
@@ -1318,16 +1327,15 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
     constexpr size_t smem = p2_tile_smem<T, TI>();
     static_assert(smem <= 48 * 1024, "P2 tile exceeds the default dynamic shared memory");
     const P2StencilIndex* ix = (const P2StencilIndex*)op->d_p2idx;
-    const dim3 fgrid((unsigned)((tri_host(op->N) + 255) / 256), 4, nm);
-    if (op->bc == HHG_DIRICHLET) {
-      p2_tile_kernel<T, TI, true><<<(unsigned)tt.n, 256, smem, s>>>(dconst<T>(op), st, tt.d, tt.kchunk,
-                                                                    I->d_pstart, x, y);
-      p2_face_kernel<T, true><<<fgrid, 256, 0, s>>>(dconst<T>(op), st, ix, I->d_pstart, x, y);
-    } else {
-      p2_tile_kernel<T, TI, false><<<(unsigned)tt.n, 256, smem, s>>>(dconst<T>(op), st, tt.d, tt.kchunk,
-                                                                     I->d_pstart, x, y);
-      p2_face_kernel<T, false><<<fgrid, 256, 0, s>>>(dconst<T>(op), st, ix, I->d_pstart, x, y);
-    }
+    static_assert(smem >= sizeof(int) * (kP2StTotal + 9), "face blocks stage the stencil index in the tile's shared memory");
+    const int nfb = (int)((tri_host(op->N) + 255) / 256);
+    const unsigned grid = (unsigned)(tt.n + (int64_t)nm * 4 * nfb);
+    if (op->bc == HHG_DIRICHLET)
+      p2_tile_kernel<T, TI, true><<<grid, 256, smem, s>>>(dconst<T>(op), st, ix, tt.d, (int)tt.n, tt.kchunk, nfb,
+                                                          I->d_pstart, x, y);
+    else
+      p2_tile_kernel<T, TI, false><<<grid, 256, smem, s>>>(dconst<T>(op), st, ix, tt.d, (int)tt.n, tt.kchunk, nfb,
+                                                           I->d_pstart, x, y);
     HHG_CUDA_TRY(cudaGetLastError());
     return HHG_OK;
   }
