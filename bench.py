@@ -545,7 +545,7 @@ def main():
     order = list(min(itertools.permutations(legs), key=modelled_ms))
     comp = torch.cuda.current_stream()
     h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
-    e2e_ms = []
+    e2e_ms, e2e_apply_ms = [], []
     for s in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -556,20 +556,26 @@ def main():
                 ev = torch.cuda.Event()
                 ev.record(h2d_s)
                 ready.append(ev)
+        spans = []
         for L, ev in zip(order, ready):
             comp.wait_event(ev)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a0.record(comp)
             L["op"].apply(L["x"], out=L["y"])
-            done = torch.cuda.Event()
+            done = torch.cuda.Event(enable_timing=True)
             done.record(comp)
+            spans.append((a0, done))
             d2h_s.wait_event(done)
             with torch.cuda.stream(d2h_s):
                 L["hy"].copy_(L["y"], non_blocking=True)
         torch.cuda.synchronize()
         if s >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            e2e_apply_ms.append(sum(a.elapsed_time(b) for a, b in spans))
     _, _, e2e_value = aggregate_replicas(statistics.mean(e2e_ms), dofs_step, dev)
     e2e_detail = {"order": [L["name"] for L in order], "h2d_gbs": h2d_rate / 1e6, "d2h_gbs": d2h_rate / 1e6,
-                  "modelled_ms": modelled_ms(order), "measured_ms": statistics.mean(e2e_ms)}
+                  "modelled_ms": modelled_ms(order), "measured_ms": statistics.mean(e2e_ms),
+                  "applies_ms": statistics.mean(e2e_apply_ms)}
 
     peaks = load_peaks()
     traffic = load_traffic()
@@ -641,6 +647,7 @@ def main():
     if cb is not None:
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         line["cpu_baseline"]["legs"] = cb["legs"]
+        line["cpu_baseline"]["fmg"] = cb["fmg"]
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -102,6 +102,9 @@ __device__ __forceinline__ void eps_test_moments(const T S3[3][3], const T R3[3]
   }
 }
 
+// Index of the entry (c, d) of a symmetric 3 x 3 tensor stored as (0,0) (1,1) (2,2) (0,1) (0,2) (1,2).
+__device__ __forceinline__ int eps_sym(int c, int d) { return c == d ? c : c + d + 2; }
+
 // grad of component fields: G[c][d] = d u_c / d x_d = sum_e Jinv[e][d] ghat_c[e]
 template <typename T>
 __device__ __forceinline__ void phys_grad(const T* Ji, const T gh[3], T G[3]) {
@@ -111,9 +114,17 @@ __device__ __forceinline__ void phys_grad(const T* Ji, const T gh[3], T G[3]) {
 
 // MODE 0: out += A u (all right-hand sides); MODE 2: out_m += sum_r g_r^T (dA/dmu_m) u_r.
 // One CTA per task of its colour: up to cpb consecutive cubes of one row (cj, ck) of one macro,
-// times the right-hand sides.
+// times the right-hand sides.  MODE 0 keeps each thread's affine gradient terms P (36 values) and
+// nodal mu (10) in shared memory, column threadIdx.x of a [value][thread] array: the quadrature
+// loop then holds only the 36 stress moments and one gradient in registers, which lets two CTAs
+// (16 warps) share an SM to keep the FP64 pipes fed; reading P costs 36 shared loads per point
+// against about 90 FP64 operations.
+constexpr int kEpsThreads = 256;
+template <typename T, bool FIELD>
+constexpr size_t eps_apply_smem() { return (sizeof(T) * (36 + (FIELD ? kMaxQ : 0)) + sizeof(int) * 10) * kEpsThreads; }
+
 template <typename T, int MODE, bool FIELD, bool DIR>
-__global__ void __launch_bounds__(256) eps_color_kernel(const OpConst<T>* __restrict__ cst,
+__global__ void __launch_bounds__(kEpsThreads, MODE == 0 ? 2 : 1) eps_color_kernel(const OpConst<T>* __restrict__ cst,
                                                          const int4* __restrict__ tasks, int color, int cpb,
                                                          int nrhs, T mu_const, const T* __restrict__ x,
                                                          const T* __restrict__ g, const T* __restrict__ mu,
@@ -132,87 +143,124 @@ __global__ void __launch_bounds__(256) eps_color_kernel(const OpConst<T>* __rest
   if (MODE == 2 && __all_sync(0xffffffffu, !live)) return;
   const int64_t base = c.base;
   const int stride = 3 * nrhs;
+  extern __shared__ __align__(16) unsigned char eps_smem_raw[];
+  T* __restrict__ Ps = reinterpret_cast<T*>(eps_smem_raw) + threadIdx.x;   // MODE 0: P[v] at Ps[v * kEpsThreads]
+  T* __restrict__ Ms = Ps + 36 * kEpsThreads;   // MODE 0, field: mu(x_q) w_q |det J| at the points
+  int* __restrict__ Is = reinterpret_cast<int*>(reinterpret_cast<T*>(eps_smem_raw) + (FIELD ? 36 + kMaxQ : 36) * kEpsThreads) +
+                         threadIdx.x;           // MODE 0: node indices
+#pragma unroll 1
   for (int o = 0; o < 6; ++o) {
     const bool tet_ok = live && ci + cj + ck <= n - 1 - (o == 0 ? 0 : (o == 5 ? 2 : 1));
     if (MODE == 0 && !tet_ok) continue;
-    int64_t idx[10];
-    T u[3][10], gv[3][10], m[10];
+    int idx[10], masked = 0;   // bit a: node a reads as zero (Dirichlet point or no micro-tet)
+    T m[10];
 #pragma unroll
     for (int a = 0; a < 10; ++a) {
       const int pi = 2 * ci + enode_d(o, a, 0), pj = 2 * cj + enode_d(o, a, 1), pk = 2 * ck + enode_d(o, a, 2);
-      idx[a] = tet_ok ? packed_index(N, pi, pj, pk) : 0;
-      const bool masked = !tet_ok || (DIR && on_dirichlet(c.bnd_table, N, pi, pj, pk));
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) {
-        const int64_t e = (base + idx[a]) * stride + cc * nrhs + r;
-        u[cc][a] = masked ? T(0) : __ldg(x + e);
-        if (MODE == 2) gv[cc][a] = masked ? T(0) : __ldg(g + e);
-      }
-      m[a] = FIELD ? (tet_ok ? __ldg(mu + base + idx[a]) : T(0)) : mu_const;
+      idx[a] = tet_ok ? (int)packed_index(N, pi, pj, pk) : 0;
+      if (MODE == 0) Is[a * kEpsThreads] = idx[a];
+      if (!tet_ok || (DIR && on_dirichlet(c.bnd_table, N, pi, pj, pk))) masked |= 1 << a;
+      if (MODE == 0 && FIELD) m[a] = __ldg(mu + base + idx[a]);
     }
     const T* Ji = c.Jinv[o];
     const T wdet = c.adet[o];
-    T y[3][10];
+    if (MODE == 0 && FIELD) {
+      // mu at the quadrature points, times the weight and |det J|, once per micro-tet
+#pragma unroll 1
+      for (int q = 0; q < c.nq; ++q) {
+        T muq = T(0);
+#pragma unroll
+        for (int a = 0; a < 10; ++a) muq += c.psi[q][a] * m[a];
+        Ms[q * kEpsThreads] = muq * c.w[q] * wdet;
+      }
+    }
     T dmu[10];
 #pragma unroll
-    for (int a = 0; a < 10; ++a) {
-      y[0][a] = y[1][a] = y[2][a] = T(0);
-      dmu[a] = T(0);
-    }
+    for (int a = 0; a < 10; ++a) dmu[a] = T(0);
     // physical gradients of the components, affine in lambda: G_c = P[c][0] + sum_b lambda_b P[c][b]
-    T P[3][4][3];
+    // (MODE 0: one component at a time into shared memory, P[c][t][d] at Ps[(12 c + 3 t + d) kEpsThreads])
+    T P[3][4][3], gv[3][10];
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
-      T W[4][3];
-      eps_grad_affine<T>(u[cc], W);
+      T u[10], W[4][3];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) phys_grad<T>(Ji, W[t], P[cc][t]);
+      for (int a = 0; a < 10; ++a) {
+        const int64_t e = (base + idx[a]) * stride + cc * nrhs + r;
+        u[a] = (masked >> a) & 1 ? T(0) : __ldg(x + e);
+        if (MODE == 2) gv[cc][a] = (masked >> a) & 1 ? T(0) : __ldg(g + e);
+      }
+      eps_grad_affine<T>(u, W);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        phys_grad<T>(Ji, W[t], P[cc][t]);
+        if (MODE == 0)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) Ps[(12 * cc + 3 * t + d) * kEpsThreads] = P[cc][t][d];
+      }
     }
     if (MODE == 0) {
-      // physical moments of the stress: Q[c][0] = sum_q S_c, Q[c][b] = sum_q lambda_b S_c
-      T Q[3][4][3];
+      // physical moments of the stress: Q[t][v] = sum_q lambda_t S_v (lambda_0 = 1), S = s (G + G^T)
+      // = 2 mu eps(u) w |det J| symmetric, so only its six entries v = (0,0) (1,1) (2,2) (0,1) (0,2)
+      // (1,2) are accumulated (the entry of (c, d) is eps_sym(c, d))
+      T Q[4][6];
 #pragma unroll
-      for (int cc = 0; cc < 3; ++cc)
+      for (int t = 0; t < 4; ++t)
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) Q[cc][t][d] = T(0);
+        for (int v = 0; v < 6; ++v) Q[t][v] = T(0);
+#pragma unroll 1
       for (int q = 0; q < c.nq; ++q) {
         const T l1 = c.lam[q][1], l2 = c.lam[q][2], l3 = c.lam[q][3];
         T G[3][3];
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc)
 #pragma unroll
-          for (int d = 0; d < 3; ++d)
-            G[cc][d] = fma(l3, P[cc][3][d], fma(l2, P[cc][2][d], fma(l1, P[cc][1][d], P[cc][0][d])));
-        T muq = T(0);
-#pragma unroll
-        for (int a = 0; a < 10; ++a) muq += c.psi[q][a] * m[a];
-        const T s = muq * c.w[q] * wdet;
-        // S = s (G + G^T) = 2 mu eps(u) w |det J|
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc)
-#pragma unroll
           for (int d = 0; d < 3; ++d) {
-            const T Sd = s * (G[cc][d] + G[d][cc]);
-            Q[cc][0][d] += Sd;
-            Q[cc][1][d] = fma(l1, Sd, Q[cc][1][d]);
-            Q[cc][2][d] = fma(l2, Sd, Q[cc][2][d]);
-            Q[cc][3][d] = fma(l3, Sd, Q[cc][3][d]);
+            const T* pc = Ps + (12 * cc + d) * kEpsThreads;
+            G[cc][d] = fma(l3, pc[9 * kEpsThreads], fma(l2, pc[6 * kEpsThreads], fma(l1, pc[3 * kEpsThreads], pc[0])));
           }
-      }
-      // y_c += sum_q (J^{-1} S_c) . grad_ref phi: map the moments back once, then test
+        const T s = FIELD ? Ms[q * kEpsThreads] : mu_const * c.w[q] * wdet;
+        const T s2 = s + s;
+        T Sv[6];
+        Sv[0] = s2 * G[0][0];
+        Sv[1] = s2 * G[1][1];
+        Sv[2] = s2 * G[2][2];
+        Sv[3] = s * (G[0][1] + G[1][0]);
+        Sv[4] = s * (G[0][2] + G[2][0]);
+        Sv[5] = s * (G[1][2] + G[2][1]);
 #pragma unroll
+        for (int v = 0; v < 6; ++v) {
+          Q[0][v] += Sv[v];
+          Q[1][v] = fma(l1, Sv[v], Q[1][v]);
+          Q[2][v] = fma(l2, Sv[v], Q[2][v]);
+          Q[3][v] = fma(l3, Sv[v], Q[3][v]);
+        }
+      }
+      // y_c += sum_q (J^{-1} S_c) . grad_ref phi: map the moments back once, then test; the moments
+      // go to shared memory (over P, no longer needed) so that one component at a time is in
+      // registers, and each component is added to out as soon as it is formed
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int v = 0; v < 6; ++v) Ps[(6 * t + v) * kEpsThreads] = Q[t][v];
+#pragma unroll 1
       for (int cc = 0; cc < 3; ++cc) {
-        T R3[3], S3[3][3];
+        T R3[3], S3[3][3], yc[10], Qc[4][3];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) Qc[t][d] = Ps[(6 * t + eps_sym(cc, d)) * kEpsThreads];
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-          R3[e] = Ji[e * 3 + 0] * Q[cc][0][0] + Ji[e * 3 + 1] * Q[cc][0][1] + Ji[e * 3 + 2] * Q[cc][0][2];
+          R3[e] = Ji[e * 3 + 0] * Qc[0][0] + Ji[e * 3 + 1] * Qc[0][1] + Ji[e * 3 + 2] * Qc[0][2];
 #pragma unroll
           for (int b = 0; b < 3; ++b)
-            S3[e][b] = Ji[e * 3 + 0] * Q[cc][b + 1][0] + Ji[e * 3 + 1] * Q[cc][b + 1][1] + Ji[e * 3 + 2] * Q[cc][b + 1][2];
+            S3[e][b] = Ji[e * 3 + 0] * Qc[b + 1][0] + Ji[e * 3 + 1] * Qc[b + 1][1] + Ji[e * 3 + 2] * Qc[b + 1][2];
         }
-        eps_test_moments<T>(S3, R3, y[cc]);
+#pragma unroll
+        for (int a = 0; a < 10; ++a) yc[a] = T(0);
+        eps_test_moments<T>(S3, R3, yc);
+#pragma unroll
+        for (int a = 0; a < 10; ++a) out[(base + Is[a * kEpsThreads]) * stride + cc * nrhs + r] += yc[a];
       }
     } else {
       T Pg[3][4][3];
@@ -243,15 +291,7 @@ __global__ void __launch_bounds__(256) eps_color_kernel(const OpConst<T>* __rest
         for (int a = 0; a < 10; ++a) dmu[a] += c.psi[q][a] * tq;
       }
     }
-    if (MODE == 0) {
-#pragma unroll
-      for (int a = 0; a < 10; ++a)
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          const int64_t e = (base + idx[a]) * stride + cc * nrhs + r;
-          out[e] += y[cc][a];
-        }
-    } else {
+    if (MODE == 2) {
       // sum over the right-hand sides of this cube (consecutive lanes of one warp), one writer
 #pragma unroll
       for (int a = 0; a < 10; ++a)
@@ -290,7 +330,7 @@ int launch_eps(const hhg_op* op, const OpConst<T>* cst, int mode, int nrhs, cons
     return fail(HHG_E_UNSUPPORTED, "epsilon adjoint: nrhs must divide 32");
   if (nrhs > 256) return fail(HHG_E_UNSUPPORTED, "epsilon: at most 256 right-hand sides per call");
   // tasks of live cubes per colour (cached in the operator for this number of cubes per CTA)
-  const int cpb = 256 / nrhs;
+  const int cpb = kEpsThreads / nrhs;
   if (op->eps_cpb != cpb) {
     std::vector<int4> tv;
     int64_t off[9];
@@ -322,7 +362,14 @@ int launch_eps(const hhg_op* op, const OpConst<T>* cst, int mode, int nrhs, cons
     const unsigned grid = (unsigned)(op->eps_off[color + 1] - op->eps_off[color]);
     if (grid == 0) continue;
     const int4* tk = op->d_eps_tasks + op->eps_off[color];
-#define HHG_EPS(M, F, D) eps_color_kernel<T, M, F, D><<<grid, 256, 0, s>>>(cst, tk, color, cpb, nrhs, muc, x, g, mu, out)
+#define HHG_EPS(M, F, D)                                                                                       \
+  do {                                                                                                       \
+    const size_t sm = M == 0 ? eps_apply_smem<T, F>() : 0;                                                   \
+    if (sm > 48 * 1024)                                                                                      \
+      HHG_CUDA_TRY(cudaFuncSetAttribute(eps_color_kernel<T, M, F, D>,                                      \
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));              \
+    eps_color_kernel<T, M, F, D><<<grid, kEpsThreads, sm, s>>>(cst, tk, color, cpb, nrhs, muc, x, g, mu, out); \
+  } while (0)
     const bool dir = op->bc == HHG_DIRICHLET;
     if (mode == 0) {
       if (field) {
