@@ -10,8 +10,11 @@
 //   i: a lane adds the low-i face of its right neighbour (warp shuffle);
 //   j: a warp adds the low-j face of the warp above it (shared memory);
 //   k: the top face of a cube is carried in registers to the next layer.
-// Adjacent CTAs overlap by one cube in i and j; the overlapping cube's points are
-// written by exactly one of them, so every point is written once.
+// Adjacent CTAs overlap by one cube in i (and in j on small lattices); the overlapping cube's
+// points are written by exactly one of them.  On lattices of at least kMarchJAtomicN cubes per edge
+// the tiles do not overlap in j: the output is zeroed first, the points on a tile's two j-faces are
+// added atomically by the two tiles that share them, all others are stored once, and the Dirichlet
+// rows are written afterwards by march_dirichlet_kernel.
 //
 // Local matrices are never stored: the quadrature is fused with the local apply
 // (Remark 4.1): grad u at each point from the 10 nodal values, scaled by
@@ -220,7 +223,7 @@ __device__ __forceinline__ void sincos2pi<float>(float x, float* s, float* c) {
 
 // AFF (P2, variable coefficient, APPLY): affine gradient + moment test (rules of many points) or the
 // tabulated direct form (rules of few points).
-template <typename T, int R, int COEF, int MODE, bool DIR, bool AFF = true>
+template <typename T, int R, int COEF, int MODE, bool DIR, bool AFF = true, bool JATOM = false>
 __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __restrict__ cst,
                                                             const int4* __restrict__ tasks, int kChunk,
                                                             const T* __restrict__ x, const T* __restrict__ g,
@@ -248,16 +251,18 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n = c.n, N = c.N;
-  const int ti0 = 31 * task.x, tj0 = (kWarps - 1) * task.y, K0 = kChunk * kc;
+  constexpr int JW = JATOM ? kWarps : kWarps - 1;   // rows of cubes owned along j
+  const int ti0 = 31 * task.x, tj0 = JW * task.y, K0 = kChunk * kc;
   if (ti0 + tj0 + K0 > n) return;   // lowest point owned by the CTA lies outside the macro (uniform)
   const int ci = ti0 + lane - 1;
-  const int cj = tj0 + warp - 1;
+  const int cj = tj0 + warp - (JATOM ? 0 : 1);
   const int ck_last = min(K0 + kChunk - 1, n - ti0 - tj0);
   const int64_t base = c.base;
   const uint32_t table = c.bnd_table;
   // owned local index ranges in i (lanes) and j (warps)
   const int a_lo = lane == 0 ? R : 1, a_hi = lane == 31 ? R - 1 : R;
-  const int b_lo = warp == 0 ? R : 1, b_hi = warp == kWarps - 1 ? R - 1 : R;
+  // (JATOM: warp 0 also owns its low face and the last warp its high face, both added atomically)
+  const int b_lo = warp == 0 ? (JATOM ? 0 : R) : 1, b_hi = (warp == kWarps - 1 && !JATOM) ? R - 1 : R;
 
   T carry[P * P];
 #pragma unroll
@@ -590,6 +595,15 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
             if (pi < 0 || pj < 0 || pi + pj + pk > N) continue;
             const int64_t idx = base + packed_index(N, pi, pj, pk);
             T v = acc[cx + P * (cy + P * cz)];
+            if (JATOM) {
+              // Dirichlet rows: written by march_dirichlet_kernel (the output is zeroed before)
+              if (DIR && MODE != MODE_ADJ && on_dirichlet(table, N, pi, pj, pk)) continue;
+              if (cy == 0 || (cy == R && warp == kWarps - 1))
+                atomicAdd(out + idx, v);   // a j-face shared with the tile below / above
+              else
+                out[idx] = v;
+              continue;
+            }
             if (DIR && MODE != MODE_ADJ && on_dirichlet(table, N, pi, pj, pk))
               v = (MODE == MODE_APPLY || MODE == MODE_N1) ? x[idx] : (MODE == MODE_DIAG ? T(1) : T(0));
             out[idx] = v;
@@ -598,12 +612,66 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
   }
 }
 
+// Dirichlet rows after an atomic-j march: y = x (apply, Nedelec), 1 (diagonal); one thread per point
+// of each face triangle (face f, point t), a point on several faces written more than once with the
+// same value.
+template <typename T>
+__global__ void march_dirichlet_kernel(const OpConst<T>* __restrict__ cst, int mode, const T* __restrict__ x,
+                                       T* __restrict__ y) {
+  const OpConst<T>& c = cst[blockIdx.z];
+  const int N = c.N, f = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (N + 1) * (N + 2) / 2) return;
+  // (a, b) with a + b <= N: b by the row starts of the triangle, a the position in the row
+  int b = 0, rem = t;
+  {
+    const float bq = 2.0f * N + 3.0f;
+    b = (int)(0.5f * (bq - sqrtf(fmaxf(bq * bq - 8.0f * (float)t, 0.0f))));
+    b = max(0, min(b, N));
+    auto rs = [&](int r) { return (r * (2 * N + 3 - r)) >> 1; };
+    if (b < N && rs(b + 1) <= t) ++b;
+    if (b > 0 && rs(b) > t) --b;
+    rem = t - rs(b);
+  }
+  const int a = rem;
+  int i, j, k;
+  if (f == 0) {
+    i = 0; j = a; k = b;
+  } else if (f == 1) {
+    i = a; j = 0; k = b;
+  } else if (f == 2) {
+    i = a; j = b; k = 0;
+  } else {
+    i = N - a - b; j = a; k = b;
+  }
+  if (!on_dirichlet(c.bnd_table, N, i, j, k)) return;
+  const int64_t idx = c.base + packed_index(N, i, j, k);
+  y[idx] = mode == MODE_DIAG ? T(1) : x[idx];
+}
+
 template <typename T, int R, int COEF, int MODE, bool AFF = true>
 static int launch_march_t(const hhg_op* op, const OpConst<T>* cst, const T* x, const T* g, const T* kf, T* out,
                           cudaStream_t s, N1Args<T> n1a = N1Args<T>()) {
   const Interface* I = op->itf;
   const unsigned grid = (unsigned)I->n_march_tasks;
-  if (op->bc == HHG_DIRICHLET)
+  const bool dir = op->bc == HHG_DIRICHLET;
+  if (march_jw(op->n) == kMarchWarps) {
+    HHG_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(T) * (size_t)op->npts, s));
+    if (dir)
+      march_kernel<T, R, COEF, MODE, true, AFF, true><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks,
+                                                                                   I->march_kchunk, x, g, kf, out, n1a);
+    else
+      march_kernel<T, R, COEF, MODE, false, AFF, true><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks,
+                                                                                    I->march_kchunk, x, g, kf, out, n1a);
+    HHG_CUDA_TRY(cudaGetLastError());
+    if (dir && (MODE == MODE_APPLY || MODE == MODE_N1 || MODE == MODE_DIAG)) {
+      const dim3 fg((unsigned)((((int64_t)op->N + 1) * (op->N + 2) / 2 + 255) / 256), 4, op->mesh->nmacro());
+      march_dirichlet_kernel<T><<<fg, 256, 0, s>>>(cst, MODE, x, out);
+      HHG_CUDA_TRY(cudaGetLastError());
+    }
+    return HHG_OK;
+  }
+  if (dir)
     march_kernel<T, R, COEF, MODE, true, AFF><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x, g,
                                                                             kf, out, n1a);
   else
