@@ -82,13 +82,15 @@ struct Interface {
   ~Interface();
 };
 
-// Tile shape of the marching kernels (march.cu): 32 lanes along i (31 owned), kMarchWarps warps
-// along j, march_kchunk cube layers along k.  Below kMarchJAtomicN cubes per edge the warps overlap
-// the tile below by one cube (kMarchWarps - 1 owned) and every point is stored once; from
-// kMarchJAtomicN on all kMarchWarps rows of cubes are the tile's own and the two j-faces of a tile
-// are summed into the zeroed output with atomic adds (no cube is integrated twice along j).
+// Tile shape of the marching kernels (march.cu): 32 lanes along i, kMarchWarps warps along j,
+// march_kchunk cube layers along k.  Below kMarchJAtomicN cubes per edge the tiles overlap their
+// neighbours below by one cube in i and j (31 x (kMarchWarps - 1) owned) and every point is stored
+// once; from kMarchJAtomicN on all 32 x kMarchWarps columns of cubes are the tile's own and the
+// points on the tile's i- and j-faces are summed into the zeroed output with atomic adds (no cube is
+// integrated twice along i or j).
 constexpr int kMarchWarps = 8;
 constexpr int kMarchJAtomicN = 64;
+__host__ __device__ constexpr int march_iw(int n) { return n >= kMarchJAtomicN ? 32 : 31; }
 __host__ __device__ constexpr int march_jw(int n) { return n >= kMarchJAtomicN ? kMarchWarps : kMarchWarps - 1; }
 // Tile of the P1 stencil kernel (ops.cu): 8 warps = 8 rows j, 32 lanes x kStencilV points along i.
 constexpr int kStencilWarps = 8;

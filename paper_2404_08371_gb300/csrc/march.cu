@@ -10,10 +10,10 @@
 //   i: a lane adds the low-i face of its right neighbour (warp shuffle);
 //   j: a warp adds the low-j face of the warp above it (shared memory);
 //   k: the top face of a cube is carried in registers to the next layer.
-// Adjacent CTAs overlap by one cube in i (and in j on small lattices); the overlapping cube's
-// points are written by exactly one of them.  On lattices of at least kMarchJAtomicN cubes per edge
-// the tiles do not overlap in j: the output is zeroed first, the points on a tile's two j-faces are
-// added atomically by the two tiles that share them, all others are stored once, and the Dirichlet
+// On small lattices adjacent CTAs overlap by one cube in i and j; the overlapping cube's points
+// are written by exactly one of them.  On lattices of at least kMarchJAtomicN cubes per edge the
+// tiles do not overlap in i or j: the output is zeroed first, the points on a tile's i- and j-faces
+// are added atomically by the tiles that share them, all others are stored once, and the Dirichlet
 // rows are written afterwards by march_dirichlet_kernel.
 //
 // Local matrices are never stored: the quadrature is fused with the local apply
@@ -251,17 +251,17 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n = c.n, N = c.N;
-  constexpr int JW = JATOM ? kWarps : kWarps - 1;   // rows of cubes owned along j
-  const int ti0 = 31 * task.x, tj0 = JW * task.y, K0 = kChunk * kc;
+  constexpr int IW = JATOM ? 32 : 31, JW = JATOM ? kWarps : kWarps - 1;   // cubes owned along i, j
+  const int ti0 = IW * task.x, tj0 = JW * task.y, K0 = kChunk * kc;
   if (ti0 + tj0 + K0 > n) return;   // lowest point owned by the CTA lies outside the macro (uniform)
-  const int ci = ti0 + lane - 1;
+  const int ci = ti0 + lane - (JATOM ? 0 : 1);
   const int cj = tj0 + warp - (JATOM ? 0 : 1);
   const int ck_last = min(K0 + kChunk - 1, n - ti0 - tj0);
   const int64_t base = c.base;
   const uint32_t table = c.bnd_table;
   // owned local index ranges in i (lanes) and j (warps)
-  const int a_lo = lane == 0 ? R : 1, a_hi = lane == 31 ? R - 1 : R;
-  // (JATOM: warp 0 also owns its low face and the last warp its high face, both added atomically)
+  // (JATOM: lane 0 also owns its low face and lane 31 its high face, both added atomically)
+  const int a_lo = lane == 0 ? (JATOM ? 0 : R) : 1, a_hi = (lane == 31 && !JATOM) ? R - 1 : R;
   const int b_lo = warp == 0 ? (JATOM ? 0 : R) : 1, b_hi = (warp == kWarps - 1 && !JATOM) ? R - 1 : R;
 
   T carry[P * P];
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
 #pragma unroll
       for (int cy = 0; cy < P; ++cy) {
         const T v = shfl_down<T>(acc[0 + P * (cy + P * cz)]);
-        acc[R + P * (cy + P * cz)] += v;
+        if (lane < 31) acc[R + P * (cy + P * cz)] += v;
       }
     // j: add the low-j face of the warp above
 #pragma unroll
@@ -598,8 +598,8 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
             if (JATOM) {
               // Dirichlet rows: written by march_dirichlet_kernel (the output is zeroed before)
               if (DIR && MODE != MODE_ADJ && on_dirichlet(table, N, pi, pj, pk)) continue;
-              if (cy == 0 || (cy == R && warp == kWarps - 1))
-                atomicAdd(out + idx, v);   // a j-face shared with the tile below / above
+              if (cx == 0 || cy == 0 || (cx == R && lane == 31) || (cy == R && warp == kWarps - 1))
+                atomicAdd(out + idx, v);   // an i- or j-face shared with a neighbouring tile
               else
                 out[idx] = v;
               continue;

@@ -522,19 +522,19 @@ int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
   // first), with the k-chunk shortened until there are enough tasks to fill the GPU
   {
     const int64_t n = (int64_t)1 << lvl;
-    const int jw = march_jw((int)n);
-    const int jh = jw == kMarchWarps ? 0 : 1;   // overlapping row of cubes below the tile
+    const int iw = march_iw((int)n), jw = march_jw((int)n);
+    const int h = jw == kMarchWarps ? 0 : 1;   // overlapping column / row of cubes below the tile
     int kch = 32;
     std::vector<std::pair<int64_t, int4>> tasks;
     for (;;) {
       tasks.clear();
       for (int64_t kc = 0; kc * kch <= n; ++kc)
         for (int64_t ty = 0; ty * jw + kc * kch <= n; ++ty)
-          for (int64_t tx = 0; tx * 31 + ty * jw + kc * kch <= n; ++tx) {
+          for (int64_t tx = 0; tx * iw + ty * jw + kc * kch <= n; ++tx) {
             int64_t work = 1;   // the top layer still writes carried points
             for (int64_t ck = std::max<int64_t>(kc * kch - 1, 0); ck <= kc * kch + kch - 1; ++ck)
-              for (int64_t cj = std::max<int64_t>(ty * jw - jh, 0); cj <= ty * jw + jw - 1; ++cj) {
-                const int64_t hi = std::min<int64_t>(tx * 31 + 30, n - 1 - cj - ck), lo = std::max<int64_t>(tx * 31 - 1, 0);
+              for (int64_t cj = std::max<int64_t>(ty * jw - h, 0); cj <= ty * jw + jw - 1; ++cj) {
+                const int64_t hi = std::min<int64_t>(tx * iw + iw - 1, n - 1 - cj - ck), lo = std::max<int64_t>(tx * iw - h, 0);
                 if (hi >= lo) work += hi - lo + 1;
               }
             tasks.push_back({work, int4{(int)tx, (int)ty, (int)kc, 0}});

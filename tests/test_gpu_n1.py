@@ -52,6 +52,23 @@ def test_n1_apply_parity(meshname, level, kind, bc, dtype):
     assert np.all(y.reshape(len(t), -1)[:, vert] == 0.0)
 
 
+def test_n1_apply_parity_atomic_tiles():
+    """Level 6 (64 cubes per edge): the marching tiles add the points on their i- and j-faces
+    atomically; every edge checked."""
+    import paper_2404_08371_gb300 as hhg
+    from gpu_helpers import rel_err
+    v, t = W.reference_tet()
+    mesh = hhg.Mesh(v, t, 6)
+    S = OA.EdgeSpace(OM.MacroMesh(v, t), 6)
+    la, lb, oa, ob = _coeffs(S, "field", torch.float64)
+    op = hhg.CurlCurl(mesh, la, lb, bc="dirichlet")
+    xg = W.uniform(S.ndof, seed=0)
+    xp = torch.tensor(OL.n1_to_packed(S, xg), dtype=torch.float64, device="cuda")
+    y = op.apply(xp).cpu().numpy()
+    ref = OA.n1_matrix(S, oa, ob, 4, "dirichlet") @ xg
+    assert rel_err(OL.n1_from_packed(S, y), ref) <= TOL[torch.float64]
+
+
 def test_n1_gradients_in_kernel_level3():
     """curl-curl on discrete gradients vanishes through the GPU apply (Neumann, beta = 0)."""
     import paper_2404_08371_gb300 as hhg
