@@ -141,7 +141,10 @@ int hhg_op_set_field(hhg_op_t* op, const void* field, int field_dtype);
  * vectors of the op's space (ncomp = 3 for EPSILON), nrhs right-hand sides
  * (nrhs >= 1; > 1 only for EPSILON, at most 256, else HHG_E_UNSUPPORTED).
  * y is overwritten; x and y must not overlap.  The apply computes every
- * local matrix on the fly. */
+ * local matrix on the fly.  Variable-coefficient, P2 and Nedelec applies on
+ * lattices of 64 or more cubes per edge add the points on the faces of their
+ * GPU tiles atomically (at most four partial sums a point), so two calls may
+ * differ in the last bits there; all other results repeat bit for bit. */
 int hhg_op_apply(hhg_op_t* op, const void* x, void* y, int dtype, int nrhs, void* stream);
 
 /* Adjoint in the coefficient of a FIELD operator (A is linear in k):
