@@ -68,3 +68,56 @@ def test_symmetry_and_dirichlet_spd():
     # curl-curl alone is singular (gradients); its null space has the dimension of the gradients
     ev = np.linalg.eigvalsh(Kn)
     assert np.sum(np.abs(ev) < 1e-10 * ev.max()) == S.V1.ndof - 1
+
+
+def _n1_field_at(space, u, xi):
+    """E_h at the mapped reference points xi of every element: sum_e u_e s_e phi_e (Whitney)."""
+    J, adet, Jinv = fe.jacobians(space.elem_X)
+    G = np.einsum("eji,aj->eai", Jinv, fe.GRAD_BARY)                  # grad lambda_a, (E, 4, 3)
+    lam = fe.bary(xi)                                                  # (nq, 4)
+    ue = u[space.elem_dofs] * space.elem_sign                          # (E, 6)
+    out = np.zeros((len(space.elem_X), len(xi), 3))
+    for e, (a, b) in enumerate(M.P2_EDGES):
+        phi = lam[None, :, a, None] * G[:, None, b, :] - lam[None, :, b, None] * G[:, None, a, :]
+        out += ue[:, e, None, None] * phi
+    return out, J, adet
+
+
+def test_n1_solution_converges_first_order():
+    """Section 7.3 checks that the Nedelec FMG solution converges as O(h) in L2.  Pinned here on the
+    oracle with a manufactured field on the unit cube: E = (sin pi y sin pi z, sin pi x sin pi z,
+    sin pi x sin pi y) has zero tangential trace on the boundary and div E = 0, so with
+    alpha = beta = 1, curl curl E + E = (2 pi^2 + 1) E.  The Galerkin solution (Dirichlet
+    tangential trace, exact sparse solve) must approach E with ratio about 1/2 per level."""
+    import scipy.sparse.linalg as spla
+    from oracle import quadrature
+
+    def E(p):
+        s = np.sin(np.pi * p)
+        return np.stack([s[:, 1] * s[:, 2], s[:, 0] * s[:, 2], s[:, 0] * s[:, 1]], axis=1)
+
+    mm = M.MacroMesh(*W.cube6())
+    xi, w = quadrature.rule(5)
+    errs = []
+    for level in (1, 2, 3, 4):
+        S = A.EdgeSpace(mm, level)
+        K = A.n1_matrix(S, ("const", 1.0), ("const", 1.0), 4, "dirichlet")
+        # load vector b_e = int f . phi_e, f = (2 pi^2 + 1) E, element by element
+        unit = np.zeros(S.ndof)
+        b = np.zeros(S.ndof)
+        _, J, adet = _n1_field_at(S, unit, xi)
+        pts = fe.map_points(S.elem_X, J, xi)
+        fq = (2 * np.pi ** 2 + 1) * E(pts.reshape(-1, 3)).reshape(len(S.elem_X), len(w), 3)
+        G = np.einsum("eji,aj->eai", fe.jacobians(S.elem_X)[2], fe.GRAD_BARY)
+        lam = fe.bary(xi)
+        for e, (a, c) in enumerate(M.P2_EDGES):
+            phi = lam[None, :, a, None] * G[:, None, c, :] - lam[None, :, c, None] * G[:, None, a, :]
+            be = np.einsum("k,q,kqd,kqd->k", adet, w, fq, phi) * S.elem_sign[:, e]
+            np.add.at(b, S.elem_dofs[:, e], be)
+        b[S.boundary] = 0.0
+        u = spla.spsolve(K.tocsc(), b)
+        Eh, _, _ = _n1_field_at(S, u, xi)
+        err = Eh - E(pts.reshape(-1, 3)).reshape(Eh.shape)
+        errs.append(np.sqrt(np.einsum("k,q,kqd->", adet, w, err ** 2)))
+    ratios = np.array(errs[1:]) / np.array(errs[:-1])
+    assert np.all(ratios < 0.62) and ratios[-1] > 0.4, (errs, ratios)
