@@ -112,23 +112,56 @@ __device__ __forceinline__ void phys_grad(const T* Ji, const T gh[3], T G[3]) {
   for (int d = 0; d < 3; ++d) G[d] = Ji[0 * 3 + d] * gh[0] + Ji[1 * 3 + d] * gh[1] + Ji[2 * 3 + d] * gh[2];
 }
 
-// MODE 0: out += A u (all right-hand sides); MODE 2: out_m += sum_r g_r^T (dA/dmu_m) u_r.
-// One CTA per task of its colour: up to cpb consecutive cubes of one row (cj, ck) of one macro,
-// times the right-hand sides.  MODE 0 keeps each thread's affine gradient terms P (36 values) and
-// nodal mu (10) in shared memory, column threadIdx.x of a [value][thread] array: the quadrature
-// loop then holds only the 36 stress moments and one gradient in registers, which lets two CTAs
-// (16 warps) share an SM to keep the FP64 pipes fed; reading P costs 36 shared loads per point
-// against about 90 FP64 operations.
+// The operator needs only the symmetric gradient E = grad u + grad u^T (six entries, order of
+// eps_sym), and E is affine in lambda like grad u: E(q) = H0 + sum_b lambda_b Hb, with Hb[v] =
+// P[c][b][d] + P[d][b][c] for v = (c, d) from the affine gradient terms P of the components.
+// H (24 values) is summed into the thread's shared-memory column one component at a time.
+template <typename T, int TH>
+__device__ __forceinline__ void eps_sym_affine(const OpConst<T>& c, int o, const int* idx, int masked, const T* __restrict__ x,
+                                               int64_t base, int stride, int comp_stride, T* __restrict__ Hs) {
+  const T* Ji = c.Jinv[o];
+#pragma unroll
+  for (int v = 0; v < 24; ++v) Hs[v * TH] = T(0);
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc) {
+    T u[10], W[4][3];
+#pragma unroll
+    for (int a = 0; a < 10; ++a)
+      u[a] = (masked >> a) & 1 ? T(0) : __ldg(x + (base + idx[a]) * stride + cc * comp_stride);
+    eps_grad_affine<T>(u, W);
+#pragma unroll
+    for (int tt = 0; tt < 4; ++tt) {
+      T p3[3];
+      phys_grad<T>(Ji, W[tt], p3);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Hs[(6 * tt + eps_sym(cc, d)) * TH] += (cc == d ? T(2) : T(1)) * p3[d];
+    }
+  }
+}
+
+template <int TH, typename T>
+__device__ __forceinline__ void eps_sym_at(const T* __restrict__ Hs, T l1, T l2, T l3, T E[6]) {
+#pragma unroll
+  for (int v = 0; v < 6; ++v)
+    E[v] = fma(l3, Hs[(18 + v) * TH], fma(l2, Hs[(12 + v) * TH], fma(l1, Hs[(6 + v) * TH], Hs[v * TH])));
+}
+
+// Apply, out += A u for all right-hand sides.  One CTA per task of its colour: up to cpb
+// consecutive cubes of one row (cj, ck) of one macro, times the right-hand sides.  Each thread
+// keeps its affine symmetric-gradient terms H (24 values), mu(x_q) w_q |det J| at the points and
+// its node indices in its own column threadIdx.x of a [value][thread] shared-memory array: the
+// quadrature loop then holds only the stress moments and one symmetric gradient in registers,
+// which lets two CTAs (16 warps) share an SM to keep the FP64 pipes fed; reading H costs 24
+// shared loads per point against about 50 FP64 operations.
 constexpr int kEpsThreads = 256;
 template <typename T, bool FIELD>
-constexpr size_t eps_apply_smem() { return (sizeof(T) * (36 + (FIELD ? kMaxQ : 0)) + sizeof(int) * 10) * kEpsThreads; }
+constexpr size_t eps_apply_smem() { return (sizeof(T) * (24 + (FIELD ? kMaxQ : 0)) + sizeof(int) * 10) * kEpsThreads; }
 
-template <typename T, int MODE, bool FIELD, bool DIR>
-__global__ void __launch_bounds__(kEpsThreads, MODE == 0 ? 2 : 1) eps_color_kernel(const OpConst<T>* __restrict__ cst,
-                                                         const int4* __restrict__ tasks, int color, int cpb,
-                                                         int nrhs, T mu_const, const T* __restrict__ x,
-                                                         const T* __restrict__ g, const T* __restrict__ mu,
-                                                         T* __restrict__ out) {
+template <typename T, bool FIELD, bool DIR>
+__global__ void __launch_bounds__(kEpsThreads, 2) eps_color_kernel(const OpConst<T>* __restrict__ cst,
+                                                                    const int4* __restrict__ tasks, int color, int cpb,
+                                                                    int nrhs, T mu_const, const T* __restrict__ x,
+                                                                    const T* __restrict__ mu, T* __restrict__ out) {
   const int4 task = tasks[blockIdx.x];
   const int macro = task.w;
   const OpConst<T>& c = cst[macro];
@@ -139,32 +172,30 @@ __global__ void __launch_bounds__(kEpsThreads, MODE == 0 ? 2 : 1) eps_color_kern
   const int cj = 2 * task.y + ((color >> 1) & 1);
   const int ck = 2 * task.z + ((color >> 2) & 1);
   const bool live = t / nrhs < cpb && ci + cj + ck <= n - 1;
-  if (MODE == 0 && !live) return;
-  if (MODE == 2 && __all_sync(0xffffffffu, !live)) return;
+  if (!live) return;
   const int64_t base = c.base;
   const int stride = 3 * nrhs;
   extern __shared__ __align__(16) unsigned char eps_smem_raw[];
-  T* __restrict__ Ps = reinterpret_cast<T*>(eps_smem_raw) + threadIdx.x;   // MODE 0: P[v] at Ps[v * kEpsThreads]
-  T* __restrict__ Ms = Ps + 36 * kEpsThreads;   // MODE 0, field: mu(x_q) w_q |det J| at the points
-  int* __restrict__ Is = reinterpret_cast<int*>(reinterpret_cast<T*>(eps_smem_raw) + (FIELD ? 36 + kMaxQ : 36) * kEpsThreads) +
-                         threadIdx.x;           // MODE 0: node indices
+  T* __restrict__ Ps = reinterpret_cast<T*>(eps_smem_raw) + threadIdx.x;   // H[v] at Ps[v * kEpsThreads]
+  T* __restrict__ Ms = Ps + 24 * kEpsThreads;   // field: mu(x_q) w_q |det J| at the points
+  int* __restrict__ Is = reinterpret_cast<int*>(reinterpret_cast<T*>(eps_smem_raw) + (FIELD ? 24 + kMaxQ : 24) * kEpsThreads) +
+                         threadIdx.x;           // node indices
 #pragma unroll 1
   for (int o = 0; o < 6; ++o) {
-    const bool tet_ok = live && ci + cj + ck <= n - 1 - (o == 0 ? 0 : (o == 5 ? 2 : 1));
-    if (MODE == 0 && !tet_ok) continue;
-    int idx[10], masked = 0;   // bit a: node a reads as zero (Dirichlet point or no micro-tet)
+    if (ci + cj + ck > n - 1 - (o == 0 ? 0 : (o == 5 ? 2 : 1))) continue;
+    int idx[10], masked = 0;   // bit a: node a reads as zero (Dirichlet point)
     T m[10];
 #pragma unroll
     for (int a = 0; a < 10; ++a) {
       const int pi = 2 * ci + enode_d(o, a, 0), pj = 2 * cj + enode_d(o, a, 1), pk = 2 * ck + enode_d(o, a, 2);
-      idx[a] = tet_ok ? (int)packed_index(N, pi, pj, pk) : 0;
-      if (MODE == 0) Is[a * kEpsThreads] = idx[a];
-      if (!tet_ok || (DIR && on_dirichlet(c.bnd_table, N, pi, pj, pk))) masked |= 1 << a;
-      if (MODE == 0 && FIELD) m[a] = __ldg(mu + base + idx[a]);
+      idx[a] = (int)packed_index(N, pi, pj, pk);
+      Is[a * kEpsThreads] = idx[a];
+      if (DIR && on_dirichlet(c.bnd_table, N, pi, pj, pk)) masked |= 1 << a;
+      if (FIELD) m[a] = __ldg(mu + base + idx[a]);
     }
     const T* Ji = c.Jinv[o];
     const T wdet = c.adet[o];
-    if (MODE == 0 && FIELD) {
+    if (FIELD) {
       // mu at the quadrature points, times the weight and |det J|, once per micro-tet
 #pragma unroll 1
       for (int q = 0; q < c.nq; ++q) {
@@ -174,125 +205,125 @@ __global__ void __launch_bounds__(kEpsThreads, MODE == 0 ? 2 : 1) eps_color_kern
         Ms[q * kEpsThreads] = muq * c.w[q] * wdet;
       }
     }
-    T dmu[10];
+    // affine symmetric gradient of u into shared memory
+    eps_sym_affine<T, kEpsThreads>(c, o, idx, masked, x + r, base, stride, nrhs, Ps);
+    // physical moments of the stress: Q[t][v] = sum_q lambda_t S_v (lambda_0 = 1), S = s (G + G^T)
+    // = 2 mu eps(u) w |det J| symmetric, so only its six entries v = (0,0) (1,1) (2,2) (0,1) (0,2)
+    // (1,2) are accumulated (the entry of (c, d) is eps_sym(c, d))
+    T Q[4][6];
 #pragma unroll
-    for (int a = 0; a < 10; ++a) dmu[a] = T(0);
-    // physical gradients of the components, affine in lambda: G_c = P[c][0] + sum_b lambda_b P[c][b]
-    // (MODE 0: one component at a time into shared memory, P[c][t][d] at Ps[(12 c + 3 t + d) kEpsThreads])
-    T P[3][4][3], gv[3][10];
+    for (int tt = 0; tt < 4; ++tt)
 #pragma unroll
-    for (int cc = 0; cc < 3; ++cc) {
-      T u[10], W[4][3];
+      for (int v = 0; v < 6; ++v) Q[tt][v] = T(0);
+#pragma unroll 1
+    for (int q = 0; q < c.nq; ++q) {
+      const T l1 = c.lam[q][1], l2 = c.lam[q][2], l3 = c.lam[q][3];
+      T E[6];
+      eps_sym_at<kEpsThreads>(Ps, l1, l2, l3, E);
+      const T s = FIELD ? Ms[q * kEpsThreads] : mu_const * c.w[q] * wdet;
+      T Sv[6];
 #pragma unroll
-      for (int a = 0; a < 10; ++a) {
-        const int64_t e = (base + idx[a]) * stride + cc * nrhs + r;
-        u[a] = (masked >> a) & 1 ? T(0) : __ldg(x + e);
-        if (MODE == 2) gv[cc][a] = (masked >> a) & 1 ? T(0) : __ldg(g + e);
-      }
-      eps_grad_affine<T>(u, W);
+      for (int v = 0; v < 6; ++v) Sv[v] = s * E[v];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        phys_grad<T>(Ji, W[t], P[cc][t]);
-        if (MODE == 0)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) Ps[(12 * cc + 3 * t + d) * kEpsThreads] = P[cc][t][d];
+      for (int v = 0; v < 6; ++v) {
+        Q[0][v] += Sv[v];
+        Q[1][v] = fma(l1, Sv[v], Q[1][v]);
+        Q[2][v] = fma(l2, Sv[v], Q[2][v]);
+        Q[3][v] = fma(l3, Sv[v], Q[3][v]);
       }
     }
-    if (MODE == 0) {
-      // physical moments of the stress: Q[t][v] = sum_q lambda_t S_v (lambda_0 = 1), S = s (G + G^T)
-      // = 2 mu eps(u) w |det J| symmetric, so only its six entries v = (0,0) (1,1) (2,2) (0,1) (0,2)
-      // (1,2) are accumulated (the entry of (c, d) is eps_sym(c, d))
-      T Q[4][6];
+    // y_c += sum_q (J^{-1} S_c) . grad_ref phi: map the moments back once, then test; the moments
+    // go to shared memory (over H, no longer needed) so that one component at a time is in
+    // registers, and each component is added to out as soon as it is formed
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
+    for (int tt = 0; tt < 4; ++tt)
 #pragma unroll
-        for (int v = 0; v < 6; ++v) Q[t][v] = T(0);
+      for (int v = 0; v < 6; ++v) Ps[(6 * tt + v) * kEpsThreads] = Q[tt][v];
+#pragma unroll 1
+    for (int cc = 0; cc < 3; ++cc) {
+      T R3[3], S3[3][3], yc[10], Qc[4][3];
+#pragma unroll
+      for (int tt = 0; tt < 4; ++tt)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Qc[tt][d] = Ps[(6 * tt + eps_sym(cc, d)) * kEpsThreads];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        R3[e] = Ji[e * 3 + 0] * Qc[0][0] + Ji[e * 3 + 1] * Qc[0][1] + Ji[e * 3 + 2] * Qc[0][2];
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          S3[e][b] = Ji[e * 3 + 0] * Qc[b + 1][0] + Ji[e * 3 + 1] * Qc[b + 1][1] + Ji[e * 3 + 2] * Qc[b + 1][2];
+      }
+#pragma unroll
+      for (int a = 0; a < 10; ++a) yc[a] = T(0);
+      eps_test_moments<T>(S3, R3, yc);
+#pragma unroll
+      for (int a = 0; a < 10; ++a) out[(base + Is[a * kEpsThreads]) * stride + cc * nrhs + r] += yc[a];
+    }
+  }
+}
+
+// mu-adjoint, out_m += sum_r g_r^T (dA/dmu_m) u_r with mu a P2 field: per quadrature point
+// t_q = w_q |det J| grad g : (grad u + grad u^T) = w_q |det J| E(g) : E(u) / 2 summed over the
+// right-hand sides of a cube (consecutive lanes of one warp, nrhs divides 32) and tested against
+// the ten basis values.  The tasks are the apply's (up to cpb cubes of a row); a CTA of
+// kEpsAdjThreads threads takes them in two halves.  Each thread keeps the affine symmetric-gradient
+// terms of u and of g (24 + 24 values) in its own column of shared memory, so that three CTAs
+// (12 warps) share an SM.
+constexpr int kEpsAdjThreads = kEpsThreads / 2;
+template <typename T>
+constexpr size_t eps_adjoint_smem() { return sizeof(T) * 48 * kEpsAdjThreads; }
+
+template <typename T, bool DIR>
+__global__ void __launch_bounds__(kEpsAdjThreads, 3) eps_adjoint_kernel(const OpConst<T>* __restrict__ cst,
+                                                                         const int4* __restrict__ tasks, int color,
+                                                                         int cpb, int nrhs, const T* __restrict__ x,
+                                                                         const T* __restrict__ g, T* __restrict__ out) {
+  const int4 task = tasks[blockIdx.x];
+  const OpConst<T>& c = cst[task.w];
+  const int n = c.n, N = c.N;
+  const int r = threadIdx.x % nrhs;
+  const int cj = 2 * task.y + ((color >> 1) & 1);
+  const int ck = 2 * task.z + ((color >> 2) & 1);
+  const int64_t base = c.base;
+  const int stride = 3 * nrhs;
+  extern __shared__ __align__(16) unsigned char eps_smem_raw[];
+  T* __restrict__ Hu = reinterpret_cast<T*>(eps_smem_raw) + threadIdx.x;   // H of u at Hu[v * kEpsAdjThreads]
+  T* __restrict__ Hg = Hu + 24 * kEpsAdjThreads;                            // H of g
+  for (int half = 0; half < 2; ++half) {
+    const int slot = (threadIdx.x + half * kEpsAdjThreads) / nrhs;
+    const int ci = 2 * (task.x + slot) + (color & 1);
+    const bool live = slot < cpb && ci + cj + ck <= n - 1;
+    if (__all_sync(0xffffffffu, !live)) continue;   // whole warp (the shuffles below need all lanes)
+#pragma unroll 1
+    for (int o = 0; o < 6; ++o) {
+      const bool tet_ok = live && ci + cj + ck <= n - 1 - (o == 0 ? 0 : (o == 5 ? 2 : 1));
+      int idx[10], masked = 0;   // bit a: node a reads as zero (Dirichlet point or no micro-tet)
+#pragma unroll
+      for (int a = 0; a < 10; ++a) {
+        const int pi = 2 * ci + enode_d(o, a, 0), pj = 2 * cj + enode_d(o, a, 1), pk = 2 * ck + enode_d(o, a, 2);
+        idx[a] = tet_ok ? (int)packed_index(N, pi, pj, pk) : 0;
+        if (!tet_ok || (DIR && on_dirichlet(c.bnd_table, N, pi, pj, pk))) masked |= 1 << a;
+      }
+      const T wdet = c.adet[o];
+      eps_sym_affine<T, kEpsAdjThreads>(c, o, idx, masked, x + r, base, stride, nrhs, Hu);
+      eps_sym_affine<T, kEpsAdjThreads>(c, o, idx, masked, g + r, base, stride, nrhs, Hg);
+      T dmu[10];
+#pragma unroll
+      for (int a = 0; a < 10; ++a) dmu[a] = T(0);
 #pragma unroll 1
       for (int q = 0; q < c.nq; ++q) {
         const T l1 = c.lam[q][1], l2 = c.lam[q][2], l3 = c.lam[q][3];
-        T G[3][3];
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const T* pc = Ps + (12 * cc + d) * kEpsThreads;
-            G[cc][d] = fma(l3, pc[9 * kEpsThreads], fma(l2, pc[6 * kEpsThreads], fma(l1, pc[3 * kEpsThreads], pc[0])));
-          }
-        const T s = FIELD ? Ms[q * kEpsThreads] : mu_const * c.w[q] * wdet;
-        const T s2 = s + s;
-        T Sv[6];
-        Sv[0] = s2 * G[0][0];
-        Sv[1] = s2 * G[1][1];
-        Sv[2] = s2 * G[2][2];
-        Sv[3] = s * (G[0][1] + G[1][0]);
-        Sv[4] = s * (G[0][2] + G[2][0]);
-        Sv[5] = s * (G[1][2] + G[2][1]);
-#pragma unroll
-        for (int v = 0; v < 6; ++v) {
-          Q[0][v] += Sv[v];
-          Q[1][v] = fma(l1, Sv[v], Q[1][v]);
-          Q[2][v] = fma(l2, Sv[v], Q[2][v]);
-          Q[3][v] = fma(l3, Sv[v], Q[3][v]);
-        }
-      }
-      // y_c += sum_q (J^{-1} S_c) . grad_ref phi: map the moments back once, then test; the moments
-      // go to shared memory (over P, no longer needed) so that one component at a time is in
-      // registers, and each component is added to out as soon as it is formed
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int v = 0; v < 6; ++v) Ps[(6 * t + v) * kEpsThreads] = Q[t][v];
-#pragma unroll 1
-      for (int cc = 0; cc < 3; ++cc) {
-        T R3[3], S3[3][3], yc[10], Qc[4][3];
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) Qc[t][d] = Ps[(6 * t + eps_sym(cc, d)) * kEpsThreads];
-#pragma unroll
-        for (int e = 0; e < 3; ++e) {
-          R3[e] = Ji[e * 3 + 0] * Qc[0][0] + Ji[e * 3 + 1] * Qc[0][1] + Ji[e * 3 + 2] * Qc[0][2];
-#pragma unroll
-          for (int b = 0; b < 3; ++b)
-            S3[e][b] = Ji[e * 3 + 0] * Qc[b + 1][0] + Ji[e * 3 + 1] * Qc[b + 1][1] + Ji[e * 3 + 2] * Qc[b + 1][2];
-        }
-#pragma unroll
-        for (int a = 0; a < 10; ++a) yc[a] = T(0);
-        eps_test_moments<T>(S3, R3, yc);
-#pragma unroll
-        for (int a = 0; a < 10; ++a) out[(base + Is[a * kEpsThreads]) * stride + cc * nrhs + r] += yc[a];
-      }
-    } else {
-      T Pg[3][4][3];
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) {
-        T W[4][3];
-        eps_grad_affine<T>(gv[cc], W);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) phys_grad<T>(Ji, W[t], Pg[cc][t]);
-      }
-      for (int q = 0; q < c.nq; ++q) {
-        const T l1 = c.lam[q][1], l2 = c.lam[q][2], l3 = c.lam[q][3];
-        T G[3][3], Gg[3][3];
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            G[cc][d] = fma(l3, P[cc][3][d], fma(l2, P[cc][2][d], fma(l1, P[cc][1][d], P[cc][0][d])));
-            Gg[cc][d] = fma(l3, Pg[cc][3][d], fma(l2, Pg[cc][2][d], fma(l1, Pg[cc][1][d], Pg[cc][0][d])));
-          }
-        T tq = T(0);
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) tq += Gg[cc][d] * (G[cc][d] + G[d][cc]);
+        T Eu[6], Eg[6];
+        eps_sym_at<kEpsAdjThreads>(Hu, l1, l2, l3, Eu);
+        eps_sym_at<kEpsAdjThreads>(Hg, l1, l2, l3, Eg);
+        // E(g) : E(u) / 2 = the diagonal products halved plus the off-diagonal products
+        T tq = T(0.5) * (Eg[0] * Eu[0] + Eg[1] * Eu[1] + Eg[2] * Eu[2]);
+        tq = fma(Eg[3], Eu[3], fma(Eg[4], Eu[4], fma(Eg[5], Eu[5], tq)));
         tq *= c.w[q] * wdet;
 #pragma unroll
         for (int a = 0; a < 10; ++a) dmu[a] += c.psi[q][a] * tq;
       }
-    }
-    if (MODE == 2) {
-      // sum over the right-hand sides of this cube (consecutive lanes of one warp), one writer
+      // sum over the right-hand sides of this cube, one writer (cubes of one colour share no point)
 #pragma unroll
       for (int a = 0; a < 10; ++a)
         for (int off = 1; off < nrhs; off <<= 1) dmu[a] += __shfl_xor_sync(0xffffffffu, dmu[a], off);
@@ -362,25 +393,34 @@ int launch_eps(const hhg_op* op, const OpConst<T>* cst, int mode, int nrhs, cons
     const unsigned grid = (unsigned)(op->eps_off[color + 1] - op->eps_off[color]);
     if (grid == 0) continue;
     const int4* tk = op->d_eps_tasks + op->eps_off[color];
-#define HHG_EPS(M, F, D)                                                                                       \
+#define HHG_EPS(F, D)                                                                                          \
   do {                                                                                                       \
-    const size_t sm = M == 0 ? eps_apply_smem<T, F>() : 0;                                                   \
+    const size_t sm = eps_apply_smem<T, F>();                                                                \
     if (sm > 48 * 1024)                                                                                      \
-      HHG_CUDA_TRY(cudaFuncSetAttribute(eps_color_kernel<T, M, F, D>,                                      \
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));              \
-    eps_color_kernel<T, M, F, D><<<grid, kEpsThreads, sm, s>>>(cst, tk, color, cpb, nrhs, muc, x, g, mu, out); \
+      HHG_CUDA_TRY(cudaFuncSetAttribute(eps_color_kernel<T, F, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        (int)sm));                                                           \
+    eps_color_kernel<T, F, D><<<grid, kEpsThreads, sm, s>>>(cst, tk, color, cpb, nrhs, muc, x, mu, out);     \
+  } while (0)
+#define HHG_EPS_ADJ(D)                                                                                         \
+  do {                                                                                                       \
+    const size_t sm = eps_adjoint_smem<T>();                                                                 \
+    if (sm > 48 * 1024)                                                                                      \
+      HHG_CUDA_TRY(cudaFuncSetAttribute(eps_adjoint_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                        (int)sm));                                                           \
+    eps_adjoint_kernel<T, D><<<grid, kEpsAdjThreads, sm, s>>>(cst, tk, color, cpb, nrhs, x, g, out);         \
   } while (0)
     const bool dir = op->bc == HHG_DIRICHLET;
     if (mode == 0) {
       if (field) {
-        if (dir) HHG_EPS(0, true, true); else HHG_EPS(0, true, false);
+        if (dir) HHG_EPS(true, true); else HHG_EPS(true, false);
       } else {
-        if (dir) HHG_EPS(0, false, true); else HHG_EPS(0, false, false);
+        if (dir) HHG_EPS(false, true); else HHG_EPS(false, false);
       }
     } else {
-      if (dir) HHG_EPS(2, true, true); else HHG_EPS(2, true, false);
+      if (dir) HHG_EPS_ADJ(true); else HHG_EPS_ADJ(false);
     }
 #undef HHG_EPS
+#undef HHG_EPS_ADJ
     HHG_CUDA_TRY(cudaGetLastError());
   }
   if (mode == 0 && op->bc == HHG_DIRICHLET) {
