@@ -166,3 +166,52 @@ def test_layout_roundtrip():
     assert len(xp) == 6 * M.lattice_size(4)
     assert L.copies_spread(S, xp) == 0.0
     assert np.array_equal(L.from_packed(S, xp), x)
+
+
+def test_epsilon_solution_is_third_order():
+    """The P2 vector epsilon operator (Section 7.4 names it) with a manufactured displacement on the
+    unit cube: u = phi (1, 1, 1), phi = sin pi x sin pi y sin pi z (zero on the boundary),
+    mu = 1 + x/2, f = -div(2 mu eps(u)) = -mu (Lap u + grad div u) - 2 eps(u) grad mu in closed
+    form.  The Galerkin solution (exact sparse solve) must approach u as O(h^3) in L2."""
+    import scipy.sparse.linalg as spla
+    from oracle import mg
+
+    p = np.pi
+
+    def parts(x):
+        s, c = np.sin(p * x), np.cos(p * x)
+        phi = s[:, 0] * s[:, 1] * s[:, 2]
+        d1 = p * np.stack([c[:, 0] * s[:, 1] * s[:, 2], s[:, 0] * c[:, 1] * s[:, 2], s[:, 0] * s[:, 1] * c[:, 2]], 1)
+        d2 = np.empty((len(x), 3, 3))                                 # second derivatives of phi
+        for i in range(3):
+            for j in range(3):
+                if i == j:
+                    d2[:, i, j] = -p * p * phi
+                else:
+                    k = 3 - i - j
+                    d2[:, i, j] = p * p * c[:, i] * c[:, j] * s[:, k]
+        return phi, d1, d2
+
+    def f_comp(comp):
+        def f(x):
+            phi, d1, d2 = parts(x)
+            mu = 1.0 + 0.5 * x[:, 0]
+            lap = -3.0 * p * p * phi                                    # Lap u_c, every component
+            graddiv = d2[:, comp, :].sum(axis=1)                        # d_c (phi_x + phi_y + phi_z)
+            eps_c0 = 0.5 * (d1[:, comp] + d1[:, 0])                     # eps(u)_{c,x}
+            return -mu * (lap + graddiv) - 2.0 * eps_c0 * 0.5           # grad mu = (1/2, 0, 0)
+        return f
+
+    mm = M.MacroMesh(*W.cube6())
+    errs = []
+    for level in (1, 2, 3):
+        S = A.Space(mm, level, 2)
+        K = A.epsilon_matrix(S, ("func", lambda x: 1.0 + 0.5 * x[:, 0]), 4, "dirichlet")
+        b = np.zeros(3 * S.ndof)
+        for comp in range(3):
+            b[comp::3] = mg.load_vector(S, f_comp(comp))
+        u = spla.spsolve(K.tocsc(), b)
+        e2 = sum(mg.l2_error(S, u[comp::3], lambda x: parts(x)[0]) ** 2 for comp in range(3))
+        errs.append(np.sqrt(e2))
+    ratios = np.array(errs[1:]) / np.array(errs[:-1])
+    assert 0.09 < ratios[-1] < 0.16 and ratios[0] < 0.2, (errs, ratios)
