@@ -98,3 +98,17 @@ def test_n1_fmg_reaches_the_discretisation_error():
     assert hist[-1] <= 1e-10 and cycles <= 30, (cycles, hist[-1])
     xd = spla.spsolve(H.A[L].tocsc(), bs[L])
     assert np.abs(x - xd).max() <= 1e-8 * np.abs(xd).max()
+
+
+def test_gradient_space_operator_is_p1_diffusion_with_beta():
+    """G^T A G over the vertices is the P1 diffusion operator with coefficient beta: curl grad = 0
+    leaves the beta-mass of the Whitney gradients, which are the gradients of the P1 hat functions.
+    (So the nodal part of the hybrid smoother is a P1 variable-coefficient apply.)"""
+    mm = _mesh("cube6")
+    S = A.EdgeSpace(mm, 2)
+    a = 1.0 + 0.5 * np.sin(3.0 * S.V1.coords[:, 0])
+    b = np.exp(W.fourier_field(S.V1.coords, seed=3))
+    K = A.n1_matrix(S, ("field", S.V1, a), ("field", S.V1, b), 4, "neumann")
+    G = A.n1_gradient(S)
+    D = A.diffusion_matrix(S.V1, ("field", S.V1, b), 2, "neumann")
+    assert abs(G.T @ K @ G - D).max() <= 1e-13 * abs(D).max()
