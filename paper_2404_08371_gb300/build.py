@@ -70,7 +70,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return obj
 
     if jobs:
-        with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+        with concurrent.futures.ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(jobs))) as ex:
             list(ex.map(compile_one, jobs))
     if jobs or not os.path.exists(LIB) or force:
         cmd = [_nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-cudart", "static"]
