@@ -164,16 +164,19 @@ def diffusion_coeff_adjoint(space: Space, kspace: Space, u, g, quad_degree: int 
 
 
 def epsilon_coeff_adjoint(space: Space, u, g, quad_degree: int = 4, bc: str = "dirichlet"):
-    """dmu_m = g^T (dA/dmu_m) u for a P2 viscosity field; u, g of length 3*ndof."""
+    """dmu_m = g^T (dA/dmu_m) u for a P2 viscosity field; u, g of length 3*ndof, or (3*ndof, nrhs)
+    for a batch, in which case the result is summed over the right-hand sides."""
     u = np.asarray(u, dtype=np.float64).copy()
     g = np.asarray(g, dtype=np.float64).copy()
+    if u.ndim == 1:
+        u, g = u[:, None], g[:, None]
     if bc == "dirichlet":
         vb = vector_boundary(space)
         u[vb] = 0.0
         g[vb] = 0.0
     K = fe.epsilon_coeff_derivative(space.elem_X, quad_degree)
     vd = (3 * space.elem_dofs[:, :, None] + np.arange(3)[None, None, :]).reshape(len(space.elem_dofs), 30)
-    contrib = np.einsum("ei,emij,ej->em", g[vd], K, u[vd])
+    contrib = np.einsum("eir,emij,ejr->em", g[vd], K, u[vd], optimize=True)
     dk = np.zeros(space.ndof)
     np.add.at(dk, space.elem_dofs, contrib)
     return dk
@@ -243,6 +246,151 @@ def sampled_diffusion_rows(macro_xyz, level: int, degree: int, coeff, quad_degre
             xl = np.where(on_boundary(nodes), 0.0, xl)
         out[s] = sum(loc[e, rows[e], :] @ xl[e] for e in range(len(tv)))
     return out
+
+
+def point_copies(mesh: MacroMesh, m: int, p, N: int):
+    """Every (macro, local lattice point) that stores the point p (resolution N) of macro m.
+
+    Exact: the point's global key (nonzero barycentric weights on global vertex ids) is matched
+    against each macro's vertex list; a macro holds the point when it has all the key's vertices.
+    """
+    key = point_keys(mesh.tets[m], np.asarray(p, dtype=np.int64)[None], N)[0]
+    vids, wts = key[0::2], key[1::2]
+    out = []
+    for m2 in range(mesh.nmacro):
+        t2 = [int(v) for v in mesh.tets[m2]]
+        if not all(int(v) in t2 for v, w in zip(vids, wts) if w > 0):
+            continue
+        w4 = np.zeros(4, dtype=np.int64)
+        for v, w in zip(vids, wts):
+            if w > 0:
+                w4[t2.index(int(v))] = w
+        out.append((m2, w4[1:].copy()))
+    return out
+
+
+def _on_dirichlet(mesh: MacroMesh, m: int, pts, N: int):
+    """Lattice points (k, 3) or one point (3,) of macro m that lie on the domain boundary.
+
+    A point lies in the relative interior of the face spanned by the macro vertices with a
+    nonzero barycentric weight (its support); it is on a boundary face F exactly when its support
+    is a subset of F's three vertices.  This also catches points on a macro edge or vertex that
+    touches the boundary while none of that macro's own faces is boundary.
+    """
+    pts = np.asarray(pts, dtype=np.int64)
+    one = pts.ndim == 1
+    pts = pts.reshape(-1, 3)
+    w = np.stack([N - pts.sum(axis=-1), pts[:, 0], pts[:, 1], pts[:, 2]], axis=-1)
+    tet = [int(v) for v in mesh.tets[m]]
+    hit = np.zeros(len(pts), dtype=bool)
+    for face, owners in mesh.faces.items():
+        if len(owners) != 1:
+            continue
+        outside = np.array([v not in face for v in tet])
+        hit |= ~np.any((w > 0) & outside[None, :], axis=1)
+    return bool(hit[0]) if one else hit
+
+
+def incident_tets(q, n: int, degree: int):
+    """Micro-tets of one macro (n intervals per edge) that have the lattice point q (resolution
+    degree*n) as a local node: their index-space vertices (E, 4, 3) and q's local node number."""
+    q = np.asarray(q, dtype=np.int64)
+    lo = (q + degree - 1) // degree - 1
+    hi = q // degree
+    tets, rows = [], []
+    for cz in range(max(lo[2], 0), hi[2] + 1):
+        for cy in range(max(lo[1], 0), hi[1] + 1):
+            for cx in range(max(lo[0], 0), hi[0] + 1):
+                c = np.array([cx, cy, cz])
+                for o in range(6):
+                    if c.sum() > n - 1 - CLASS_SHRINK[o]:
+                        continue
+                    tv = c[None, :] + CLASS_OFFSETS[o]
+                    hit = np.nonzero(np.all(local_nodes(tv[None], degree)[0] == q[None, :], axis=1))[0]
+                    if len(hit):
+                        tets.append(tv)
+                        rows.append(int(hit[0]))
+    return np.array(tets), np.array(rows)
+
+
+def _epsilon_rows_of_copy(mesh, m, q, level, mu_packed, quad_degree):
+    """Micro-tets of macro m around its local P2 point q: local nodes, packed positions of the
+    nodes, q's row number and the local epsilon matrices with mu interpolated from mu_packed."""
+    n, N = 2 ** level, 2 ** (level + 1)
+    P = (N + 1) * (N + 2) * (N + 3) // 6
+    tv, rows = incident_tets(q, n, 2)
+    X = physical(mesh.vertices[mesh.tets[m]], tv, n)
+    nodes = local_nodes(tv, 2)
+    pos = packed_position(nodes.reshape(-1, 3), N).reshape(nodes.shape[:2])
+    xi, _ = quadrature.rule(quad_degree)
+    muq = fe.field_at_points(2, xi, np.asarray(mu_packed)[m * P + pos])
+    return X, nodes, rows, muq
+
+
+def sampled_epsilon_rows(mesh: MacroMesh, level: int, mu_packed: np.ndarray, x_at, samples, quad_degree: int = 4,
+                         bc: str = "dirichlet") -> np.ndarray:
+    """(A x) of the P2 vector epsilon operator at sampled points of a multi-macro mesh.
+
+    Point by point: the sum, over every macro that stores the point and every micro-tet of that
+    macro around it, of the point's three rows of the local matrix (fe.epsilon_local, mu
+    interpolated from that macro's copy of the P2 field mu_packed) times the local x.  Points on
+    the Dirichlet boundary return x; with DIRICHLET, boundary nodes enter with x = 0.
+    x_at(m, pts) gives x at lattice points (k, 3) of macro m as (k, 3, nrhs); samples is a list
+    of (macro, lattice point).  Returns (len(samples), 3, nrhs).
+    """
+    N = 2 ** (level + 1)
+    out = []
+    for m, p in samples:
+        copies = point_copies(mesh, m, p, N)
+        if bc == "dirichlet" and any(_on_dirichlet(mesh, m2, q, N) for m2, q in copies):
+            out.append(np.asarray(x_at(m, np.asarray(p)[None]))[0])
+            continue
+        acc = 0.0
+        for m2, q in copies:
+            X, nodes, rows, muq = _epsilon_rows_of_copy(mesh, m2, q, level, mu_packed, quad_degree)
+            loc = fe.epsilon_local(X, quad_degree, muq)                       # (E, 30, 30)
+            xl = np.asarray(x_at(m2, nodes.reshape(-1, 3)), dtype=np.float64)  # (E*10, 3, nrhs)
+            nrhs = xl.shape[-1]
+            if bc == "dirichlet":
+                xl = np.where(_on_dirichlet(mesh, m2, nodes.reshape(-1, 3), N)[:, None, None], 0.0, xl)
+            xl = xl.reshape(len(X), 30, nrhs)
+            for e in range(len(X)):
+                acc = acc + loc[e, 3 * rows[e]:3 * rows[e] + 3, :] @ xl[e]
+        out.append(acc)
+    return np.array(out)
+
+
+def sampled_epsilon_adjoint(mesh: MacroMesh, level: int, u_at, g_at, samples, quad_degree: int = 4,
+                            bc: str = "dirichlet") -> np.ndarray:
+    """dmu_m = sum_r g_r^T (dA/dmu_m) u_r at sampled P2 points m of a multi-macro mesh.
+
+    The same sum over macros and micro-tets as sampled_epsilon_rows, with the derivative of the
+    local matrix in the nodal value of mu at the point (fe.epsilon_coeff_derivative); with
+    DIRICHLET, u and g enter with their boundary entries set to zero.  Returns (len(samples),).
+    """
+    N = 2 ** (level + 1)
+    n = 2 ** level
+    out = []
+    for m, p in samples:
+        acc = 0.0
+        for m2, q in point_copies(mesh, m, p, N):
+            tv, rows = incident_tets(q, n, 2)
+            X = physical(mesh.vertices[mesh.tets[m2]], tv, n)
+            nodes = local_nodes(tv, 2).reshape(-1, 3)
+            K = fe.epsilon_coeff_derivative(X, quad_degree)                   # (E, 10, 30, 30)
+            ul = np.asarray(u_at(m2, nodes), dtype=np.float64)
+            gl = np.asarray(g_at(m2, nodes), dtype=np.float64)
+            if bc == "dirichlet":
+                zb = _on_dirichlet(mesh, m2, nodes, N)[:, None, None]
+                ul = np.where(zb, 0.0, ul)
+                gl = np.where(zb, 0.0, gl)
+            nrhs = ul.shape[-1]
+            ul = ul.reshape(len(X), 30, nrhs)
+            gl = gl.reshape(len(X), 30, nrhs)
+            for e in range(len(X)):
+                acc += float(np.einsum("ir,ij,jr->", gl[e], K[e, rows[e]], ul[e]))
+        out.append(acc)
+    return np.array(out)
 
 
 # ---------------------------------------------------------------------------

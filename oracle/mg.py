@@ -15,7 +15,8 @@ Readings where the paper is silent:
     the given order (order applications of A);
   * FMG solves level 0 exactly, then per level prolongs the previous
     solution and runs one V(nu1, nu2); further V-cycles run until
-    ||b - A x||_2 / ||b||_2 <= tol.
+    ||b - A x||_2 / ||b||_2 <= tol; the coarse levels' right-hand sides are
+    restrictions of the fine one.
 Pinned by: P reproduces the fine interpolant of coarse-exact polynomials,
 R = P^T, the V-cycle contraction factor stays below a fixed bound as the level
 grows, and the discretisation error falls at the textbook rate
@@ -192,11 +193,19 @@ class Hierarchy:
             x = chebyshev(A, dinv, b, x, self.lam[l], self.order)
         return x
 
-    def fmg(self, bs, nu1: int = 2, nu2: int = 2, tol: float = 1e-10, max_cycles: int = 50):
-        """FMG then V-cycles on the finest level; bs[l] the right-hand side of level l.
+    def fmg(self, b, nu1: int = 2, nu2: int = 2, tol: float = 1e-10, max_cycles: int = 50):
+        """FMG then V-cycles on the finest level for the fine right-hand side b.
 
+        The right-hand sides of the coarser levels are restrictions of b: b_{l-1} = P_l^T b_l with
+        the boundary rows zero (the same transfer the V-cycle applies to residuals).
         Returns (x, number of V-cycles on the finest level after FMG, history of relative residuals).
         """
+        bs = [None] * (self.L + 1)
+        bs[self.L] = np.asarray(b, dtype=np.float64).copy()
+        bs[self.L][self.spaces[self.L].boundary] = 0.0
+        for l in range(self.L, 0, -1):
+            bs[l - 1] = self.P[l].T @ bs[l]
+            bs[l - 1][self.spaces[l - 1].boundary] = 0.0
         x = scipy.linalg.cho_solve(self.coarse_cho, bs[0])
         for l in range(1, self.L + 1):
             x = self.P[l] @ x

@@ -131,8 +131,15 @@ class N1Hierarchy:
             x = self.smooth(l, b, x)
         return x
 
-    def fmg(self, bs, nu1: int = 2, nu2: int = 2, tol: float = 1e-10, max_cycles: int = 50):
-        """FMG then V-cycles on the finest level; returns (x, V-cycles after FMG, residual history)."""
+    def fmg(self, b, nu1: int = 2, nu2: int = 2, tol: float = 1e-10, max_cycles: int = 50):
+        """FMG then V-cycles on the finest level for the fine right-hand side b (coarse right-hand
+        sides by restriction, boundary rows zero); returns (x, V-cycles after FMG, residual history)."""
+        bs = [None] * (self.L + 1)
+        bs[self.L] = np.asarray(b, dtype=np.float64).copy()
+        bs[self.L][self.spaces[self.L].boundary] = 0.0
+        for l in range(self.L, 0, -1):
+            bs[l - 1] = self.P[l].T @ bs[l]
+            bs[l - 1][self.spaces[l - 1].boundary] = 0.0
         x = scipy.linalg.lu_solve(self.coarse_lu, bs[0])
         for l in range(1, self.L + 1):
             x = self.P[l] @ x

@@ -98,7 +98,7 @@ def test_fmg_converges_and_discretisation_order():
     for degree, L in [(1, 4), (2, 3)]:
         H = mg.Hierarchy(mm, L, degree, quad_degree=2 if degree == 1 else 4)
         bs = [mg.load_vector(s, W.manufactured_f) for s in H.spaces]
-        x, cycles, hist = H.fmg(bs, tol=1e-10)
+        x, cycles, hist = H.fmg(bs[L], tol=1e-10)
         assert hist[-1] <= 1e-10 and cycles <= 15
         # error on each level of the hierarchy, solved directly
         e = []

@@ -215,3 +215,53 @@ def test_epsilon_solution_is_third_order():
         errs.append(np.sqrt(e2))
     ratios = np.array(errs[1:]) / np.array(errs[:-1])
     assert 0.09 < ratios[-1] < 0.16 and ratios[0] < 0.2, (errs, ratios)
+
+
+def _keyed(mesh, N, nrhs, seed):
+    """x_at(m, pts) from the counter-based keyed generator: equal values at every copy of a point."""
+    def at(m, pts):
+        keys = M.point_keys(mesh.tets[m], np.asarray(pts), N)
+        return W.uniform_keyed(keys, 3 * nrhs, seed).reshape(-1, 3, nrhs)
+    return at
+
+
+def _interface_samples(S, rng, count):
+    """Lattice points of every kind: inside a macro, on shared and boundary faces, edges, vertices."""
+    N = S.N
+    w = np.stack([N - S.pts.sum(axis=1), S.pts[:, 0], S.pts[:, 1], S.pts[:, 2]], axis=1)
+    zeros = (w == 0).sum(axis=1)
+    out = []
+    for m in rng.choice(S.mesh.nmacro, size=count):
+        for z in (0, 1, 2, 3):
+            cand = np.nonzero(zeros == z)[0]
+            if len(cand):
+                out.append((int(m), S.pts[rng.choice(cand)]))
+    return out
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+@pytest.mark.parametrize("meshname,level", [("cube48", 1), ("cube6", 2)])
+def test_sampled_epsilon_rows_match_assembled(meshname, level, bc):
+    """The sampled epsilon rows and mu-adjoint (every macro that stores a point, every micro-tet
+    around it) against the assembled operator and adjoint, on points of every kind."""
+    S = _space(meshname, level, 2)
+    nrhs = 3
+    mu = W.viscosity_mu(S.coords)
+    mu_p = L.to_packed(S, mu)
+    K = A.epsilon_matrix(S, ("field", S, mu), 4, bc)
+    xat, gat = _keyed(S.mesh, S.N, nrhs, 7), _keyed(S.mesh, S.N, nrhs, 8)
+    P = M.lattice_size(S.N)
+    xp = np.concatenate([xat(m, S.pts) for m in range(S.mesh.nmacro)])       # packed, consistent copies
+    gp = np.concatenate([gat(m, S.pts) for m in range(S.mesh.nmacro)])
+    assert L.copies_spread(S, xp.reshape(-1), 3, nrhs) == 0.0
+    X = L.from_packed(S, xp.reshape(-1), 3, nrhs).reshape(S.ndof * 3, nrhs)
+    G = L.from_packed(S, gp.reshape(-1), 3, nrhs).reshape(S.ndof * 3, nrhs)
+    Y = (K @ X).reshape(S.ndof, 3, nrhs)
+    dmu = sum(A.epsilon_coeff_adjoint(S, X[:, r], G[:, r], 4, bc) for r in range(nrhs))
+    samples = _interface_samples(S, np.random.default_rng(3), 6)
+    ys = A.sampled_epsilon_rows(S.mesh, level, mu_p, xat, samples, 4, bc)
+    ds = A.sampled_epsilon_adjoint(S.mesh, level, xat, gat, samples, 4, bc)
+    gids = [S.gid[m, M.packed_position(p[None], S.N)[0]] for m, p in samples]
+    assert np.allclose(ys, Y[gids], rtol=1e-13, atol=1e-13 * np.abs(Y).max())
+    assert np.allclose(ds, dmu[gids], rtol=1e-13, atol=1e-13 * np.abs(dmu).max())
+    assert P * S.mesh.nmacro == len(xp)

@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = [
     "reference_tet", "kuhn_box", "cube6", "cube48", "cuboid36",
-    "uniform", "fourier_field_params", "fourier_field", "sin3_coeff",
+    "uniform", "uniform_keyed", "fourier_field_params", "fourier_field", "sin3_coeff",
     "manufactured_u", "manufactured_f", "viscosity_mu",
 ]
 
@@ -79,6 +79,37 @@ def cuboid36():
 def uniform(n: int, seed: int, dtype=np.float64) -> np.ndarray:
     """n values uniform on [-1, 1] from numpy's default_rng(seed)."""
     return np.random.default_rng(seed).uniform(-1.0, 1.0, n).astype(dtype)
+
+
+_MASK64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def _splitmix64(z: np.ndarray) -> np.ndarray:
+    """The splitmix64 finaliser (Steele, Lea and Flood, OOPSLA 2014) on uint64 arrays."""
+    z = (z + np.uint64(0x9E3779B97F4A7C15)) & _MASK64
+    z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _MASK64
+    z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _MASK64
+    return z ^ (z >> np.uint64(31))
+
+
+def uniform_keyed(keys: np.ndarray, ncols: int, seed: int) -> np.ndarray:
+    """Values uniform on [-1, 1) that depend only on a point's integer key, the column and the seed.
+
+    keys: (P, K) integers identifying each point (the caller passes an exact global key, so every
+    stored copy of a point shared by several macros receives the same values).  Returns (P, ncols):
+    column c of point p is splitmix64 chained over (seed, key words, c), its top 53 bits scaled to
+    [0, 1), then mapped to [-1, 1).  Counter-based, so any subset of points can be regenerated alone.
+    """
+    keys = np.asarray(keys, dtype=np.int64)
+    with np.errstate(over="ignore"):
+        h = np.full(len(keys), np.uint64(seed) ^ np.uint64(0x5851F42D4C957F2D), dtype=np.uint64)
+        for c in range(keys.shape[1]):
+            h = _splitmix64(h ^ keys[:, c].astype(np.uint64))
+        out = np.empty((len(keys), ncols))
+        for c in range(ncols):
+            z = _splitmix64(h ^ np.uint64(c + 1))
+            out[:, c] = (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return 2.0 * out - 1.0
 
 
 def fourier_field_params(seed: int = 0, modes: int = 8):
