@@ -39,12 +39,6 @@ LEGS = [
     ("p2_sin3_f64", 2, ("sin3",), 4, "f64"),
     ("p2_sin3_f32", 2, ("sin3",), 4, "f32"),
 ]
-# Legs that stand in while a kernel of the list above is not built yet.
-FALLBACK_LEGS = {
-    "p1_sin3_f64": ("p1_const_f64", 1, ("const", 1.0), 2, "f64"),
-    "p1_sin3_f32": ("p1_const_f32", 1, ("const", 1.0), 2, "f32"),
-}
-
 # Algorithmic FLOPs per unit (point or micro-tet) of each apply variant.
 def flops_per_unit(name: str, degree: int, nq: int):
     if name.startswith("p1_const"):
@@ -58,6 +52,15 @@ def flops_per_unit(name: str, degree: int, nq: int):
     return ("dof", 0.0)
 
 
+# FLOP (FMA = 2) per micro-tet and right-hand side of the epsilon kernels as formulated: the affine
+# symmetric gradient of the three components (390: reference affine terms, J^-1 map, 24 entries),
+# per quadrature point its value (36), the stress (6) and its moments (42), i.e. 84 x 14 points, the
+# moments mapped back and tested (342), mu at the points shared by the right-hand sides (308 / 16);
+# the adjoint forms the terms of u and g (780), per point both gradients, E(g) : E(u) / 2 and the
+# ten basis moments (106 x 14), and sums over the right-hand sides by shuffles (40).
+EPS_FLOP_PER_TET_RHS = {"apply": 390 + 84 * 14 + 342 + 19, "adjoint": 780 + 106 * 14 + 40}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -67,9 +70,14 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-# FP64 / FP32 peaks from unit counts at the maximum SM clock (152 SMs x 2 / 128 FMA per clock x
-# 2 FLOP x 2.07 GHz); FMA-chain probes measure 1.10 / 77.0 TFLOP/s (profiles/alu_peaks.md)
-ALU_PEAK_TFLOPS = {"f64": 1.26, "f32": 80.5}
+# FP64 / FP32 ALU peaks from unit counts: FMA per clock per SM (GB300: 2 FP64, 128 FP32; the
+# FMA-chain probe paper_2404_08371_gb300/peaks.cu measures the per-clock rate) x 2 FLOP x SMs x the
+# SM clock sampled by nvidia-smi during the timed region (the maximum clock if no sample was taken).
+FMA_PER_CLK_SM = {"f64": 2, "f32": 128}
+
+
+def alu_peak_tflops(dt: str, sms: int, sm_mhz: float) -> float:
+    return FMA_PER_CLK_SM[dt] * 2.0 * sms * sm_mhz * 1e6 / 1e12
 
 
 def load_traffic():
@@ -135,58 +143,99 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(seconds_budget: float = 20.0):
-    """The oracle as it stands on the host: element-by-element CSR assembly + SpMV (FP64, 1 thread).
+def host_cpu():
+    """CPU model, logical CPU count and the CPUs this process may run on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(), "machine": platform.machine(),
+            "nproc": os.cpu_count(), "affinity": len(os.sched_getaffinity(0))}
 
-    Bounded sample: the same macro and coefficients at level 6 (P1) and
-    level 5 (P2); MDoF/s of one apply = interior DoFs / SpMV time, plus the
-    assembly time per DoF reported separately.
-    """
+
+CPU_LEGS = [("p1_sin3", 1, 7, 2), ("p2_sin3", 2, 6, 4)]   # (name, degree, level, quadrature degree)
+
+
+def cpu_assemble():
+    """The oracle's operators of the CPU sample: the reference macro, sin3 coefficient, Dirichlet,
+    P1 at level 7 and P2 at level 6 (366,145 points each; the level-8 operators take minutes to
+    assemble, beyond a bounded sample).  Returns [(name, level, interior dofs, CSR, x, seconds)]."""
     import workloads as W
     from oracle import assemble as OA, mesh as OM
-    v, t = W.reference_tet()
-    mm = OM.MacroMesh(v, t)
-    res = {}
-    tot_dofs, tot_spmv, tot_asm = 0, 0.0, 0.0
-    for name, degree, level, qd in [("p1_sin3", 1, 6, 2), ("p2_sin3", 2, 5, 4)]:
+    mm = OM.MacroMesh(*W.reference_tet())
+    out = []
+    for name, degree, level, qd in CPU_LEGS:
         t0 = time.perf_counter()
         S = OA.Space(mm, level, degree)
         A = OA.diffusion_matrix(S, ("sin3",), qd, "dirichlet")
-        t_asm = time.perf_counter() - t0
-        x = W.uniform(S.ndof, seed=0)
-        reps = 0
-        t0 = time.perf_counter()
-        while True:
-            A @ x
-            reps += 1
-            if time.perf_counter() - t0 > 1.0 and reps >= 3:
-                break
-        t_spmv = (time.perf_counter() - t0) / reps
-        nint = int(S.interior.sum())
-        res[name] = {"level": level, "dofs": nint, "spmv_mdofs": nint / t_spmv / 1e6,
-                     "assembly_s": t_asm, "assembly_plus_spmv_mdofs": nint / (t_asm + t_spmv) / 1e6}
-        tot_dofs += nint
-        tot_spmv += t_spmv
-        tot_asm += t_asm
+        out.append((name, level, int(S.interior.sum()), A, W.uniform(S.ndof, seed=0), time.perf_counter() - t0))
+    return out
+
+
+def time_spmv(fn, min_s: float = 1.0) -> float:
+    """Mean seconds of fn() over repetitions filling at least min_s (at least 3)."""
+    fn()
+    reps, t0 = 0, time.perf_counter()
+    while reps < 3 or time.perf_counter() - t0 < min_s:
+        fn()
+        reps += 1
+    return (time.perf_counter() - t0) / reps
+
+
+def cpu_baseline():
+    """The oracle as it stands on the host: element-by-element CSR assembly, then the sparse apply,
+    (i) scipy on one thread, (ii) the oracle's OpenMP CSR product on every core, (iii) assembly
+    timed apart; plus the oracle's FP64 FMG on the FMG workload's mesh at level 4."""
+    from oracle import spmv
+    host = host_cpu()
+    threads = spmv.max_threads()
+    res = {}
+    dofs = t1 = tn = t_asm = 0.0
+    for name, level, nint, A, x, ta in cpu_assemble():
+        op = spmv.CsrSpmv(A)
+        s1 = time_spmv(lambda: A @ x)
+        sn = time_spmv(lambda: op(x, threads))
+        res[name] = {"level": level, "dofs": nint, "spmv_1thread_mdofs": nint / s1 / 1e6,
+                     "spmv_all_cores_mdofs": nint / sn / 1e6, "assembly_s": ta,
+                     "assembly_plus_spmv_mdofs": nint / (ta + s1) / 1e6}
+        dofs, t1, tn, t_asm = dofs + nint, t1 + s1, tn + sn, t_asm + ta
     # the oracle's FP64 FMG + V(2,2) on the FMG workload's mesh, at a level it finishes in seconds
-    from oracle import mg as OMG
+    import workloads as W
+    from oracle import mesh as OM, mg as OMG
     fl = 4
     t0 = time.perf_counter()
     H = OMG.Hierarchy(OM.MacroMesh(*W.cube6()), fl, 2, quad_degree=4)
-    bs = [OMG.load_vector(sp, W.manufactured_f) for sp in H.spaces]
+    b = OMG.load_vector(H.spaces[fl], W.manufactured_f)
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
-    xf, cycles, hist = H.fmg(bs, tol=1e-10)
+    xf, cycles, hist = H.fmg(b, tol=1e-10)
     t_solve = time.perf_counter() - t0
     nint = int(H.spaces[fl].interior.sum())
-    fmg = {"workload": "unit cube as 6 macros, level %d, P2 Poisson, FMG + V(2,2), tol 1e-10, FP64" % fl,
+    fmg = {"workload": "unit cube as 6 macros, level %d, P2 Poisson, FMG (coarse right-hand sides restricted) "
+                       "+ V(2,2), tol 1e-10, FP64, one thread" % fl,
            "dofs": nint, "setup_s": t_setup, "solve_s": t_solve, "cycles": cycles,
            "rel_residual": float(hist[-1]), "l2_error": OMG.l2_error(H.spaces[fl], xf, W.manufactured_u),
            "mdofs_per_s": nint / t_solve / 1e6}
-    return {"value": tot_dofs / tot_spmv / 1e6, "unit": "MDoF/s", "cores": 1, "kind": "oracle",
-            "sample": "reference macro, P1 sin3 at level 6 + P2 sin3 at level 5, FP64 CSR SpMV (assembly timed "
-                      "separately: %.1f s)" % tot_asm,
-            "legs": res, "fmg": fmg}
+    return {"value": dofs / tn / 1e6, "unit": "MDoF/s", "cores": threads, "kind": "oracle",
+            "sample": "reference macro, sin3 coefficient, Dirichlet: P1 at level 7 + P2 at level 6 (366,145 points "
+                      "each, the level-8 workload's operators at 1/8 of its size), FP64 CSR product on %d OpenMP "
+                      "threads (assembly timed separately: %.1f s)" % (threads, t_asm),
+            "value_1thread": dofs / t1 / 1e6, "host": host, "legs": res, "fmg": fmg}
 
 
 def run_fmg(hhg, torch, level: int, reps: int = 1):
@@ -280,7 +329,7 @@ def run_const_legs(hhg, torch, flush, peak_gbs: float, reps: int = 5):
     return out
 
 
-def run_eps(hhg, torch, flush, level: int = 6, nrhs: int = 16, reps: int = 1):
+def run_eps(hhg, torch, flush, fp64_peak: float, level: int = 6, nrhs: int = 16, reps: int = 1):
     """P2 vector epsilon operator on the unit cube as 48 macros, mu = 10^(3(z-0.5)) as a P2 field,
     nrhs seeded right-hand sides in one launch (FP64), and its adjoint in mu."""
     import workloads as W
@@ -300,10 +349,47 @@ def run_eps(hhg, torch, flush, level: int = 6, nrhs: int = 16, reps: int = 1):
     ms = time_apply(torch, lambda: op.apply(x, out=y, nrhs=nrhs), flush, reps)
     ms_adj = time_apply(torch, lambda: op.adjoint_coeff(x, y, nrhs=nrhs), flush, reps)
     ntet = len(t) * 8 ** level
+    fl_apply = EPS_FLOP_PER_TET_RHS["apply"] * ntet * nrhs
+    fl_adj = EPS_FLOP_PER_TET_RHS["adjoint"] * ntet * nrhs
     return {"workload": "unit cube as 48 macros, level %d, P2 vector epsilon, mu = 10^(3(z-0.5)) P2 field, "
                         "%d right-hand sides, FP64, Dirichlet" % (level, nrhs),
             "apply_ms": ms, "adjoint_ms": ms_adj, "mdofs": 3 * inner * nrhs / ms / 1e3,
-            "adjoint_mdofs": 3 * inner * nrhs / ms_adj / 1e3, "micro_tets": ntet}
+            "adjoint_mdofs": 3 * inner * nrhs / ms_adj / 1e3, "micro_tets": ntet,
+            "flop_per_tet_per_rhs": dict(EPS_FLOP_PER_TET_RHS),
+            "apply_tflops": fl_apply / ms / 1e9, "apply_fp64_frac": fl_apply / ms / 1e9 / fp64_peak,
+            "adjoint_tflops": fl_adj / ms_adj / 1e9, "adjoint_fp64_frac": fl_adj / ms_adj / 1e9 / fp64_peak,
+            "fp64_peak_tflops": fp64_peak}
+
+
+def run_adjoint(hhg, torch, flush, peak_gbs: float, level: int = 7, reps: int = 5):
+    """The coefficient-inversion workload's kernels: reference macro at level 7, P1, k = exp(g) as a
+    P1 nodal field (g the seeded sum of 8 Fourier modes, amplitude 0.5), u and g ~ U[-1, 1] (seeds 1
+    and 2), Dirichlet; the adjoint dk_v = sum_T 1/4 g_T^T A0_T u_T (reads u and g, writes dk) and
+    the apply of the same operator, FP64 and FP32."""
+    import workloads as W
+    v, t = W.reference_tet()
+    mesh = hhg.Mesh(v, t, level)
+    n = mesh.vec_size(1)
+    xyz = mesh.coordinates(1).cpu().numpy()
+    kval = np.exp(W.fourier_field(xyz, seed=0))
+    tot, inner = mesh.dof_count(1)
+    out = {"workload": "reference macro, level %d, P1, k = exp(g) P1 field (8 Fourier modes, amplitude 0.5), "
+                       "Dirichlet: adjoint dL/dk and apply" % level}
+    for dt, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+        k = torch.from_numpy(kval).to("cuda", tdt)
+        op = hhg.Operator(mesh, degree=1, coeff=("field_p1", k), bc="dirichlet", quad_degree=2)
+        u = torch.from_numpy(W.uniform(n, seed=1)).to("cuda", tdt)
+        g = torch.from_numpy(W.uniform(n, seed=2)).to("cuda", tdt)
+        dk = torch.empty_like(u)
+        y = torch.empty_like(u)
+        ms_adj = time_apply(torch, lambda: op.adjoint_coeff(u, g, out=dk), flush, reps)
+        ms_app = time_apply(torch, lambda: op.apply(u, out=y), flush, reps)
+        nbytes = 3 * n * u.element_size()          # read u and g, write dk
+        out[dt] = {"adjoint_ms": ms_adj, "adjoint_mdofs": inner / ms_adj / 1e3, "adjoint_gbs": nbytes / ms_adj / 1e6,
+                   "adjoint_hbm_frac": nbytes / ms_adj / 1e6 / peak_gbs, "apply_ms": ms_app,
+                   "apply_mdofs": inner / ms_app / 1e3, "points": n}
+        del op, k, u, g, dk, y
+    return out
 
 
 def run_n1(hhg, torch, flush, level: int = 7, reps: int = 3):
@@ -392,24 +478,35 @@ def run_precomputed(hhg, torch, flush, level: int = 8, reps: int = 3):
 
 
 def run_reference(args):
+    """The oracle as the reference arm: its operators assembled once (outside the steps, as the
+    library's operators are created before its timed region), then every step applies each leg
+    once with the oracle's OpenMP CSR product on all host cores.  Rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    t0 = time.perf_counter()
+    from oracle import spmv
+    threads = spmv.max_threads()
+    legs = [(nint, spmv.CsrSpmv(A), x) for _, _, nint, A, x, _ in cpu_assemble()]
+    dofs = sum(nint for nint, _, _ in legs)
     times = []
-    cb = None
     for s in range(args.warmup + args.steps):
-        cb = cpu_baseline()
+        t0 = time.perf_counter()
+        for _, op, x in legs:
+            op(x, threads)
         if s >= args.warmup:
             times.append(time.perf_counter() - t0)
-        t0 = time.perf_counter()
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MDoF/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    ms = 1e3 * statistics.mean(times)
+    value = dofs / (ms * 1e-3) / 1e6
+    sample = ("reference macro, sin3 coefficient, Dirichlet: P1 at level 7 + P2 at level 6 (366,145 points each, "
+              "the level-8 workload's operators at 1/8 of its size), FP64 CSR product on %d OpenMP threads" % threads)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MDoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "reference macro-tetrahedron, variable-coefficient P1/P2 diffusion (bounded "
-                                   "sample of the level-8 workload: P1 level 6, P2 level 5)"},
-            "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample", "value", "unit")},
-            "e2e": {"value": cb["value"], "unit": "MDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                                   "sample of the level-8 workload: P1 level 7, P2 level 6)"},
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "sample": sample, "value": value, "unit": "MDoF/s",
+                             "host": host_cpu()},
+            "e2e": {"value": value, "unit": "MDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
@@ -445,27 +542,12 @@ def main():
     v, t = W.reference_tet()
     mesh = hhg.Mesh(v, t, LEVEL)
     legs = []
-    skipped = []
     for leg in LEGS:
         name, degree, coeff, qd, dt = leg
-        try:
-            op = hhg.Operator(mesh, degree=degree, coeff=coeff, bc="dirichlet", quad_degree=qd)
-            x0 = torch.empty(mesh.vec_size(degree), dtype=torch.float64, device=dev)
-            x0.copy_(torch.from_numpy(W.uniform(mesh.vec_size(degree), seed=0)))
-            x = x0 if dt == "f64" else x0.float()
-            op.apply(x)
-            torch.cuda.synchronize()
-        except _lib.HHGError as e:
-            if e.code != _lib.HHG_E_UNSUPPORTED:
-                raise
-            if name not in FALLBACK_LEGS:
-                skipped.append(name)
-                continue
-            skipped.append(name)
-            name, degree, coeff, qd, dt = FALLBACK_LEGS[name]
-            op = hhg.Operator(mesh, degree=degree, coeff=coeff, bc="dirichlet", quad_degree=qd)
-            x0 = torch.from_numpy(W.uniform(mesh.vec_size(degree), seed=0)).to(dev)
-            x = x0 if dt == "f64" else x0.float()
+        op = hhg.Operator(mesh, degree=degree, coeff=coeff, bc="dirichlet", quad_degree=qd)
+        x0 = torch.empty(mesh.vec_size(degree), dtype=torch.float64, device=dev)
+        x0.copy_(torch.from_numpy(W.uniform(mesh.vec_size(degree), seed=0)))
+        x = x0 if dt == "f64" else x0.float()
         y = torch.empty_like(x)
         tot, inner = mesh.dof_count(degree)
         legs.append({"name": name, "op": op, "x": x, "y": y, "dofs": inner, "npts": x.numel(),
@@ -506,6 +588,13 @@ def main():
         step_ms += sum(L["ms"]) / args.steps
     dofs_step = sum(L["dofs"] for L in legs)
     step_ms, dofs_all, value = aggregate_replicas(step_ms, dofs_step, dev)
+    # the same rate over the FP64 legs alone and over the FP32 legs alone
+    value_by_dt = {}
+    for dt in ("f64", "f32"):
+        sel = [L for L in legs if L["dt"] == dt]
+        if sel:
+            value_by_dt[dt] = aggregate_replicas(sum(sum(L["ms"]) / args.steps for L in sel),
+                                                 sum(L["dofs"] for L in sel), dev)[2]
 
     # end to end through the C-ABI with host buffers: pinned H2D of x, apply, D2H of y
     h2d = d2h = 0
@@ -579,6 +668,9 @@ def main():
 
     peaks = load_peaks()
     traffic = load_traffic()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    run_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    alu_peak = {dt: alu_peak_tflops(dt, sms, run_mhz) for dt in FMA_PER_CLK_SM}
     details = {}
     dom = None
     for L in legs:
@@ -590,7 +682,7 @@ def main():
         d = {"ms": ms, "mdofs": L["dofs"] / (ms * 1e-3) / 1e6, "gbs": nbytes / (ms * 1e-3) / 1e9,
              "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
              "tflops": flops / (ms * 1e-3) / 1e12,
-             "alu_frac": flops / (ms * 1e-3) / 1e12 / ALU_PEAK_TFLOPS[L["dt"]],
+             "alu_frac": flops / (ms * 1e-3) / 1e12 / alu_peak[L["dt"]],
              "dofs": L["dofs"], "bytes": nbytes, "flops": flops}
         details[L["name"]] = d
         if dom is None or ms > details[dom]["ms"]:
@@ -598,8 +690,11 @@ def main():
     D = details[dom]
     dom_leg = [L for L in legs if L["name"] == dom][0]
     if D["alu_frac"] > D["hbm_frac"]:
-        roof = {"bound": "alu", "achieved": D["tflops"], "peak": ALU_PEAK_TFLOPS[dom_leg["dt"]], "unit": "TFLOP/s",
-                "frac": D["alu_frac"], "peak_src": "unit-count peak at 2.07 GHz (profiles/alu_peaks.md)"}
+        roof = {"bound": "alu", "achieved": D["tflops"], "peak": alu_peak[dom_leg["dt"]], "unit": "TFLOP/s",
+                "frac": D["alu_frac"],
+                "peak_src": "unit-count %s peak: %d FMA/clock/SM x 2 FLOP x %d SMs x %.0f MHz (median SM clock "
+                            "sampled during the timed region)" % (dom_leg["dt"], FMA_PER_CLK_SM[dom_leg["dt"]], sms,
+                                                                  run_mhz)}
     else:
         roof = {"bound": "hbm", "achieved": D["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": D["hbm_frac"],
                 "peak_src": peaks["src"] + " (burst copy)"}
@@ -614,7 +709,9 @@ def main():
     if not args.no_extra:
         extra["const_legs"] = run_const_legs(hhg, torch, flush, peaks["hbm_gbs"])
         torch.cuda.empty_cache()
-        extra["epsilon"] = run_eps(hhg, torch, flush)
+        extra["coefficient_adjoint"] = run_adjoint(hhg, torch, flush, peaks["hbm_gbs"])
+        torch.cuda.empty_cache()
+        extra["epsilon"] = run_eps(hhg, torch, flush, alu_peak["f64"])
         torch.cuda.empty_cache()
         extra["n1"] = run_n1(hhg, torch, flush)
         torch.cuda.empty_cache()
@@ -633,13 +730,14 @@ def main():
     # per apply on a single macro: the marching kernel, plus the Dirichlet-row kernel on lattices
     # whose marching tiles add their shared j-faces atomically (at least 64 cubes per edge)
     launches = sum(2 if 2 ** LEVEL >= 64 else 1 for _ in legs) * args.steps
-    line = {"metric": METRIC, "value": value, "unit": "MDoF/s", "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC, "value": value, "value_f64_legs": value_by_dt.get("f64"),
+            "value_f32_legs": value_by_dt.get("f32"), "unit": "MDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "+".join(sorted({L["dt"] for L in legs})), "data": "synthetic",
             "config": {"workload": "reference macro-tetrahedron at level %d, legs: %s" % (
                 LEVEL, ", ".join(L["name"] for L in legs)), "level": LEVEL, "bc": "dirichlet",
                 "l2": "flushed before every apply (512 MB write)", "parallelism": "replicas" if world > 1 else "1gpu"},
-            "legs": details, "legs_not_built": skipped, "roofline": roof,
+            "legs": details, "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "MDoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "e2e_detail": e2e_detail,
             "gpu_launches": launches, "clocks": clk, "wall_s_timed": wall}
@@ -648,8 +746,8 @@ def main():
         line["fmg"] = fmg
     if cb is not None:
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
-        line["cpu_baseline"]["legs"] = cb["legs"]
-        line["cpu_baseline"]["fmg"] = cb["fmg"]
+        for k in ("value_1thread", "host", "legs", "fmg"):
+            line["cpu_baseline"][k] = cb[k]
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
