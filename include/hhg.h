@@ -141,10 +141,10 @@ int hhg_op_set_field(hhg_op_t* op, const void* field, int field_dtype);
  * vectors of the op's space (ncomp = 3 for EPSILON), nrhs right-hand sides
  * (nrhs >= 1; > 1 only for EPSILON, at most 256, else HHG_E_UNSUPPORTED).
  * y is overwritten; x and y must not overlap.  The apply computes every
- * local matrix on the fly.  Variable-coefficient, P2 and Nedelec applies on
- * lattices of 64 or more cubes per edge add the points on the faces of their
- * GPU tiles atomically (at most four partial sums a point), so two calls may
- * differ in the last bits there; all other results repeat bit for bit. */
+ * local matrix on the fly.  Results repeat bit for bit from call to call:
+ * on lattices of 64 or more cubes per edge the points on the faces between
+ * GPU tiles collect their partial sums (at most four) in a fixed order,
+ * through a scratch array allocated with the operator. */
 int hhg_op_apply(hhg_op_t* op, const void* x, void* y, int dtype, int nrhs, void* stream);
 
 /* Adjoint in the coefficient of a FIELD operator (A is linear in k):
@@ -157,7 +157,10 @@ int hhg_op_apply(hhg_op_t* op, const void* x, void* y, int dtype, int nrhs, void
 int hhg_op_apply_adjoint_coeff(hhg_op_t* op, const void* u, const void* g, void* dk, int dtype, int nrhs,
                                void* stream);
 
-/* d = diag(A) (Dirichlet rows: 1), packed, overwritten (scalar ops). */
+/* d = diag(A) (Dirichlet rows: 1), packed, overwritten.  Scalar DIFFUSION
+ * operators and CURLCURL operators (Eq. N1; the diagonal of an edge does not
+ * depend on its orientation; vertex points of the doubled lattice, which
+ * carry no DoF, get 0). */
 int hhg_op_diagonal(hhg_op_t* op, void* d, int dtype, void* stream);
 
 /* Precomputed variant of Eq. 4.1 for a variable-coefficient DIFFUSION op
@@ -203,6 +206,25 @@ int hhg_prolongate(const hhg_mesh_t* mesh, int level_fine, int degree, const voi
 int hhg_restrict(const hhg_mesh_t* mesh, int level_fine, int degree, const void* rf, void* rc, int dtype,
                  void* stream);
 
+/* Grid transfers of Nedelec edge vectors (Eq. N1 space, Section 8's
+ * multigrid for the curl-curl problem).  xf = P xc: the tangential integral
+ * along every fine edge of the coarse Whitney field (the spaces are nested);
+ * rc = P^T rf over distinct fine edges, coarse Dirichlet (tangential
+ * boundary) entries zero.  Vectors in the packed Nedelec layout of
+ * hhg_op_create_curlcurl (doubled lattice, each copy in its macro's
+ * orientation, vertex points zero); both outputs consistent, overwritten. */
+int hhg_prolongate_edges(const hhg_mesh_t* mesh, int level_fine, const void* xc, void* xf, int dtype, void* stream);
+int hhg_restrict_edges(const hhg_mesh_t* mesh, int level_fine, const void* rf, void* rc, int dtype, void* stream);
+
+/* Discrete gradient of the Nedelec space (the nodal part of Hiptmair's
+ * hybrid smoother, Section 8).  hhg_gradient: e = G p, the tangential
+ * integral of grad p along every edge of level `level`, p a consistent P1
+ * packed vector of that level, e a packed Nedelec vector (vertex points 0).
+ * hhg_gradient_transpose: p = G^T e over distinct edges, Dirichlet vertices
+ * zero, consistent.  Outputs overwritten; errors HHG_E_ARG, HHG_E_CUDA. */
+int hhg_gradient(const hhg_mesh_t* mesh, int level, const void* p, void* e, int dtype, void* stream);
+int hhg_gradient_transpose(const hhg_mesh_t* mesh, int level, const void* e, void* p, int dtype, void* stream);
+
 /* Load vector b_i = int f phi_i for f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
  * (the manufactured Poisson right-hand side), by the 14-point rule per
  * micro-tet; Dirichlet entries zero.  FP64 output, packed, overwritten. */
@@ -231,9 +253,10 @@ int hhg_cheb_smooth(hhg_op_t* op, const void* b, void* x, const void* dinv, doub
  * Limits and rules:
  *  - the operator's vectors may have at most 524288 entries
  *    (hhg_vec_size); larger operators get HHG_E_ARG;
- *  - the first call on a device looks up the array's device address for that
- *    device (cudaGetSymbolAddress); make that first call before any stream
- *    capture begins;
+ *  - the array's device address is looked up (cudaGetSymbolAddress, which
+ *    can load the library's device image) when an operator is created on
+ *    the device, so the call itself triggers no module loading; create the
+ *    operator before any stream capture begins;
  *  - all calls share the one array, which keeps the last call's contents
  *    (nothing in it needs to start at zero); calls that overlap on the GPU,
  *    e.g. on two streams at once, race with each other;

@@ -153,3 +153,23 @@ class N1Hierarchy:
             cycles += 1
             hist.append(np.linalg.norm(b - A @ x) / nb)
         return x, cycles, hist
+
+
+def load_vector(S: EdgeSpace, f, quad_degree: int = 5) -> np.ndarray:
+    """b_e = integral of f . phi_e over the domain for a vector field f of points (n, 3) -> (n, 3),
+    by element quadrature with the Whitney functions phi_e (global orientation); boundary entries
+    (tangential trace) zero."""
+    from . import quadrature
+    from .mesh import P2_EDGES as EDGES
+    xi, w = quadrature.rule(quad_degree)
+    lam = fe.bary(xi)
+    J, adet, Jinv = fe.jacobians(S.elem_X)
+    G = np.einsum("eji,aj->eai", Jinv, fe.GRAD_BARY)
+    pts = fe.map_points(S.elem_X, J, xi)
+    fq = f(pts.reshape(-1, 3)).reshape(len(S.elem_X), len(w), 3)
+    b = np.zeros(S.ndof)
+    for e, (a, c) in enumerate(EDGES):
+        phi = lam[None, :, a, None] * G[:, None, c, :] - lam[None, :, c, None] * G[:, None, a, :]
+        np.add.at(b, S.elem_dofs[:, e], np.einsum("k,q,kqd,kqd->k", adet, w, fq, phi) * S.elem_sign[:, e])
+    b[S.boundary] = 0.0
+    return b

@@ -108,6 +108,31 @@ class Mesh:
                                _stream()), "hhg_restrict")
         return out
 
+    def prolongate_edges(self, xc: torch.Tensor, level_fine: int, out: torch.Tensor | None = None):
+        out = self.empty(2, xc.dtype, level_fine) if out is None else out
+        check(lib.hhg_prolongate_edges(self.handle, level_fine, _dev_ptr(xc), _dev_ptr(out), dtype_code(xc),
+                                       _stream()), "hhg_prolongate_edges")
+        return out
+
+    def restrict_edges(self, rf: torch.Tensor, level_fine: int, out: torch.Tensor | None = None):
+        out = self.empty(2, rf.dtype, level_fine - 1) if out is None else out
+        check(lib.hhg_restrict_edges(self.handle, level_fine, _dev_ptr(rf), _dev_ptr(out), dtype_code(rf), _stream()),
+              "hhg_restrict_edges")
+        return out
+
+    def gradient(self, p: torch.Tensor, level: int | None = None, out: torch.Tensor | None = None):
+        lvl = self.level if level is None else level
+        out = self.empty(2, p.dtype, lvl) if out is None else out
+        check(lib.hhg_gradient(self.handle, lvl, _dev_ptr(p), _dev_ptr(out), dtype_code(p), _stream()), "hhg_gradient")
+        return out
+
+    def gradient_transpose(self, e: torch.Tensor, level: int | None = None, out: torch.Tensor | None = None):
+        lvl = self.level if level is None else level
+        out = self.empty(1, e.dtype, lvl) if out is None else out
+        check(lib.hhg_gradient_transpose(self.handle, lvl, _dev_ptr(e), _dev_ptr(out), dtype_code(e), _stream()),
+              "hhg_gradient_transpose")
+        return out
+
     def rhs_sin3_poisson(self, degree: int, level: int | None = None):
         lvl = self.level if level is None else level
         b = self.empty(degree, torch.float64, lvl)

@@ -360,13 +360,19 @@ int launch_eps(const hhg_op* op, const OpConst<T>* cst, int mode, int nrhs, cons
   if (mode == 2 && (nrhs > 32 || (32 % nrhs) != 0))
     return fail(HHG_E_UNSUPPORTED, "epsilon adjoint: nrhs must divide 32");
   if (nrhs > 256) return fail(HHG_E_UNSUPPORTED, "epsilon: at most 256 right-hand sides per call");
-  // tasks of live cubes per colour (cached in the operator for this number of cubes per CTA)
+  // tasks of live cubes per colour, cached in the operator per number of cubes per CTA: built and
+  // uploaded (asynchronously, on the caller's stream) at the first call with this batch size
   const int cpb = kEpsThreads / nrhs;
-  if (op->eps_cpb != cpb) {
-    std::vector<int4> tv;
-    int64_t off[9];
+  EpsTasks* et = nullptr;
+  {
+    auto it = op->eps_tasks.find(cpb);
+    if (it != op->eps_tasks.end()) et = it->second.get();
+  }
+  if (!et) {
+    std::unique_ptr<EpsTasks> nt(new EpsTasks());
+    std::vector<int4>& tv = nt->host;
     for (int color = 0; color < 8; ++color) {
-      off[color] = (int64_t)tv.size();
+      nt->off[color] = (int64_t)tv.size();
       const int px = color & 1, py = (color >> 1) & 1, pz = (color >> 2) & 1;
       for (int m = 0; m < nm; ++m)
         for (int kz = 0; kz < nz; ++kz)
@@ -377,22 +383,19 @@ int launch_eps(const hhg_op* op, const OpConst<T>* cst, int mode, int nrhs, cons
             for (int st = 0; st < len; st += cpb) tv.push_back(int4{st, jy, kz, m});
           }
     }
-    off[8] = (int64_t)tv.size();
-    cudaFree(op->d_eps_tasks);
-    op->d_eps_tasks = nullptr;
-    op->eps_cpb = 0;
-    HHG_CUDA_TRY(cudaMalloc(&op->d_eps_tasks, sizeof(int4) * std::max<size_t>(tv.size(), 1)));
+    nt->off[8] = (int64_t)tv.size();
+    HHG_CUDA_TRY(cudaMalloc(&nt->d, sizeof(int4) * std::max<size_t>(tv.size(), 1)));
     if (!tv.empty())
-      HHG_CUDA_TRY(cudaMemcpy(op->d_eps_tasks, tv.data(), sizeof(int4) * tv.size(), cudaMemcpyHostToDevice));
-    for (int c = 0; c < 9; ++c) op->eps_off[c] = off[c];
-    op->eps_cpb = cpb;
+      HHG_CUDA_TRY(cudaMemcpyAsync(nt->d, tv.data(), sizeof(int4) * tv.size(), cudaMemcpyHostToDevice, s));
+    et = nt.get();
+    op->eps_tasks[cpb] = std::move(nt);
   }
   const size_t bytes = sizeof(T) * (size_t)op->npts * (mode == 0 ? 3 * nrhs : 1);
   HHG_CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));
   for (int color = 0; color < 8; ++color) {
-    const unsigned grid = (unsigned)(op->eps_off[color + 1] - op->eps_off[color]);
+    const unsigned grid = (unsigned)(et->off[color + 1] - et->off[color]);
     if (grid == 0) continue;
-    const int4* tk = op->d_eps_tasks + op->eps_off[color];
+    const int4* tk = et->d + et->off[color];
 #define HHG_EPS(F, D)                                                                                          \
   do {                                                                                                       \
     const size_t sm = eps_apply_smem<T, F>();                                                                \

@@ -54,6 +54,15 @@ struct TileTasks {
   int kchunk = 32;
 };
 
+// Task list of the epsilon kernels for one number of cubes per CTA: tasks of colour c at
+// d[off[c] .. off[c+1]); the host copy stays alive while the asynchronous upload may read it.
+struct EpsTasks {
+  int4* d = nullptr;
+  int64_t off[9] = {0};
+  std::vector<int4> host;
+  ~EpsTasks() { cudaFree(d); }
+};
+
 struct Interface {
   int64_t ngroups = 0;
   int64_t nmembers = 0;
@@ -175,6 +184,12 @@ template <typename T>
 int launch_make_consistent(const Interface* itf, T* x, int per_point, cudaStream_t s);
 // Element-centric kernels (march.cu); mode 0 apply, 1 diagonal, 2 coefficient adjoint,
 // 3 load vector of f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z).
+// Scratch of the marching kernels' shared tile faces for an operator on lattices of at least
+// kMarchJAtomicN cubes per edge (march.cu); allocated at operator creation.
+int alloc_face_scratch(struct ::hhg_op* op);
+// Device address of the allocation-free smoother's scratch array on the current device (mg.cu),
+// looked up at operator creation.
+int noalloc_prepare();
 // Precomputed variant (march.cu): local matrices of all micro-tets into elem, and applies from them.
 template <typename T>
 int launch_elem_store(const struct ::hhg_op* op, T* elem, cudaStream_t s);
@@ -188,9 +203,14 @@ int launch_march(const struct ::hhg_op* op, const OpConst<T>* cst, int mode, con
 // Nedelec curl-curl + mass apply (march.cu, R = 2 traversal of the doubled lattice).
 template <typename T>
 int launch_n1(const struct ::hhg_op* op, const T* x, T* y, cudaStream_t s);
+template <typename T>
+int launch_n1_diag(const struct ::hhg_op* op, T* d, cudaStream_t s);
 // Interface sum with orientation signs (edge points of the doubled lattice).
 template <typename T>
 int launch_interface_sum_signed(const Interface* itf, T* y, bool dirichlet, cudaStream_t s);
+// Nedelec vectors: every copy of a shared edge set from the owner copy with its orientation sign.
+template <typename T>
+int launch_make_consistent_signed(const Interface* itf, T* x, cudaStream_t s);
 // P2 vector epsilon operator (eps.cu): mode 0 apply to nrhs right-hand sides, 2 adjoint in mu.
 template <typename T>
 int launch_eps(const struct ::hhg_op* op, const OpConst<T>* cst, int mode, int nrhs, const T* x, const T* g,
@@ -245,10 +265,8 @@ struct hhg_op {
   void* d_elem = nullptr;
   int elem_dtype = -1;
   // epsilon operator: per colour, the CTAs of live cubes (ci/2 start, cj/2, ck/2, macro), built on
-  // first use for eps_cpb cubes per CTA
-  mutable int4* d_eps_tasks = nullptr;
-  mutable int64_t eps_off[9] = {0};
-  mutable int eps_cpb = 0;
+  // the first use of each number of cubes per CTA (256 / nrhs) and kept
+  mutable std::map<int, std::unique_ptr<hhg::EpsTasks>> eps_tasks;
   void* d_n1_64 = nullptr;   // N1Const<double>[nmacro]
   void* d_n1_32 = nullptr;
   int N = 0, n = 0;
@@ -258,6 +276,11 @@ struct hhg_op {
   hhg::QuadRule rule;
   std::vector<hhg::OpConst<double>> h_const;
   const hhg::Interface* itf = nullptr;   // per-level data of the op's space (owned by the mesh)
+  // partial sums of the points shared by marching tiles (lattices of at least kMarchJAtomicN cubes
+  // per edge; march_kernel.cuh, FaceScratch): FP64-sized, per macro face_S slots
+  void* d_face = nullptr;
+  int64_t face_S = 0, face_Si = 0, face_Sj = 0;
+  int face_Ti = 0, face_Tj = 0;
   hhg::MGHierarchy* mg = nullptr;         // multigrid hierarchy, built by the first mg_solve
   hhg::OpWork* work = nullptr;            // work vectors of the standalone smoother calls
   ~hhg_op();

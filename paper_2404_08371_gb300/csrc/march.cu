@@ -176,6 +176,19 @@ int launch_march(const hhg_op* op, const OpConst<T>* cst, int mode, const T* x, 
   return fail(HHG_E_UNSUPPORTED, "no kernel for degree %d, coefficient %d, mode %d", op->degree, ct, mode);
 }
 
+int alloc_face_scratch(hhg_op* op) {
+  if (op->n < kMarchJAtomicN || op->kind == HHG_EPSILON) return HHG_OK;
+  const int64_t R = op->degree, N = op->N;
+  const int64_t Fi = 32 * R, Fj = kWarps * R;
+  op->face_Ti = (int)(N / Fi);
+  op->face_Tj = (int)(N / Fj);
+  op->face_Si = face_tri_sum(Fi, op->face_Ti, N);
+  op->face_Sj = face_tri_sum(Fj, op->face_Tj, N);
+  op->face_S = op->face_Si + op->face_Sj + (int64_t)op->face_Ti * op->face_Tj * (N + 1);
+  HHG_CUDA_TRY(cudaMalloc(&op->d_face, sizeof(double) * (size_t)op->face_S * op->mesh->nmacro()));
+  return HHG_OK;
+}
+
 // Squared L2 error of u_h against u = sin(pi x) sin(pi y) sin(pi z): one thread per cube,
 // the six micro-tets with the op's quadrature rule; per-CTA partial sums (no atomics).
 template <int R>
@@ -307,6 +320,15 @@ int launch_n1(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
   const OpConst<T>* cst = (const OpConst<T>*)(sizeof(T) == 8 ? op->d_const64 : op->d_const32);
   return launch_march_t<T, 2, HHG_COEFF_CONST, MODE_N1>(op, cst, x, nullptr, nullptr, y, s, a);
 }
+// Diagonal of the Nedelec operator (vertex points of the doubled lattice, which carry no DoF, get 0).
+template <typename T>
+int launch_n1_diag(const hhg_op* op, T* d, cudaStream_t s) {
+  const OpConst<T>* cst = (const OpConst<T>*)(sizeof(T) == 8 ? op->d_const64 : op->d_const32);
+  return launch_march_t<T, 2, HHG_COEFF_CONST, MODE_N1D>(op, cst, nullptr, nullptr, nullptr, d, s, n1_args<T>(op));
+}
+template int launch_n1_diag<double>(const hhg_op*, double*, cudaStream_t);
+template int launch_n1_diag<float>(const hhg_op*, float*, cudaStream_t);
+
 template int launch_n1<double>(const hhg_op*, const double*, double*, cudaStream_t);
 template int launch_n1<float>(const hhg_op*, const float*, float*, cudaStream_t);
 

@@ -13,9 +13,10 @@
 //   k: the top face of a cube is carried in registers to the next layer.
 // On small lattices adjacent CTAs overlap by one cube in i and j; the overlapping cube's points
 // are written by exactly one of them.  On lattices of at least kMarchJAtomicN cubes per edge the
-// tiles do not overlap in i or j: the output is zeroed first, the points on a tile's i- and j-faces
-// are added atomically by the tiles that share them, all others are stored once, and the Dirichlet
-// rows are written afterwards by march_dirichlet_kernel.
+// tiles do not overlap in i or j: a point on a face between tiles is stored by the lowest of them,
+// the others store their partial sums into a per-operator scratch (FaceScratch), and
+// march_finish_kernel adds those in a fixed order and writes the Dirichlet rows; no atomics, so
+// every apply is bitwise repeatable.
 //
 // Local matrices are never stored: the quadrature is fused with the local apply
 // (Remark 4.1): grad u at each point from the 10 nodal values, scaled by
@@ -32,7 +33,9 @@ namespace hhg {
 
 constexpr int kWarps = kMarchWarps;   // warps per CTA along j
 
-enum { MODE_APPLY = 0, MODE_DIAG = 1, MODE_ADJ = 2, MODE_RHS = 3, MODE_N1 = 4 };
+enum { MODE_APPLY = 0, MODE_DIAG = 1, MODE_ADJ = 2, MODE_RHS = 3, MODE_N1 = 4, MODE_N1D = 5 };
+// the Nedelec modes: apply (MODE_N1) and diagonal (MODE_N1D)
+__host__ __device__ constexpr bool is_n1_mode(int m) { return m == MODE_N1 || m == MODE_N1D; }
 
 // Extra inputs of the Nedelec mode (unused otherwise).
 template <typename T>
@@ -43,6 +46,28 @@ struct N1Args {
   T alpha_c = T(0), beta_c = T(0);
   int n = 0;                  // cubes per edge (P1 lattice resolution)
 };
+
+// Partial sums of the points that neighbouring marching tiles share (lattices of at least
+// kMarchJAtomicN cubes per edge).  Tiles own 32 x kWarps columns of cubes; a point on the face
+// between two tiles along i (pi = Fi t, Fi = 32 R) or along j (pj = Fj t', Fj = kWarps R) gets a
+// partial sum from each side, a point on both from four tiles.  The lowest tile stores its partial
+// into the output; the others store theirs into this per-op scratch, one slot each: per macro the
+// i-face points [0, Si) (faces t = 1..Ti, triangle (pj, pk) by rows pk), the j-face points
+// [Si, Si + Sj) (faces t' = 1..Tj, triangle (pi, pk)) and the corner lines [Si + Sj, S)
+// ((t, t') dense, pk = 0..N).  march_finish_kernel adds them in a fixed order.
+template <typename T>
+struct FaceScratch {
+  T* d = nullptr;
+  int64_t S = 0, Si = 0, Sj = 0;   // per macro: all slots, i-face slots, j-face slots
+  int Ti = 0, Tj = 0;              // tile faces along i and j (pi = Fi t <= N, pj = Fj t' <= N)
+};
+
+// sum_{u=1}^{T} tri(N - F u), tri(m) = (m+1)(m+2)/2, in closed form
+__host__ __device__ inline int64_t face_tri_sum(int64_t F, int64_t T, int64_t N) {
+  const int64_t a = N + 1;
+  return (T * a * (a + 1) - F * (2 * a + 1) * (T * (T + 1) / 2) + F * F * (T * (T + 1) * (2 * T + 1) / 6)) / 2;
+}
+__host__ __device__ inline int64_t face_tri_row(int64_t m, int64_t r) { return r * (2 * m + 3 - r) / 2; }
 
 __host__ __device__ constexpr int coff(int o, int v, int d) {
   constexpr int t[6][4][3] = {
@@ -229,13 +254,13 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
                                                             const int4* __restrict__ tasks, int kChunk,
                                                             const T* __restrict__ x, const T* __restrict__ g,
                                                             const T* __restrict__ kf, T* __restrict__ out,
-                                                            N1Args<T> n1a) {
+                                                            N1Args<T> n1a, FaceScratch<T> fs) {
   constexpr int P = R + 1;
   constexpr int P3 = P * P * P;
   constexpr int NL = R == 1 ? 4 : 10;
   __shared__ OpConst<T> c;
   __shared__ T xch[kWarps][P][R][32];
-  __shared__ typename std::conditional<MODE == MODE_N1, N1Const<T>, char>::type n1c;
+  __shared__ typename std::conditional<is_n1_mode(MODE), N1Const<T>, char>::type n1c;
   const int4 task = tasks[blockIdx.x];   // (i-tile, j-tile, k-chunk, macro), heaviest first
   const int macro = task.w;
   const int kc = task.z;
@@ -243,7 +268,7 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
     const int4* src = reinterpret_cast<const int4*>(cst + macro);
     int4* dst = reinterpret_cast<int4*>(&c);
     for (int t = threadIdx.x; t < (int)(sizeof(OpConst<T>) / sizeof(int4)); t += blockDim.x) dst[t] = src[t];
-    if constexpr (MODE == MODE_N1) {
+    if constexpr (is_n1_mode(MODE)) {
       const int4* s1 = reinterpret_cast<const int4*>(n1a.n1 + macro);
       int4* d1 = reinterpret_cast<int4*>(&n1c);
       for (int t = threadIdx.x; t < (int)(sizeof(N1Const<T>) / sizeof(int4)); t += blockDim.x) d1[t] = s1[t];
@@ -315,8 +340,8 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
             if (COEF == HHG_COEFF_FIELD_P1 || COEF == HHG_COEFF_FIELD_P2) kb[s] = in ? __ldg(kf + c.kbase + idx) : T(0);
           }
       // Nedelec coefficients: P1 alpha / beta at the eight cube corners (inside the macro)
-      T ca[MODE == MODE_N1 ? 8 : 1], cb[MODE == MODE_N1 ? 8 : 1];
-      if constexpr (MODE == MODE_N1 && COEF != kCoefStored) {
+      T ca[is_n1_mode(MODE) ? 8 : 1], cb[is_n1_mode(MODE) ? 8 : 1];
+      if constexpr (is_n1_mode(MODE) && COEF != kCoefStored) {
 #pragma unroll
         for (int cn = 0; cn < 8; ++cn) {
           const int vi = ci + (cn & 1), vj = cj + ((cn >> 1) & 1), vk = ck + (cn >> 2);
@@ -331,7 +356,7 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
       int64_t ncubes = 0;
       if constexpr (COEF == kCoefStored) {
         ncubes = dV(n - 1);
-        elem = kf + (int64_t)macro * 6 * (MODE == MODE_N1 ? kN1Sym : (R == 1 ? 1 : 55)) * ncubes +
+        elem = kf + (int64_t)macro * 6 * (is_n1_mode(MODE) ? kN1Sym : (R == 1 ? 1 : 55)) * ncubes +
                packed_index(n - 1, ci, cj, ck);
       }
       // analytic coefficient in FP32: sin / cos of 2 pi x at the cube origin, per coordinate
@@ -351,7 +376,7 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
           ul[a] = (MODE == MODE_APPLY || MODE == MODE_ADJ || MODE == MODE_N1) ? xb[node_slot<R>(o, a)] : T(0);
           yl[a] = T(0);
         }
-        if constexpr (MODE == MODE_N1) {
+        if constexpr (is_n1_mode(MODE)) {
           // Nedelec edge element (Eq. N1): the six edge nodes of the P2 numbering carry the DoFs.
           // A_T = mean(alpha) C_o + sum_v beta_v M_o^v (symmetric, canonical orientation), formed
           // once per micro-tet and applied to the six edge values.
@@ -374,12 +399,17 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
                 A[t] = abar * n1c.C[o][t] + bv[0] * n1c.M[o][0][t] + bv[1] * n1c.M[o][1][t] +
                        bv[2] * n1c.M[o][2][t] + bv[3] * n1c.M[o][3][t];
             }
+            if constexpr (MODE == MODE_N1D) {
 #pragma unroll
-            for (int e = 0; e < 6; ++e) {
-              T s = T(0);
+              for (int e = 0; e < 6; ++e) yl[4 + e] = A[n1_sym(e, e)];
+            } else {
 #pragma unroll
-              for (int f = 0; f < 6; ++f) s += A[e <= f ? n1_sym(e, f) : n1_sym(f, e)] * ul[4 + f];
-              yl[4 + e] = s;
+              for (int e = 0; e < 6; ++e) {
+                T s = T(0);
+#pragma unroll
+                for (int f = 0; f < 6; ++f) s += A[e <= f ? n1_sym(e, f) : n1_sym(f, e)] * ul[4 + f];
+                yl[4 + e] = s;
+              }
             }
           }
         } else if (MODE == MODE_RHS) {
@@ -597,57 +627,129 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
             const int64_t idx = base + packed_index(N, pi, pj, pk);
             T v = acc[cx + P * (cy + P * cz)];
             if (JATOM) {
-              // Dirichlet rows: written by march_dirichlet_kernel (the output is zeroed before)
+              // Dirichlet rows: written by march_finish_kernel
               if (DIR && MODE != MODE_ADJ && on_dirichlet(table, N, pi, pj, pk)) continue;
-              if (cx == 0 || cy == 0 || (cx == R && lane == 31) || (cy == R && warp == kWarps - 1))
-                atomicAdd(out + idx, v);   // an i- or j-face shared with a neighbouring tile
-              else
+              // the tile above the lowest along i (lane 0, point cx = 0) or along j (warp 0, cy = 0)
+              // of a shared face point stores its partial sum into the scratch
+              const bool si = cx == 0 && lane == 0 && ti0 > 0, sj = cy == 0 && warp == 0 && tj0 > 0;
+              if (!si && !sj) {
                 out[idx] = v;
+              } else {
+                int64_t slot;
+                if (si && !sj)
+                  slot = face_tri_sum(32 * R, task.x - 1, N) + face_tri_row(N - pi, pk) + pj;
+                else if (!si)
+                  slot = fs.Si + face_tri_sum(kWarps * R, task.y - 1, N) + face_tri_row(N - pj, pk) + pi;
+                else
+                  slot = fs.Si + fs.Sj + ((int64_t)(task.x - 1) * fs.Tj + (task.y - 1)) * (N + 1) + pk;
+                fs.d[(int64_t)macro * fs.S + slot] = v;
+              }
               continue;
             }
             if (DIR && MODE != MODE_ADJ && on_dirichlet(table, N, pi, pj, pk))
-              v = (MODE == MODE_APPLY || MODE == MODE_N1) ? x[idx] : (MODE == MODE_DIAG ? T(1) : T(0));
+              v = (MODE == MODE_APPLY || MODE == MODE_N1) ? x[idx] : (MODE == MODE_DIAG || MODE == MODE_N1D ? T(1) : T(0));
             out[idx] = v;
           }
     }
   }
 }
 
-// Dirichlet rows after an atomic-j march: y = x (apply, Nedelec), 1 (diagonal); one thread per point
-// of each face triangle (face f, point t), a point on several faces written more than once with the
-// same value.
-template <typename T>
-__global__ void march_dirichlet_kernel(const OpConst<T>* __restrict__ cst, int mode, const T* __restrict__ x,
-                                       T* __restrict__ y) {
-  const OpConst<T>& c = cst[blockIdx.z];
-  const int N = c.N, f = blockIdx.y;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (N + 1) * (N + 2) / 2) return;
-  // (a, b) with a + b <= N: b by the row starts of the triangle, a the position in the row
-  int b = 0, rem = t;
-  {
-    const float bq = 2.0f * N + 3.0f;
-    b = (int)(0.5f * (bq - sqrtf(fmaxf(bq * bq - 8.0f * (float)t, 0.0f))));
-    b = max(0, min(b, N));
-    auto rs = [&](int r) { return (r * (2 * N + 3 - r)) >> 1; };
-    if (b < N && rs(b + 1) <= t) ++b;
-    if (b > 0 && rs(b) > t) --b;
-    rem = t - rs(b);
+// Row and position of entry r of a triangle of rows 0..m, row q holding m - q + 1 entries.
+__device__ __forceinline__ void tri_decode(int m, int64_t r, int& row, int& pos) {
+  const float bq = 2.0f * m + 3.0f;
+  int q = (int)(0.5f * (bq - sqrtf(fmaxf(bq * bq - 8.0f * (float)r, 0.0f))));
+  q = max(0, min(q, m));
+  if (q < m && face_tri_row(m, q + 1) <= r) ++q;
+  if (q > 0 && face_tri_row(m, q) > r) --q;
+  row = q;
+  pos = (int)(r - face_tri_row(m, q));
+}
+
+// Largest t in 1..T with face_tri_sum(F, t - 1, N) <= q (the tile face holding compact slot q).
+__device__ __forceinline__ int face_of_slot(int64_t F, int T, int64_t N, int64_t q) {
+  int lo = 1, hi = T;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (face_tri_sum(F, mid - 1, N) <= q)
+      lo = mid;
+    else
+      hi = mid - 1;
   }
-  const int a = rem;
+  return lo;
+}
+
+// Completes a march on lattices of at least kMarchJAtomicN cubes per edge; blockIdx.y = macro.
+// Blocks x < nfb: every shared tile-face point adds the partial sums that the tiles above the
+// lowest stored in the scratch, in the fixed order ((lowest + i-side) + j-side) + corner, so an
+// apply is bitwise repeatable.  Blocks x >= nfb (dir_rows): the Dirichlet rows, y = x (apply,
+// Nedelec), 1 (diagonal) or 0 (load vector), one thread per point of each macro face triangle;
+// the first part leaves those points alone (skip_dir), so no point is written by both.
+template <typename T>
+__global__ void march_finish_kernel(const OpConst<T>* __restrict__ cst, int R, int mode, bool dir_rows, bool skip_dir,
+                                    const T* __restrict__ x, T* __restrict__ y, FaceScratch<T> fs, int nfb) {
+  const OpConst<T>& c = cst[blockIdx.y];
+  const int N = c.N;
+  const uint32_t table = c.bnd_table;
+  if ((int)blockIdx.x < nfb) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= fs.Si + fs.Sj) return;
+    const int Fi = 32 * R, Fj = kWarps * R;
+    const T* __restrict__ D = fs.d + (int64_t)blockIdx.y * fs.S;
+    int pi, pj, pk;
+    if (q < fs.Si) {
+      const int t = face_of_slot(Fi, fs.Ti, N, q);
+      tri_decode(N - Fi * t, q - face_tri_sum(Fi, t - 1, N), pk, pj);
+      pi = Fi * t;
+    } else {
+      const int64_t q2 = q - fs.Si;
+      const int t2 = face_of_slot(Fj, fs.Tj, N, q2);
+      tri_decode(N - Fj * t2, q2 - face_tri_sum(Fj, t2 - 1, N), pk, pi);
+      pj = Fj * t2;
+      if (pi > 0 && pi % Fi == 0) return;   // on an i-face too: summed by that face's slot
+    }
+    if (skip_dir && on_dirichlet(table, N, pi, pj, pk)) return;
+    const int64_t idx = c.base + packed_index(N, pi, pj, pk);
+    T v = y[idx] + D[q];
+    if (q < fs.Si && pj > 0 && pj % Fj == 0) {
+      const int t = pi / Fi, t2 = pj / Fj;
+      v += D[fs.Si + face_tri_sum(Fj, t2 - 1, N) + face_tri_row(N - pj, pk) + pi];
+      v += D[fs.Si + fs.Sj + ((int64_t)(t - 1) * fs.Tj + (t2 - 1)) * (N + 1) + pk];
+    }
+    y[idx] = v;
+    return;
+  }
+  if (!dir_rows) return;
+  const int nb = (int)((((int64_t)N + 1) * (N + 2) / 2 + blockDim.x - 1) / blockDim.x);
+  const int b = blockIdx.x - nfb, f = b / nb;
+  const int t = (b - f * nb) * blockDim.x + threadIdx.x;
+  if (t >= (N + 1) * (N + 2) / 2) return;
+  int rowb, a;
+  tri_decode(N, t, rowb, a);   // (a, rowb) with a + rowb <= N
   int i, j, k;
   if (f == 0) {
-    i = 0; j = a; k = b;
+    i = 0; j = a; k = rowb;
   } else if (f == 1) {
-    i = a; j = 0; k = b;
+    i = a; j = 0; k = rowb;
   } else if (f == 2) {
-    i = a; j = b; k = 0;
+    i = a; j = rowb; k = 0;
   } else {
-    i = N - a - b; j = a; k = b;
+    i = N - a - rowb; j = a; k = rowb;
   }
-  if (!on_dirichlet(c.bnd_table, N, i, j, k)) return;
+  if (!on_dirichlet(table, N, i, j, k)) return;
   const int64_t idx = c.base + packed_index(N, i, j, k);
-  y[idx] = mode == MODE_DIAG ? T(1) : x[idx];
+  y[idx] = (mode == MODE_DIAG || mode == MODE_N1D) ? T(1) : (mode == MODE_RHS ? T(0) : x[idx]);
+}
+
+template <typename T>
+FaceScratch<T> face_scratch(const hhg_op* op) {
+  FaceScratch<T> f;
+  f.d = (T*)op->d_face;
+  f.S = op->face_S;
+  f.Si = op->face_Si;
+  f.Sj = op->face_Sj;
+  f.Ti = op->face_Ti;
+  f.Tj = op->face_Tj;
+  return f;
 }
 
 template <typename T, int R, int COEF, int MODE, bool AFF = true>
@@ -657,27 +759,31 @@ int launch_march_t(const hhg_op* op, const OpConst<T>* cst, const T* x, const T*
   const unsigned grid = (unsigned)I->n_march_tasks;
   const bool dir = op->bc == HHG_DIRICHLET;
   if (march_jw(op->n) == kMarchWarps) {
-    HHG_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(T) * (size_t)op->npts, s));
+    if (!op->d_face) return fail(HHG_E_CUDA, "march: the operator has no tile-face scratch");
+    const FaceScratch<T> fs = face_scratch<T>(op);
     if (dir)
-      march_kernel<T, R, COEF, MODE, true, AFF, true><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks,
-                                                                                   I->march_kchunk, x, g, kf, out, n1a);
+      march_kernel<T, R, COEF, MODE, true, AFF, true><<<grid, 32 * kWarps, 0, s>>>(
+          cst, I->d_march_tasks, I->march_kchunk, x, g, kf, out, n1a, fs);
     else
-      march_kernel<T, R, COEF, MODE, false, AFF, true><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks,
-                                                                                    I->march_kchunk, x, g, kf, out, n1a);
+      march_kernel<T, R, COEF, MODE, false, AFF, true><<<grid, 32 * kWarps, 0, s>>>(
+          cst, I->d_march_tasks, I->march_kchunk, x, g, kf, out, n1a, fs);
     HHG_CUDA_TRY(cudaGetLastError());
-    if (dir && (MODE == MODE_APPLY || MODE == MODE_N1 || MODE == MODE_DIAG)) {
-      const dim3 fg((unsigned)((((int64_t)op->N + 1) * (op->N + 2) / 2 + 255) / 256), 4, op->mesh->nmacro());
-      march_dirichlet_kernel<T><<<fg, 256, 0, s>>>(cst, MODE, x, out);
+    const bool rows = dir && MODE != MODE_ADJ;
+    const int nfb = (int)((fs.Si + fs.Sj + 255) / 256);
+    const int nb = rows ? 4 * (int)((((int64_t)op->N + 1) * (op->N + 2) / 2 + 255) / 256) : 0;
+    if (nfb + nb > 0) {
+      march_finish_kernel<T><<<dim3((unsigned)(nfb + nb), op->mesh->nmacro()), 256, 0, s>>>(
+          cst, R, MODE, rows, rows, x, out, fs, nfb);
       HHG_CUDA_TRY(cudaGetLastError());
     }
     return HHG_OK;
   }
   if (dir)
     march_kernel<T, R, COEF, MODE, true, AFF><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x, g,
-                                                                            kf, out, n1a);
+                                                                            kf, out, n1a, FaceScratch<T>());
   else
     march_kernel<T, R, COEF, MODE, false, AFF><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x,
-                                                                             g, kf, out, n1a);
+                                                                             g, kf, out, n1a, FaceScratch<T>());
   HHG_CUDA_TRY(cudaGetLastError());
   return HHG_OK;
 }
@@ -712,9 +818,11 @@ int launch_march_t(const hhg_op* op, const OpConst<T>* cst, const T* x, const T*
   X(float, 2, HHG_COEFF_FIELD_P2, hhg::MODE_ADJ, true)
 #define HHG_MARCH_SHARD_6(X)                                                                            \
   X(double, 2, HHG_COEFF_CONST, hhg::MODE_APPLY, true) X(double, 2, hhg::kCoefStored, hhg::MODE_APPLY, true) \
-  X(double, 2, hhg::kCoefStored, hhg::MODE_N1, true) X(double, 2, HHG_COEFF_CONST, hhg::MODE_N1, true)
+  X(double, 2, hhg::kCoefStored, hhg::MODE_N1, true) X(double, 2, HHG_COEFF_CONST, hhg::MODE_N1, true) \
+  X(double, 2, HHG_COEFF_CONST, hhg::MODE_N1D, true)
 #define HHG_MARCH_SHARD_7(X)                                                                            \
   X(float, 2, HHG_COEFF_CONST, hhg::MODE_APPLY, true) X(float, 2, hhg::kCoefStored, hhg::MODE_APPLY, true) \
-  X(float, 2, hhg::kCoefStored, hhg::MODE_N1, true) X(float, 2, HHG_COEFF_CONST, hhg::MODE_N1, true)
+  X(float, 2, hhg::kCoefStored, hhg::MODE_N1, true) X(float, 2, HHG_COEFF_CONST, hhg::MODE_N1, true) \
+  X(float, 2, HHG_COEFF_CONST, hhg::MODE_N1D, true)
 #define HHG_MARCH_INSTANTIATE(T, R, C, M, A) template HHG_MARCH_DECL(T, R, C, M, A);
 #define HHG_MARCH_EXTERN(T, R, C, M, A) extern template HHG_MARCH_DECL(T, R, C, M, A);

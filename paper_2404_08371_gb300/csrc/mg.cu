@@ -97,13 +97,13 @@ static int locate(int R, const double xi[3], double* w) {
   return -1;
 }
 
+static int upload_transfer_tables(int R, TransferTables* T, const std::vector<int>& cls, const std::vector<double>& w64);
+
 static int build_transfer_tables(int R, TransferTables* T) {
-  T->R = R;
   const int W = 2 * R + 1;
-  T->npos = W * W * W;
-  const int nloc = R == 1 ? 4 : 10;
-  std::vector<int> cls(T->npos);
-  std::vector<double> w64(T->npos * 10, 0.0);
+  const int npos = W * W * W;
+  std::vector<int> cls(npos);
+  std::vector<double> w64(npos * 10, 0.0);
   for (int az = 0; az < W; ++az)
     for (int ay = 0; ay < W; ++ay)
       for (int ax = 0; ax < W; ++ax) {
@@ -112,6 +112,96 @@ static int build_transfer_tables(int R, TransferTables* T) {
         cls[t] = locate(R, xi, &w64[10 * t]);
         if (cls[t] < 0) return fail(HHG_E_CUDA, "transfer table: point not located");
       }
+  return upload_transfer_tables(R, T, cls, w64);
+}
+
+// Canonical lattice direction of the edge whose doubled-lattice midpoint has parity (pi, pj, pk): the
+// parity vector with its second nonzero component negated ((1,1,0) -> (1,-1,0), (1,1,1) -> (1,-1,1)).
+static void edge_canonical_dir(int pi, int pj, int pk, int d[3]) {
+  d[0] = pi;
+  d[1] = pj;
+  d[2] = pk;
+  if (pi && pj) d[1] = -1;
+  else if ((pi || pj) && pk) d[2] = -1;
+}
+
+// Nedelec prolongation (Section 8; the tangential integrals of the coarse Whitney field along the
+// fine edges).  Fine edge midpoints in the doubled fine lattice sit at positions a in [0, 4]^3 of a
+// coarse cube; a position with an odd coordinate is an edge of canonical direction d, the fine edge
+// vector is d/2 and its midpoint a/4 in coarse cube coordinates.  The coarse Whitney functions
+// phi_AB = lambda_A grad lambda_B - lambda_B grad lambda_A of the containing coarse micro-tet are
+// linear, so the tangential integral is phi_AB(a/4) . d/2; the coarse DoF of edge (A, B) is the
+// integral along its own canonical direction, so the weight carries the sign of V_B - V_A against
+// it.  Index space is enough: tangential integrals are invariant under the affine map of a macro.
+// Vertex positions (all coordinates even) carry no DoF and get zero weights.
+static int build_n1_transfer_tables(TransferTables* T) {
+  const int R = 2, W = 5, npos = W * W * W;
+  std::vector<int> cls(npos, 0);
+  std::vector<double> w64(npos * 10, 0.0);
+  for (int az = 0; az < W; ++az)
+    for (int ay = 0; ay < W; ++ay)
+      for (int ax = 0; ax < W; ++ax) {
+        const int t = ax + W * (ay + W * az);
+        if (!((ax | ay | az) & 1)) continue;
+        const double xi[3] = {ax / 4.0, ay / 4.0, az / 4.0};
+        double wp2[10];
+        const int o = locate(R, xi, wp2);
+        if (o < 0) return fail(HHG_E_CUDA, "edge transfer table: point not located");
+        cls[t] = o;
+        // barycentric coordinates and index-space gradients of the coarse micro-tet of class o
+        double D[3][3];
+        for (int r = 0; r < 3; ++r)
+          for (int b = 0; b < 3; ++b) D[r][b] = kClassOffsets[o][b + 1][r] - kClassOffsets[o][0][r];
+        const double det = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
+                           D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                           D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+        double Di[3][3];   // inverse: row b-1 is grad lambda_b
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c) {
+            const int r1 = (c + 1) % 3, r2 = (c + 2) % 3, c1 = (r + 1) % 3, c2 = (r + 2) % 3;
+            Di[r][c] = (D[r1][c1] * D[r2][c2] - D[r1][c2] * D[r2][c1]) / det;
+          }
+        double g[4][3], lam[4];
+        for (int d = 0; d < 3; ++d) {
+          g[1][d] = Di[0][d];
+          g[2][d] = Di[1][d];
+          g[3][d] = Di[2][d];
+          g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
+        }
+        double l3[3];
+        for (int b = 0; b < 3; ++b) {
+          l3[b] = 0.0;
+          for (int d = 0; d < 3; ++d) l3[b] += Di[b][d] * (xi[d] - kClassOffsets[o][0][d]);
+        }
+        lam[1] = l3[0];
+        lam[2] = l3[1];
+        lam[3] = l3[2];
+        lam[0] = 1.0 - l3[0] - l3[1] - l3[2];
+        int dv[3];
+        edge_canonical_dir(ax & 1, ay & 1, az & 1, dv);
+        const double tv[3] = {dv[0] / 2.0, dv[1] / 2.0, dv[2] / 2.0};
+        for (int e = 0; e < 6; ++e) {
+          const int A = kP2Edges[e][0], B = kP2Edges[e][1];
+          double val = 0.0;
+          for (int d = 0; d < 3; ++d) val += (lam[A] * g[B][d] - lam[B] * g[A][d]) * tv[d];
+          int vec[3], dc[3];
+          for (int d = 0; d < 3; ++d) vec[d] = kClassOffsets[o][B][d] - kClassOffsets[o][A][d];
+          edge_canonical_dir((kClassOffsets[o][A][0] + kClassOffsets[o][B][0]) & 1,
+                             (kClassOffsets[o][A][1] + kClassOffsets[o][B][1]) & 1,
+                             (kClassOffsets[o][A][2] + kClassOffsets[o][B][2]) & 1, dc);
+          const double sg = (vec[0] == dc[0] && vec[1] == dc[1] && vec[2] == dc[2]) ? 1.0 : -1.0;
+          w64[10 * t + 4 + e] = sg * val;
+        }
+      }
+  return upload_transfer_tables(R, T, cls, w64);
+}
+
+// Restriction stencils (columns of P per coarse node type on an unbounded lattice) and upload.
+static int upload_transfer_tables(int R, TransferTables* T, const std::vector<int>& cls, const std::vector<double>& w64) {
+  T->R = R;
+  const int W = 2 * R + 1;
+  T->npos = W * W * W;
+  const int nloc = R == 1 ? 4 : 10;
   // restriction stencils: column C of P for a coarse node of each type, on an unbounded lattice
   const int ntypes = R == 1 ? 1 : 8;
   std::vector<int> st_ptr{0}, st_off;
@@ -325,6 +415,14 @@ __global__ void invert_kernel(int64_t n, T* __restrict__ d) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) d[t] = T(1) / d[t];
 }
 
+// 1/d, and 0 where d is 0 (the vertex points of a Nedelec vector, which carry no DoF)
+template <typename T>
+__global__ void invert_or_zero_kernel(int64_t n, T* __restrict__ d) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride)
+    d[t] = d[t] != T(0) ? T(1) / d[t] : T(0);
+}
+
 // Counter-based start vector of the power iteration: splitmix64 of (seed, position), uniform on [-1, 1),
 // zero on Dirichlet points.
 __global__ void start_vector_kernel(LevelArgs L, const MacroGeom* __restrict__ mg, uint64_t seed, double* __restrict__ v) {
@@ -392,9 +490,10 @@ struct OpWork {
 // ---------------------------------------------------------------------------
 // Transfer entry points
 // ---------------------------------------------------------------------------
+// R = 1, 2: the scalar P1 / P2 tables; R = 3: the Nedelec edge tables (on the P2 position grid).
 static TransferTables* transfer_tables(int R, int* status) {
   // per device, built on first use (device index up to 64)
-  static TransferTables* cache[64][3] = {};
+  static TransferTables* cache[64][4] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) {
@@ -403,7 +502,7 @@ static TransferTables* transfer_tables(int R, int* status) {
   }
   if (!cache[dev][R]) {
     TransferTables* T = new TransferTables();
-    int st = build_transfer_tables(R, T);
+    int st = R == 3 ? build_n1_transfer_tables(T) : build_transfer_tables(R, T);
     if (st != HHG_OK) {
       delete T;
       *status = st;
@@ -474,6 +573,101 @@ static int do_restrict(hhg_mesh* mesh, int lf, int degree, const T* rf, T* rc, c
   return launch_interface_sum<T>(Ic, rc, 1, true, s);
 }
 
+// Nedelec transfers: the same kernels on the doubled lattice with the edge tables; the copies of a
+// shared edge carry their macro's orientation, so restriction sums them with signs, and the
+// prolongation of a consistent coarse vector is consistent up to those signs.
+template <typename T>
+static int do_prolongate_n1(hhg_mesh* mesh, int lf, const T* xc, T* xf, cudaStream_t s) {
+  const Interface *If = nullptr, *Ic = nullptr;
+  HHG_TRY(mesh->interface(lf, 2, &If));
+  HHG_TRY(mesh->interface(lf - 1, 2, &Ic));
+  int st = 0;
+  TransferTables* TT = transfer_tables(3, &st);
+  if (!TT) return st;
+  LevelArgs F = level_args(If, 2 << lf), C = level_args(Ic, 2 << (lf - 1));
+  prolongate_kernel<T, 2><<<dim3((unsigned)If->ncta, mesh->nmacro()), 256, 0, s>>>(F, C, TT->d_pos_off, pos_w<T>(TT),
+                                                                                    xc, xf);
+  HHG_CUDA_TRY(cudaGetLastError());
+  return HHG_OK;
+}
+
+template <typename T>
+static int do_restrict_n1(hhg_mesh* mesh, int lf, const T* rf, T* rc, cudaStream_t s) {
+  const Interface *If = nullptr, *Ic = nullptr;
+  HHG_TRY(mesh->interface(lf, 2, &If));
+  HHG_TRY(mesh->interface(lf - 1, 2, &Ic));
+  int st = 0;
+  TransferTables* TT = transfer_tables(3, &st);
+  if (!TT) return st;
+  LevelArgs F = level_args(If, 2 << lf), C = level_args(Ic, 2 << (lf - 1));
+  restrict_kernel<T, 2><<<dim3((unsigned)Ic->ncta, mesh->nmacro()), 256, 0, s>>>(
+      F, C, mesh->d_macros, TT->d_st_ptr, TT->d_st_off, st_w<T>(TT), rf, rc);
+  HHG_CUDA_TRY(cudaGetLastError());
+  return launch_interface_sum_signed<T>(Ic, rc, true, s);
+}
+
+// Discrete gradient G: P1 vertex values p (level l) -> edge values of level l, the tangential
+// integral of grad p along the canonical direction d of the edge, p(m + d) - p(m - d) in doubled
+// coordinates m; vertex points of the doubled lattice get 0.
+template <typename T>
+__global__ void __launch_bounds__(256) n1_gradient_kernel(LevelArgs E, LevelArgs P1, const T* __restrict__ p,
+                                                           T* __restrict__ out) {
+  int i, j, k, q;
+  if (!plane_point(E.N, E.cta_plane, E.cta_start, E.pstart, i, j, k, q)) return;
+  const int m = blockIdx.y;
+  T v = T(0);
+  if ((i | j | k) & 1) {
+    int d[3];
+    const int pi = i & 1, pj = j & 1, pk = k & 1;
+    d[0] = pi;
+    d[1] = pj;
+    d[2] = pk;
+    if (pi && pj) d[1] = -1;
+    else if ((pi || pj) && pk) d[2] = -1;
+    const int ai = (i - d[0]) >> 1, aj = (j - d[1]) >> 1, ak = (k - d[2]) >> 1;
+    const int bi = (i + d[0]) >> 1, bj = (j + d[1]) >> 1, bk = (k + d[2]) >> 1;
+    const T* __restrict__ pm = p + (int64_t)m * P1.V;
+    v = __ldg(pm + __ldg(P1.pstart + bk) + rowst32(P1.N - bk, bj) + bi) -
+        __ldg(pm + __ldg(P1.pstart + ak) + rowst32(P1.N - ak, aj) + ai);
+  }
+  out[(int64_t)m * E.V + q] = v;
+}
+
+// Its transpose G^T: edge values r (level l) -> P1 vertex values, sum over the 14 incident edges of
+// r_e (the edge ends at the vertex) or -r_e (starts there), over the edge copies this macro owns;
+// Dirichlet vertices get 0.  The caller adds the macro copies of shared vertices.
+template <typename T>
+__global__ void __launch_bounds__(256) n1_gradient_t_kernel(LevelArgs P1, LevelArgs E, const MacroGeom* __restrict__ mg,
+                                                             const T* __restrict__ r, T* __restrict__ out) {
+  int i, j, k, q;
+  if (!plane_point(P1.N, P1.cta_plane, P1.cta_start, P1.pstart, i, j, k, q)) return;
+  const int m = blockIdx.y;
+  const uint32_t bnd = mg[m].bnd_table, own = mg[m].own_table;
+  T* o = out + (int64_t)m * P1.V + q;
+  if (on_dirichlet(bnd, P1.N, i, j, k)) {
+    *o = T(0);
+    return;
+  }
+  const T* __restrict__ rm = r + (int64_t)m * E.V;
+  const int NE = E.N;
+  T acc = T(0);
+  constexpr int kDir[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, -1, 0}, {1, 0, -1}, {0, 1, -1}, {1, -1, 1}};
+#pragma unroll
+  for (int t = 0; t < 7; ++t) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      // side 0: the edge starting at the vertex (midpoint 2v + d); side 1: ending there (2v - d)
+      const int sgn = side == 0 ? 1 : -1;
+      const int ei = 2 * i + sgn * kDir[t][0], ej = 2 * j + sgn * kDir[t][1], ek = 2 * k + sgn * kDir[t][2];
+      if (ei < 0 || ej < 0 || ek < 0 || ei + ej + ek > NE) continue;
+      if (!((own >> zero_mask(NE, ei, ej, ek)) & 1u)) continue;   // a copy owned by another macro
+      const T v = __ldg(rm + __ldg(E.pstart + ek) + rowst32(NE - ek, ej) + ei);
+      acc += side == 0 ? -v : v;
+    }
+  }
+  *o = acc;
+}
+
 static int check_transfer_args(const hhg_mesh_t* mesh, int lf, int degree, const void* a, const void* b, int dtype) {
   if (!mesh || !a || !b) return fail(HHG_E_ARG, "transfer: null pointer");
   if (lf < 1 || lf > mesh->level) return fail(HHG_E_ARG, "transfer: fine level %d outside 1..%d", lf, mesh->level);
@@ -500,6 +694,71 @@ extern "C" int hhg_restrict(const hhg_mesh_t* mesh, int level_fine, int degree, 
   if (dtype == HHG_F64)
     return do_restrict<double>(m, level_fine, degree, (const double*)rf, (double*)rc, (cudaStream_t)stream);
   return do_restrict<float>(m, level_fine, degree, (const float*)rf, (float*)rc, (cudaStream_t)stream);
+}
+
+template <typename T>
+static int do_gradient(hhg_mesh* mesh, int level, const T* p, T* e, bool transpose, cudaStream_t s) {
+  const Interface *I1 = nullptr, *I2 = nullptr;
+  HHG_TRY(mesh->interface(level, 1, &I1));
+  HHG_TRY(mesh->interface(level, 2, &I2));
+  const LevelArgs P1 = level_args(I1, 1 << level), E = level_args(I2, 2 << level);
+  if (!transpose) {
+    n1_gradient_kernel<T><<<dim3((unsigned)I2->ncta, mesh->nmacro()), 256, 0, s>>>(E, P1, p, e);
+    HHG_CUDA_TRY(cudaGetLastError());
+    return HHG_OK;
+  }
+  n1_gradient_t_kernel<T><<<dim3((unsigned)I1->ncta, mesh->nmacro()), 256, 0, s>>>(P1, E, mesh->d_macros, e,
+                                                                                   const_cast<T*>(p));
+  HHG_CUDA_TRY(cudaGetLastError());
+  return launch_interface_sum<T>(I1, const_cast<T*>(p), 1, true, s);
+}
+
+extern "C" int hhg_prolongate_edges(const hhg_mesh_t* mesh, int level_fine, const void* xc, void* xf, int dtype,
+                                    void* stream) {
+  clear_error();
+  HHG_TRY(check_transfer_args(mesh, level_fine, 2, xc, xf, dtype));
+  hhg_mesh* m = const_cast<hhg_mesh*>(mesh);
+  const Interface* If = nullptr;
+  HHG_TRY(m->interface(level_fine, 2, &If));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == HHG_F64) {
+    HHG_TRY(do_prolongate_n1<double>(m, level_fine, (const double*)xc, (double*)xf, s));
+    return launch_make_consistent_signed<double>(If, (double*)xf, s);
+  }
+  HHG_TRY(do_prolongate_n1<float>(m, level_fine, (const float*)xc, (float*)xf, s));
+  return launch_make_consistent_signed<float>(If, (float*)xf, s);
+}
+
+extern "C" int hhg_restrict_edges(const hhg_mesh_t* mesh, int level_fine, const void* rf, void* rc, int dtype,
+                                  void* stream) {
+  clear_error();
+  HHG_TRY(check_transfer_args(mesh, level_fine, 2, rf, rc, dtype));
+  hhg_mesh* m = const_cast<hhg_mesh*>(mesh);
+  if (dtype == HHG_F64)
+    return do_restrict_n1<double>(m, level_fine, (const double*)rf, (double*)rc, (cudaStream_t)stream);
+  return do_restrict_n1<float>(m, level_fine, (const float*)rf, (float*)rc, (cudaStream_t)stream);
+}
+
+extern "C" int hhg_gradient(const hhg_mesh_t* mesh, int level, const void* p, void* e, int dtype, void* stream) {
+  clear_error();
+  if (!mesh || !p || !e) return fail(HHG_E_ARG, "gradient: null pointer");
+  if (level < 0 || level > mesh->level) return fail(HHG_E_ARG, "gradient: level %d outside 0..%d", level, mesh->level);
+  if (dtype != HHG_F32 && dtype != HHG_F64) return fail(HHG_E_ARG, "gradient: bad dtype");
+  hhg_mesh* m = const_cast<hhg_mesh*>(mesh);
+  if (dtype == HHG_F64) return do_gradient<double>(m, level, (const double*)p, (double*)e, false, (cudaStream_t)stream);
+  return do_gradient<float>(m, level, (const float*)p, (float*)e, false, (cudaStream_t)stream);
+}
+
+extern "C" int hhg_gradient_transpose(const hhg_mesh_t* mesh, int level, const void* e, void* p, int dtype,
+                                      void* stream) {
+  clear_error();
+  if (!mesh || !p || !e) return fail(HHG_E_ARG, "gradient_transpose: null pointer");
+  if (level < 0 || level > mesh->level)
+    return fail(HHG_E_ARG, "gradient_transpose: level %d outside 0..%d", level, mesh->level);
+  if (dtype != HHG_F32 && dtype != HHG_F64) return fail(HHG_E_ARG, "gradient_transpose: bad dtype");
+  hhg_mesh* m = const_cast<hhg_mesh*>(mesh);
+  if (dtype == HHG_F64) return do_gradient<double>(m, level, (double*)p, (double*)e, true, (cudaStream_t)stream);
+  return do_gradient<float>(m, level, (float*)p, (float*)e, true, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -583,6 +842,14 @@ static int noalloc_scratch(void** out) {
   }
   *out = addr[dev];
   return HHG_OK;
+}
+
+// Looks the scratch array up on the current device ahead of the first hhg_cheb_smooth_noalloc call:
+// called by operator creation, which allocates anyway, so that the lookup (which can load the
+// library's device image) never happens inside the allocation-free entry point.
+int hhg::noalloc_prepare() {
+  void* p = nullptr;
+  return noalloc_scratch(&p);
 }
 
 template <typename T>
@@ -698,9 +965,17 @@ struct MGLevel {
   double lam = 1.0;
   double *dinv64 = nullptr, *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *y64 = nullptr, *d64 = nullptr;
   float *dinv32 = nullptr, *x32 = nullptr, *b32 = nullptr, *r32 = nullptr, *y32 = nullptr, *d32 = nullptr;
+  // Nedelec hierarchies: the nodal operator G^T A G of the hybrid smoother (the P1 diffusion operator
+  // with coefficient beta, Dirichlet) and its vectors over the level's P1 lattice
+  hhg_op* pop = nullptr;
+  int64_t np = 0;
+  double lam_p = 1.0;
+  double *pdinv64 = nullptr, *px64 = nullptr, *pb64 = nullptr, *py64 = nullptr, *pd64 = nullptr;
+  float *pdinv32 = nullptr, *px32 = nullptr, *pb32 = nullptr, *py32 = nullptr, *pd32 = nullptr;
 };
 
 struct MGHierarchy {
+  bool n1 = false;           // Nedelec (curl-curl + mass) hierarchy with Hiptmair's hybrid smoother
   int L = 0, coarse = 0;
   std::vector<MGLevel> lv;
   int n0 = 0;
@@ -712,9 +987,12 @@ struct MGHierarchy {
   ~MGHierarchy() {
     for (auto& l : lv) {
       for (void* p : {(void*)l.dinv64, (void*)l.x64, (void*)l.b64, (void*)l.r64, (void*)l.y64, (void*)l.d64,
-                      (void*)l.dinv32, (void*)l.x32, (void*)l.b32, (void*)l.r32, (void*)l.y32, (void*)l.d32})
+                      (void*)l.dinv32, (void*)l.x32, (void*)l.b32, (void*)l.r32, (void*)l.y32, (void*)l.d32,
+                      (void*)l.pdinv64, (void*)l.px64, (void*)l.pb64, (void*)l.py64, (void*)l.pd64,
+                      (void*)l.pdinv32, (void*)l.px32, (void*)l.pb32, (void*)l.py32, (void*)l.pd32})
         cudaFree(p);
       if (l.owned) delete l.op;
+      delete l.pop;
     }
     cudaFree(Ainv);
     cudaFree(pos);
@@ -751,13 +1029,79 @@ struct Buf<float> {
   static float* d(MGLevel& l) { return l.d32; }
   static float* dinv(MGLevel& l) { return l.dinv32; }
 };
+// the nodal vectors of a Nedelec level
+template <typename T>
+struct PBuf;
+template <>
+struct PBuf<double> {
+  static double* x(MGLevel& l) { return l.px64; }
+  static double* b(MGLevel& l) { return l.pb64; }
+  static double* y(MGLevel& l) { return l.py64; }
+  static double* d(MGLevel& l) { return l.pd64; }
+  static double* dinv(MGLevel& l) { return l.pdinv64; }
+};
+template <>
+struct PBuf<float> {
+  static float* x(MGLevel& l) { return l.px32; }
+  static float* b(MGLevel& l) { return l.pb32; }
+  static float* y(MGLevel& l) { return l.py32; }
+  static float* d(MGLevel& l) { return l.pd32; }
+  static float* dinv(MGLevel& l) { return l.pdinv32; }
+};
+
+// Transfers of the hierarchy's space.
+template <typename T>
+static int mg_restrict(MGHierarchy* H, int l, const T* rf, T* rc, cudaStream_t s) {
+  hhg_op* op = H->lv[l].op;
+  return H->n1 ? do_restrict_n1<T>(op->mesh, l, rf, rc, s) : do_restrict<T>(op->mesh, l, op->degree, rf, rc, s);
+}
+template <typename T>
+static int mg_prolongate(MGHierarchy* H, int l, const T* xc, T* xf, cudaStream_t s) {
+  hhg_op* op = H->lv[l].op;
+  if (!H->n1) return do_prolongate<T>(op->mesh, l, op->degree, xc, xf, s);
+  HHG_TRY(do_prolongate_n1<T>(op->mesh, l, xc, xf, s));
+  return launch_make_consistent_signed<T>(op->itf, xf, s);
+}
+
+// Hiptmair's hybrid smoothing step on a Nedelec level (Section 8): a Chebyshev step on the edges,
+// then one on the gradients of the interior vertices, r_p = G^T (b - A x), p = Chebyshev(A_p, r_p,
+// 0) with A_p = G^T A G (the P1 diffusion operator with coefficient beta), and x += G p.
+template <typename T>
+static int hybrid_smooth(MGLevel& L, const T* b, T* x, const hhg_mg_opts_t* o, cudaStream_t s) {
+  const int dt = sizeof(T) == 8 ? HHG_F64 : HHG_F32;
+  HHG_TRY(cheb_smooth_t<T>(L.op, b, x, Buf<T>::dinv(L), L.lam, o->cheb_lo, o->cheb_hi, o->cheb_order, Buf<T>::y(L),
+                           Buf<T>::d(L), s));
+  HHG_TRY(hhg_op_apply(L.op, x, Buf<T>::y(L), dt, 1, s));
+  residual_kernel<T><<<nblocks<T>(L.n), 256, 0, s>>>(L.n, b, Buf<T>::y(L), Buf<T>::r(L));
+  const Interface* I1 = L.pop->itf;
+  const LevelArgs P1 = level_args(I1, L.pop->N), E = level_args(L.op->itf, L.op->N);
+  const int nm = L.op->mesh->nmacro();
+  n1_gradient_t_kernel<T><<<dim3((unsigned)I1->ncta, nm), 256, 0, s>>>(P1, E, L.op->mesh->d_macros, Buf<T>::r(L),
+                                                                       PBuf<T>::b(L));
+  HHG_CUDA_TRY(cudaGetLastError());
+  HHG_TRY(launch_interface_sum<T>(I1, PBuf<T>::b(L), 1, true, s));
+  HHG_CUDA_TRY(cudaMemsetAsync(PBuf<T>::x(L), 0, sizeof(T) * L.np, s));
+  HHG_TRY(cheb_smooth_t<T>(L.pop, PBuf<T>::b(L), PBuf<T>::x(L), PBuf<T>::dinv(L), L.lam_p, o->cheb_lo, o->cheb_hi,
+                           o->cheb_order, PBuf<T>::y(L), PBuf<T>::d(L), s));
+  n1_gradient_kernel<T><<<dim3((unsigned)L.op->itf->ncta, nm), 256, 0, s>>>(E, P1, PBuf<T>::x(L), Buf<T>::y(L));
+  axpy_kernel<T, T><<<nblocks<T>(L.n), 256, 0, s>>>(L.n, x, Buf<T>::y(L), T(1));
+  HHG_CUDA_TRY(cudaGetLastError());
+  return HHG_OK;
+}
+
+template <typename T>
+static int mg_smooth(MGHierarchy* H, MGLevel& L, const T* b, T* x, const hhg_mg_opts_t* o, cudaStream_t s) {
+  if (H->n1) return hybrid_smooth<T>(L, b, x, o, s);
+  return cheb_smooth_t<T>(L.op, b, x, Buf<T>::dinv(L), L.lam, o->cheb_lo, o->cheb_hi, o->cheb_order, Buf<T>::y(L),
+                          Buf<T>::d(L), s);
+}
 
 template <typename T>
 static int coarse_solve(MGHierarchy* H, const T* b, T* x, cudaStream_t s) {
   MGLevel& l = H->lv[H->coarse];
   coarse_solve_kernel<T><<<1, 256, 0, s>>>(H->n0, H->Ainv, H->pos, b, x, l.n);
   HHG_CUDA_TRY(cudaGetLastError());
-  return launch_make_consistent<T>(l.op->itf, x, 1, s);
+  return H->n1 ? launch_make_consistent_signed<T>(l.op->itf, x, s) : launch_make_consistent<T>(l.op->itf, x, 1, s);
 }
 
 template <typename T>
@@ -766,19 +1110,15 @@ static int vcycle(MGHierarchy* H, int l, const T* b, T* x, const hhg_mg_opts_t* 
   MGLevel& L = H->lv[l];
   MGLevel& C = H->lv[l - 1];
   const int dt = sizeof(T) == 8 ? HHG_F64 : HHG_F32;
-  for (int it = 0; it < o->nu1; ++it)
-    HHG_TRY(cheb_smooth_t<T>(L.op, b, x, Buf<T>::dinv(L), L.lam, o->cheb_lo, o->cheb_hi, o->cheb_order, Buf<T>::y(L),
-                             Buf<T>::d(L), s));
+  for (int it = 0; it < o->nu1; ++it) HHG_TRY(mg_smooth<T>(H, L, b, x, o, s));
   HHG_TRY(hhg_op_apply(L.op, x, Buf<T>::y(L), dt, 1, s));
   residual_kernel<T><<<nblocks<T>(L.n), 256, 0, s>>>(L.n, b, Buf<T>::y(L), Buf<T>::r(L));
-  HHG_TRY(do_restrict<T>(L.op->mesh, l, L.op->degree, Buf<T>::r(L), Buf<T>::b(C), s));
+  HHG_TRY(mg_restrict<T>(H, l, Buf<T>::r(L), Buf<T>::b(C), s));
   HHG_CUDA_TRY(cudaMemsetAsync(Buf<T>::x(C), 0, sizeof(T) * C.n, s));
   HHG_TRY(vcycle<T>(H, l - 1, Buf<T>::b(C), Buf<T>::x(C), o, s));
-  HHG_TRY(do_prolongate<T>(L.op->mesh, l, L.op->degree, Buf<T>::x(C), Buf<T>::y(L), s));
+  HHG_TRY(mg_prolongate<T>(H, l, Buf<T>::x(C), Buf<T>::y(L), s));
   axpy_kernel<T, T><<<nblocks<T>(L.n), 256, 0, s>>>(L.n, x, Buf<T>::y(L), T(1));
-  for (int it = 0; it < o->nu2; ++it)
-    HHG_TRY(cheb_smooth_t<T>(L.op, b, x, Buf<T>::dinv(L), L.lam, o->cheb_lo, o->cheb_hi, o->cheb_order, Buf<T>::y(L),
-                             Buf<T>::d(L), s));
+  for (int it = 0; it < o->nu2; ++it) HHG_TRY(mg_smooth<T>(H, L, b, x, o, s));
   HHG_CUDA_TRY(cudaGetLastError());
   return HHG_OK;
 }
@@ -789,6 +1129,7 @@ static int setup_mg(hhg_op* op, const hhg_mg_opts_t* o, cudaStream_t s) {
   H->L = op->level;
   H->coarse = o->coarse_level;
   if (H->coarse < 0 || H->coarse > H->L) return fail(HHG_E_ARG, "mg: coarse level %d outside 0..%d", H->coarse, H->L);
+  H->n1 = op->kind == HHG_CURLCURL;
   H->lv.resize(H->L + 1);
   for (int l = H->coarse; l <= H->L; ++l) {
     MGLevel& lv = H->lv[l];
@@ -796,7 +1137,10 @@ static int setup_mg(hhg_op* op, const hhg_mg_opts_t* o, cudaStream_t s) {
       lv.op = op;
     } else {
       hhg_op_t* c = nullptr;
-      HHG_TRY(hhg_op_create(op->mesh, l, op->kind, op->degree, &op->coeff, op->bc, op->quad_degree, &c));
+      if (H->n1)
+        HHG_TRY(hhg_op_create_curlcurl(op->mesh, l, &op->coeff, &op->coeff2, op->bc, &c));
+      else
+        HHG_TRY(hhg_op_create(op->mesh, l, op->kind, op->degree, &op->coeff, op->bc, op->quad_degree, &c));
       lv.op = c;
       lv.owned = true;
     }
@@ -806,7 +1150,10 @@ static int setup_mg(hhg_op* op, const hhg_mg_opts_t* o, cudaStream_t s) {
     for (float** p : {&lv.dinv32, &lv.x32, &lv.b32, &lv.r32, &lv.y32, &lv.d32})
       HHG_CUDA_TRY(cudaMalloc(p, sizeof(float) * lv.n));
     HHG_TRY(hhg_op_diagonal(lv.op, lv.dinv64, HHG_F64, s));
-    invert_kernel<double><<<nblocks<double>(lv.n), 256, 0, s>>>(lv.n, lv.dinv64);
+    if (H->n1)
+      invert_or_zero_kernel<double><<<nblocks<double>(lv.n), 256, 0, s>>>(lv.n, lv.dinv64);
+    else
+      invert_kernel<double><<<nblocks<double>(lv.n), 256, 0, s>>>(lv.n, lv.dinv64);
     convert_kernel<float, double><<<nblocks<float>(lv.n), 256, 0, s>>>(lv.n, lv.dinv64, lv.dinv32);
     HHG_CUDA_TRY(cudaGetLastError());
     if (l > H->coarse) {
@@ -815,8 +1162,32 @@ static int setup_mg(hhg_op* op, const hhg_mg_opts_t* o, cudaStream_t s) {
       start_vector_kernel<<<dim3((unsigned)lv.op->itf->ncta, op->mesh->nmacro()), 256, 0, s>>>(LA, op->mesh->d_macros,
                                                                                              12345u, lv.x64);
       HHG_CUDA_TRY(cudaGetLastError());
-      HHG_TRY(launch_make_consistent<double>(lv.op->itf, lv.x64, 1, s));
+      if (H->n1)
+        HHG_TRY(launch_make_consistent_signed<double>(lv.op->itf, lv.x64, s));
+      else
+        HHG_TRY(launch_make_consistent<double>(lv.op->itf, lv.x64, 1, s));
       HHG_TRY(power_t<double>(lv.op, lv.dinv64, lv.x64, o->power_iters, &lv.lam, lv.y64, s));
+    }
+    if (H->n1 && l > H->coarse) {
+      // the nodal part of the hybrid smoother: G^T A G over the level's P1 lattice is the P1
+      // diffusion operator with coefficient beta (Dirichlet: interior vertices only)
+      hhg_op_t* p = nullptr;
+      HHG_TRY(hhg_op_create(op->mesh, l, HHG_DIFFUSION, 1, &op->coeff2, HHG_DIRICHLET, 2, &p));
+      lv.pop = p;
+      lv.np = p->npts;
+      for (double** q : {&lv.pdinv64, &lv.px64, &lv.pb64, &lv.py64, &lv.pd64})
+        HHG_CUDA_TRY(cudaMalloc(q, sizeof(double) * lv.np));
+      for (float** q : {&lv.pdinv32, &lv.px32, &lv.pb32, &lv.py32, &lv.pd32})
+        HHG_CUDA_TRY(cudaMalloc(q, sizeof(float) * lv.np));
+      HHG_TRY(hhg_op_diagonal(p, lv.pdinv64, HHG_F64, s));
+      invert_kernel<double><<<nblocks<double>(lv.np), 256, 0, s>>>(lv.np, lv.pdinv64);
+      convert_kernel<float, double><<<nblocks<float>(lv.np), 256, 0, s>>>(lv.np, lv.pdinv64, lv.pdinv32);
+      LevelArgs LP = level_args(p->itf, p->N);
+      start_vector_kernel<<<dim3((unsigned)p->itf->ncta, op->mesh->nmacro()), 256, 0, s>>>(LP, op->mesh->d_macros,
+                                                                                         54321u, lv.px64);
+      HHG_CUDA_TRY(cudaGetLastError());
+      HHG_TRY(launch_make_consistent<double>(p->itf, lv.px64, 1, s));
+      HHG_TRY(power_t<double>(p, lv.pdinv64, lv.px64, o->power_iters, &lv.lam_p, lv.py64, s));
     }
   }
   HHG_CUDA_TRY(cudaMalloc(&H->xf64, sizeof(double) * op->npts));
@@ -840,7 +1211,8 @@ static int setup_mg(hhg_op* op, const hhg_mg_opts_t* o, cudaStream_t s) {
             const int z = (N - i - j - k == 0) | ((i == 0) << 1) | ((j == 0) << 2) | ((k == 0) << 3);
             const bool bnd = op->bc == HHG_DIRICHLET && ((tb >> z) & 1);
             const int64_t e = (int64_t)m * V + p;
-            if (!bnd && !nonowner[e]) pos.push_back(e);
+            const bool dof = !H->n1 || ((i | j | k) & 1);   // Nedelec: edge midpoints only
+            if (dof && !bnd && !nonowner[e]) pos.push_back(e);
           }
     }
     H->n0 = (int)pos.size();
@@ -852,7 +1224,10 @@ static int setup_mg(hhg_op* op, const hhg_mg_opts_t* o, cudaStream_t s) {
       std::fill(e.begin(), e.end(), 0.0);
       e[pos[r]] = 1.0;
       HHG_CUDA_TRY(cudaMemcpyAsync(c.x64, e.data(), sizeof(double) * c.n, cudaMemcpyHostToDevice, s));
-      HHG_TRY(launch_make_consistent<double>(I, c.x64, 1, s));
+      if (H->n1)
+        HHG_TRY(launch_make_consistent_signed<double>(I, c.x64, s));
+      else
+        HHG_TRY(launch_make_consistent<double>(I, c.x64, 1, s));
       HHG_TRY(hhg_op_apply(c.op, c.x64, c.y64, HHG_F64, 1, s));
       HHG_CUDA_TRY(cudaMemcpyAsync(col.data(), c.y64, sizeof(double) * c.n, cudaMemcpyDeviceToHost, s));
       HHG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -905,10 +1280,10 @@ static int fmg_t(MGHierarchy* H, const double* b, const hhg_mg_opts_t* o, cudaSt
   else
     convert_kernel<float, double><<<nblocks<float>(F.n), 256, 0, s>>>(F.n, b, F.b32);
   for (int l = H->L; l > H->coarse; --l)
-    HHG_TRY(do_restrict<T>(H->lv[l].op->mesh, l, H->lv[l].op->degree, Buf<T>::b(H->lv[l]), Buf<T>::b(H->lv[l - 1]), s));
+    HHG_TRY(mg_restrict<T>(H, l, Buf<T>::b(H->lv[l]), Buf<T>::b(H->lv[l - 1]), s));
   HHG_TRY(coarse_solve<T>(H, Buf<T>::b(H->lv[H->coarse]), Buf<T>::x(H->lv[H->coarse]), s));
   for (int l = H->coarse + 1; l <= H->L; ++l) {
-    HHG_TRY(do_prolongate<T>(H->lv[l].op->mesh, l, H->lv[l].op->degree, Buf<T>::x(H->lv[l - 1]), Buf<T>::x(H->lv[l]), s));
+    HHG_TRY(mg_prolongate<T>(H, l, Buf<T>::x(H->lv[l - 1]), Buf<T>::x(H->lv[l]), s));
     // x_l is needed as the V-cycle's iterate; the level's y / r / d buffers are its scratch
     HHG_TRY(vcycle<T>(H, l, Buf<T>::b(H->lv[l]), Buf<T>::x(H->lv[l]), o, s));
   }
@@ -935,9 +1310,14 @@ extern "C" int hhg_mg_solve(hhg_op_t* op, const double* b, double* x, const hhg_
                             void* stream) {
   clear_error();
   if (!op || !b || !x || !opts) return fail(HHG_E_ARG, "mg_solve: null pointer");
-  if (op->kind != HHG_DIFFUSION || op->bc != HHG_DIRICHLET ||
-      (op->coeff.type != HHG_COEFF_CONST && op->coeff.type != HHG_COEFF_SIN3))
-    return fail(HHG_E_UNSUPPORTED, "mg_solve: needs a DIRICHLET diffusion operator with CONST or SIN3 coefficient");
+  const bool n1 = op->kind == HHG_CURLCURL;
+  if (op->bc != HHG_DIRICHLET)
+    return fail(HHG_E_UNSUPPORTED, "mg_solve: needs a DIRICHLET operator");
+  if (!n1 && (op->kind != HHG_DIFFUSION || (op->coeff.type != HHG_COEFF_CONST && op->coeff.type != HHG_COEFF_SIN3)))
+    return fail(HHG_E_UNSUPPORTED, "mg_solve: needs a diffusion operator with CONST or SIN3 coefficient, or a "
+                                   "curl-curl operator");
+  if (n1 && (op->coeff.type != HHG_COEFF_CONST || op->coeff2.type != HHG_COEFF_CONST))
+    return fail(HHG_E_UNSUPPORTED, "mg_solve: the curl-curl hierarchy takes CONST alpha and beta");
   if (opts->nu1 < 0 || opts->nu2 < 0 || opts->cheb_order < 1 || opts->max_iters < 0 || !(opts->tol > 0))
     return fail(HHG_E_ARG, "mg_solve: bad options");
   cudaStream_t s = (cudaStream_t)stream;
@@ -953,62 +1333,65 @@ extern "C" int hhg_mg_solve(hhg_op_t* op, const double* b, double* x, const hhg_
   MGHierarchy* H = op->mg;
   MGLevel& F = H->lv[H->L];
   const int64_t n = F.n;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, s);
-  double nb2 = 0.0;
-  HHG_TRY(hhg_vec_dot(op->mesh, op->level, op->degree, b, b, HHG_F64, 1, &nb2, s));
-  const double nb = std::sqrt(nb2);
-  if (opts->fmg) {
-    if (opts->mixed) {
-      HHG_TRY(fmg_t<float>(H, b, opts, s));
-      convert_kernel<double, float><<<nblocks<double>(n), 256, 0, s>>>(n, F.x32, x);
-    } else {
-      HHG_TRY(fmg_t<double>(H, b, opts, s));
-      HHG_CUDA_TRY(cudaMemcpyAsync(x, F.x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  // the events are released on every path, errors included
+  struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~EventPair() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
     }
-  }
+  } ev;
+  HHG_CUDA_TRY(cudaEventCreate(&ev.e0));
+  HHG_CUDA_TRY(cudaEventCreate(&ev.e1));
+  HHG_CUDA_TRY(cudaEventRecord(ev.e0, s));
   int it = 0;
   double rel = 0.0;
-  int status = HHG_OK;
-  for (;; ++it) {
-    // outer residual in FP64
-    HHG_TRY(hhg_op_apply(op, x, H->xf64, HHG_F64, 1, s));
-    residual_kernel<double><<<nblocks<double>(n), 256, 0, s>>>(n, b, H->xf64, H->rf64);
-    double r2 = 0.0;
-    HHG_TRY(hhg_vec_dot(op->mesh, op->level, op->degree, H->rf64, H->rf64, HHG_F64, 1, &r2, s));
-    rel = nb > 0 ? std::sqrt(r2) / nb : std::sqrt(r2);
-    if (stats && it < 64) stats->residual_history[it] = rel;
-    if (!std::isfinite(rel)) {
-      status = fail(HHG_E_NAN, "mg_solve: residual is not finite");
-      break;
+  // FMG, then outer iterations; every exit of the body leaves the iteration count and the last
+  // residual for the statistics
+  auto body = [&]() -> int {
+    double nb2 = 0.0;
+    HHG_TRY(hhg_vec_dot(op->mesh, op->level, op->degree, b, b, HHG_F64, 1, &nb2, s));
+    const double nb = std::sqrt(nb2);
+    if (opts->fmg) {
+      if (opts->mixed) {
+        HHG_TRY(fmg_t<float>(H, b, opts, s));
+        convert_kernel<double, float><<<nblocks<double>(n), 256, 0, s>>>(n, F.x32, x);
+      } else {
+        HHG_TRY(fmg_t<double>(H, b, opts, s));
+        HHG_CUDA_TRY(cudaMemcpyAsync(x, F.x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      }
     }
-    if (rel <= opts->tol) break;
-    if (it >= opts->max_iters) {
-      status = fail(HHG_E_NOT_CONVERGED, "mg_solve: relative residual %.3e after %d iterations", rel, it);
-      break;
+    for (;; ++it) {
+      // outer residual in FP64
+      HHG_TRY(hhg_op_apply(op, x, H->xf64, HHG_F64, 1, s));
+      residual_kernel<double><<<nblocks<double>(n), 256, 0, s>>>(n, b, H->xf64, H->rf64);
+      double r2 = 0.0;
+      HHG_TRY(hhg_vec_dot(op->mesh, op->level, op->degree, H->rf64, H->rf64, HHG_F64, 1, &r2, s));
+      rel = nb > 0 ? std::sqrt(r2) / nb : std::sqrt(r2);
+      if (stats && it < 64) stats->residual_history[it] = rel;
+      if (!std::isfinite(rel)) return fail(HHG_E_NAN, "mg_solve: residual is not finite");
+      if (rel <= opts->tol) return HHG_OK;
+      if (it >= opts->max_iters)
+        return fail(HHG_E_NOT_CONVERGED, "mg_solve: relative residual %.3e after %d iterations", rel, it);
+      // correction c = V(r) from zero, in the inner precision; x += c in FP64
+      if (opts->mixed) {
+        convert_kernel<float, double><<<nblocks<float>(n), 256, 0, s>>>(n, H->rf64, F.b32);
+        HHG_CUDA_TRY(cudaMemsetAsync(F.x32, 0, sizeof(float) * n, s));
+        HHG_TRY(vcycle<float>(H, H->L, F.b32, F.x32, opts, s));
+        axpy_kernel<double, float><<<nblocks<double>(n), 256, 0, s>>>(n, x, F.x32, 1.0);
+      } else {
+        HHG_CUDA_TRY(cudaMemcpyAsync(F.b64, H->rf64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        HHG_CUDA_TRY(cudaMemsetAsync(F.x64, 0, sizeof(double) * n, s));
+        HHG_TRY(vcycle<double>(H, H->L, F.b64, F.x64, opts, s));
+        axpy_kernel<double, double><<<nblocks<double>(n), 256, 0, s>>>(n, x, F.x64, 1.0);
+      }
+      HHG_CUDA_TRY(cudaGetLastError());
     }
-    // correction c = V(r) from zero, in the inner precision; x += c in FP64
-    if (opts->mixed) {
-      convert_kernel<float, double><<<nblocks<float>(n), 256, 0, s>>>(n, H->rf64, F.b32);
-      HHG_CUDA_TRY(cudaMemsetAsync(F.x32, 0, sizeof(float) * n, s));
-      HHG_TRY(vcycle<float>(H, H->L, F.b32, F.x32, opts, s));
-      axpy_kernel<double, float><<<nblocks<double>(n), 256, 0, s>>>(n, x, F.x32, 1.0);
-    } else {
-      HHG_CUDA_TRY(cudaMemcpyAsync(F.b64, H->rf64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      HHG_CUDA_TRY(cudaMemsetAsync(F.x64, 0, sizeof(double) * n, s));
-      HHG_TRY(vcycle<double>(H, H->L, F.b64, F.x64, opts, s));
-      axpy_kernel<double, double><<<nblocks<double>(n), 256, 0, s>>>(n, x, F.x64, 1.0);
-    }
-    HHG_CUDA_TRY(cudaGetLastError());
-  }
-  cudaEventRecord(e1, s);
-  cudaEventSynchronize(e1);
+  };
+  const int status = body();
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (cudaEventRecord(ev.e1, s) == cudaSuccess && cudaEventSynchronize(ev.e1) == cudaSuccess)
+    cudaEventElapsedTime(&ms, ev.e0, ev.e1);
   if (stats) {
     stats->iterations = it;
     stats->rel_residual = rel;

@@ -1235,6 +1235,27 @@ int launch_interface_sum_signed(const Interface* itf, T* y, bool dirichlet, cuda
   HHG_CUDA_TRY(cudaGetLastError());
   return HHG_OK;
 }
+template <typename T>
+__global__ void iface_copy_owner_signed_kernel(const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
+                                               const int8_t* __restrict__ sgn, int64_t ngroups, T* __restrict__ x) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ngroups) return;
+  const int64_t a = ptr[g], b = ptr[g + 1];
+  const T v = T(sgn[a]) * x[idx[a]];
+  for (int64_t t = a + 1; t < b; ++t) x[idx[t]] = T(sgn[t]) * v;
+}
+
+template <typename T>
+int launch_make_consistent_signed(const Interface* itf, T* x, cudaStream_t s) {
+  if (itf->ngroups == 0) return HHG_OK;
+  iface_copy_owner_signed_kernel<T><<<(unsigned)((itf->ngroups + 255) / 256), 256, 0, s>>>(itf->d_ptr, itf->d_idx,
+                                                                                          itf->d_sign, itf->ngroups, x);
+  HHG_CUDA_TRY(cudaGetLastError());
+  return HHG_OK;
+}
+template int launch_make_consistent_signed<double>(const Interface*, double*, cudaStream_t);
+template int launch_make_consistent_signed<float>(const Interface*, float*, cudaStream_t);
+
 template int launch_interface_sum_signed<double>(const Interface*, double*, bool, cudaStream_t);
 template int launch_interface_sum_signed<float>(const Interface*, float*, bool, cudaStream_t);
 
@@ -1298,8 +1319,8 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
       HHG_CUDA_TRY(cudaGetLastError());
       return HHG_OK;
     }
-    const TileTasks& tt = I->tile[kClimbPT == 4 ? 0 : 1];
     const OpConst<float>* cf = (const OpConst<float>*)op->d_const32;
+    const TileTasks& tt = I->tile[kClimbPT == 4 ? 0 : 1];
     // face blocks: slices 0-5 need tri(N) threads each, the top planes at most V(kP1ClimbTop - 1) <= 256
     static_assert(kP1ClimbTop * (kP1ClimbTop + 1) * (kP1ClimbTop + 2) / 6 <= 256, "top planes exceed one block");
     const int nfb = (int)((tri_host(op->N) + 255) / 256);
@@ -1371,8 +1392,8 @@ hhg_op::~hhg_op() {
   cudaFree(d_p2st64);
   cudaFree(d_p2st32);
   cudaFree(d_p2idx);
-  cudaFree(d_eps_tasks);
   cudaFree(d_elem);
+  cudaFree(d_face);
 }
 
 static int check_dtype(int dtype) {
@@ -1547,6 +1568,8 @@ extern "C" int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, 
     HHG_CUDA_TRY(cudaMemcpy(op->d_p2st64, w64.data(), sizeof(P2Stencil<double>) * nm, cudaMemcpyHostToDevice));
     HHG_CUDA_TRY(cudaMemcpy(op->d_p2st32, w32.data(), sizeof(P2Stencil<float>) * nm, cudaMemcpyHostToDevice));
   }
+  HHG_TRY(alloc_face_scratch(op.get()));
+  HHG_TRY(noalloc_prepare());
   *out = op.release();
   return HHG_OK;
 }
@@ -1665,11 +1688,23 @@ extern "C" int hhg_op_diagonal(hhg_op_t* op, void* d, int dtype, void* stream) {
   clear_error();
   if (!op || !d) return fail(HHG_E_ARG, "op_diagonal: null pointer");
   HHG_TRY(check_dtype(dtype));
-  if (op->kind != HHG_DIFFUSION) return fail(HHG_E_UNSUPPORTED, "op_diagonal: scalar operators only");
+  if (op->kind != HHG_DIFFUSION && op->kind != HHG_CURLCURL)
+    return fail(HHG_E_UNSUPPORTED, "op_diagonal: scalar diffusion and curl-curl operators only");
   HHG_TRY(check_field(op, dtype));
   cudaStream_t s = (cudaStream_t)stream;
   const Interface* itf = nullptr;
   HHG_TRY(op->mesh->interface(op->level, op->degree, &itf));
+  if (op->kind == HHG_CURLCURL) {
+    // the diagonal does not depend on the orientation of an edge: the copies add without signs
+    if (dtype == HHG_F64) {
+      HHG_TRY(launch_n1_diag<double>(op, (double*)d, s));
+      HHG_TRY(launch_interface_sum<double>(itf, (double*)d, 1, op->bc == HHG_DIRICHLET, s));
+    } else {
+      HHG_TRY(launch_n1_diag<float>(op, (float*)d, s));
+      HHG_TRY(launch_interface_sum<float>(itf, (float*)d, 1, op->bc == HHG_DIRICHLET, s));
+    }
+    return HHG_OK;
+  }
   if (dtype == HHG_F64) {
     HHG_TRY(launch_diag<double>(op, (double*)d, s));
     HHG_TRY(launch_interface_sum<double>(itf, (double*)d, 1, op->bc == HHG_DIRICHLET, s));
@@ -1907,6 +1942,8 @@ extern "C" int hhg_op_create_curlcurl(hhg_mesh_t* mesh, int level, const hhg_coe
   HHG_CUDA_TRY(cudaMemcpy(op->d_const32, c32.data(), sizeof(OpConst<float>) * nm, cudaMemcpyHostToDevice));
   HHG_CUDA_TRY(cudaMemcpy(op->d_n1_64, n64.data(), sizeof(N1Const<double>) * nm, cudaMemcpyHostToDevice));
   HHG_CUDA_TRY(cudaMemcpy(op->d_n1_32, n32.data(), sizeof(N1Const<float>) * nm, cudaMemcpyHostToDevice));
+  HHG_TRY(alloc_face_scratch(op.get()));
+  HHG_TRY(noalloc_prepare());
   *out = op.release();
   return HHG_OK;
 }

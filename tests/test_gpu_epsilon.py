@@ -81,8 +81,8 @@ def test_epsilon_rigid_body_modes_neumann():
 
 
 def test_epsilon_batch_sizes_on_one_operator():
-    """One operator applied with 3, 16 and again 3 right-hand sides (the per-launch task lists are
-    rebuilt when the batch size changes); more than 256 right-hand sides are refused."""
+    """One operator applied with 3, 16 and again 3 right-hand sides (the task lists are built at the
+    first call of each batch size and kept); more than 256 right-hand sides are refused."""
     import paper_2404_08371_gb300 as hhg
     from gpu_helpers import rel_err
     c, mu = _case("cube6", 1)

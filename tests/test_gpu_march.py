@@ -105,7 +105,8 @@ def test_adjoint_parity(meshname, level, degree, bc, dtype):
 
 
 # Level 6 (64 cubes per edge) is the smallest lattice on which the marching tiles own every column
-# of cubes and add the points on their i- and j-faces atomically; every point checked here.
+# of cubes and the points on their i- and j-faces collect the partial sums of the neighbouring
+# tiles through the per-operator face scratch; every point checked here.
 @pytest.mark.parametrize("meshname,degree,kind,bc,dtype", [
     ("reference_tet", 2, "sin3", "dirichlet", torch.float64),
     ("reference_tet", 2, "sin3", "dirichlet", torch.float32),
@@ -276,3 +277,42 @@ def test_bench_legs_full_size_sampled(degree, coeff, level, stored, dtype):
     ref = OA.sampled_diffusion_rows(v[t[0]], level, degree, lc, QD[degree], "dirichlet", xp, pts)
     tol = 1e-12 if dtype == torch.float64 else 1e-5
     assert np.abs(y[sample] - ref).max() <= tol * np.abs(y).max(), np.abs(y[sample] - ref).max() / np.abs(y).max()
+
+
+@pytest.mark.parametrize("case", ["p2_sin3_f64_level8_apply", "p1_sin3_f32_level8_apply", "p1_field_f64_level7_adjoint",
+                                  "p2_sin3_f64_level7_diag", "n1_cube6_level6_apply"])
+def test_march_bitwise_repeatable(case):
+    """On lattices whose marching tiles share faces (64 cubes per edge and more), two calls give
+    bit-identical results: the shared points are summed in a fixed order, without atomics."""
+    import paper_2404_08371_gb300 as hhg
+    if case.startswith("n1"):
+        v, t = W.cube6()
+        mesh = hhg.Mesh(v, t, 6)
+        xyz = mesh.coordinates(1)
+        op = hhg.CurlCurl(mesh, ("field_p1", (1.0 + xyz[:, 0] / 3.0).contiguous()),
+                          ("field_p1", (1.0 + xyz[:, 2]).contiguous()), bc="dirichlet")
+        x = torch.tensor(W.uniform(mesh.vec_size(2), seed=3), device="cuda")
+        a, b = op.apply(x), op.apply(x)
+    else:
+        v, t = W.reference_tet()
+        degree = int(case[1])
+        level = int(case.split("level")[1][0])
+        dtype = torch.float64 if "f64" in case else torch.float32
+        mesh = hhg.Mesh(v, t, level)
+        n = mesh.vec_size(degree)
+        if "field" in case:
+            k = torch.exp(torch.tensor(W.fourier_field(mesh.coordinates(degree).cpu().numpy()), device="cuda"))
+            op = hhg.Operator(mesh, degree=degree, coeff=("field_p%d" % degree, k.to(dtype)), bc="dirichlet",
+                              quad_degree=QD[degree])
+        else:
+            op = hhg.Operator(mesh, degree=degree, coeff=("sin3",), bc="dirichlet", quad_degree=QD[degree])
+        x = torch.tensor(W.uniform(n, seed=1), device="cuda").to(dtype)
+        if case.endswith("adjoint"):
+            g = torch.tensor(W.uniform(n, seed=2), device="cuda").to(dtype)
+            a, b = op.adjoint_coeff(x, g), op.adjoint_coeff(x, g)
+        elif case.endswith("diag"):
+            a, b = op.diagonal(dtype), op.diagonal(dtype)
+        else:
+            a, b = op.apply(x), op.apply(x)
+    assert torch.isfinite(a).all()
+    assert torch.equal(a, b)

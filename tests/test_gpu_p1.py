@@ -12,8 +12,8 @@ TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
 
 
 @pytest.mark.parametrize("meshname,level", [("reference_tet", 0), ("reference_tet", 1), ("reference_tet", 4),
-                                            ("reference_tet", 5), ("cube6", 2), ("cube6", 3), ("cube48", 2),
-                                            ("cuboid36", 1)])
+                                            ("reference_tet", 5), ("reference_tet", 6), ("cube6", 2), ("cube6", 3),
+                                            ("cube6", 5), ("cube48", 2), ("cuboid36", 1), ("cuboid36", 4)])
 @pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_p1_const_apply_parity(meshname, level, bc, dtype):
@@ -118,8 +118,10 @@ def test_coordinates(meshname, level, degree):
 @pytest.mark.parametrize("level", [7, 8])
 @pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
 def test_p1_const_f32_matches_f64_full_vector(level, bc):
-    """Every point of the FP32 apply (register-climbing kernel + face kernel) at sizes with rows
-    longer than one tile, against the FP64 apply of the same FP32-representable input."""
+    """Every point of the FP32 apply (register-climbing kernel + face blocks) at sizes with many
+    k-chunks and row blocks, against the FP64 apply of the same FP32-representable input; the FP64
+    apply is itself checked against the oracle's rows at level 8 (test_p1_const_level8_sampled), and
+    the FP32 apply directly at level 9 (test_p1_const_f32_level9_sampled)."""
     import paper_2404_08371_gb300 as hhg
     v, t = W.reference_tet()
     mesh = hhg.Mesh(v, t, level)
@@ -129,3 +131,42 @@ def test_p1_const_f32_matches_f64_full_vector(level, bc):
     y64 = op.apply(x32.double())
     assert torch.isfinite(y32).all()
     assert (y32 - y64).abs().max().item() <= 1e-5 * y64.abs().max().item()
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_p1_const_f32_level9_sampled(bc):
+    """The bench's FP32 P1 constant-coefficient leg (reference macro, level 9, 22.6 M points, climbing
+    kernel): sampled rows against the oracle's per-point sum on the FP32-rounded input (FP64)."""
+    import paper_2404_08371_gb300 as hhg
+    v, t = W.reference_tet()
+    level = 9
+    N = 2 ** level
+    mesh = hhg.Mesh(v, t, level)
+    op = hhg.Operator(mesh, degree=1, coeff=("const", 1.0), bc=bc)
+    n = mesh.vec_size(1)
+    xp = W.uniform(n, seed=2).astype(np.float32)
+    x = torch.from_numpy(xp).to("cuda")
+    y = op.apply(x).cpu().numpy().astype(np.float64)
+    pts = OM.lattice_points(N)
+    rng = np.random.default_rng(5)
+    near = np.nonzero((pts.min(axis=1) <= 1) | (pts.sum(axis=1) >= N - 1) | (pts[:, 2] >= N - 5))[0]
+    sample = np.concatenate([rng.choice(n, 400, replace=False), rng.choice(near, 200, replace=False), [0, n - 1]])
+    ref = OA.sampled_diffusion_rows(v[t[0]], level, 1, ("const", 1.0), 2, bc, xp.astype(np.float64), pts[sample])
+    assert np.abs(y[sample] - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_p1_const_f32_unaligned_view():
+    """Vectors that do not start on a 16-byte boundary (a view one float in) give the same result."""
+    import paper_2404_08371_gb300 as hhg
+    from gpu_helpers import Case, rel_err
+    c = Case("cube6", 5, 1)
+    op = hhg.Operator(c.mesh, degree=1, coeff=("const", 1.0), bc="dirichlet")
+    xg = W.uniform(c.S.ndof, seed=9)
+    n = c.mesh.vec_size(1)
+    buf = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = c.packed(xg, torch.float32)
+    ybuf = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
+    op.apply(buf[1:], out=ybuf[1:])
+    ref = OA.diffusion_matrix(c.S, ("const", 1.0), 2, "dirichlet") @ xg.astype(np.float32).astype(np.float64)
+    got, spread = c.unpack(ybuf[1:])
+    assert rel_err(got, ref) <= 1e-5 and spread == 0.0
