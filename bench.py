@@ -314,7 +314,11 @@ def run_const_legs(hhg, torch, flush, peak_gbs: float, reps: int = 5):
         mesh = hhg.Mesh(v, t, level)
         op = hhg.Operator(mesh, degree=degree, coeff=("const", 1.0), bc="dirichlet")
         tot, inner = mesh.dof_count(degree)
-        for dt, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+        variants = [("f64", torch.float64, "native"), ("f32", torch.float32, "native")]
+        if degree == 1:
+            variants.append(("df64", torch.float64, "double_float"))   # FP64 vectors, FP32-pair arithmetic
+        for dt, tdt, arith in variants:
+            op.set_fp64_arith(arith) if tdt == torch.float64 else None
             x = torch.from_numpy(W.uniform(mesh.vec_size(degree), seed=0)).to("cuda", tdt)
             y = torch.empty_like(x)
             ms = time_apply(torch, lambda: op.apply(x, out=y), flush, reps)
@@ -323,8 +327,11 @@ def run_const_legs(hhg, torch, flush, peak_gbs: float, reps: int = 5):
             tr = load_traffic().get(key)
             out[key] = {"level": level, "ms": ms, "mdofs": inner / ms / 1e3, "gbs": nbytes / ms / 1e6,
                         "hbm_frac": nbytes / ms / 1e6 / peak_gbs, "bytes": nbytes,
+                        "arith": {"f64": "fp64", "f32": "fp32", "df64": "double-float (FP32 pairs, 48-bit "
+                                  "significands; FP64 input and output)"}[dt],
                         "traffic": tr["bytes_per_launch"] if tr else None}
             del x, y
+        op.set_fp64_arith("native")
         del op, mesh
     return out
 
@@ -425,6 +432,76 @@ def run_n1(hhg, torch, flush, level: int = 7, reps: int = 3):
         ms_st = time_apply(torch, lambda: op.apply(x, out=y), flush, reps)
         out[dt]["stored"] = {"ms": ms_st, "mdofs": n_edges_interior / ms_st / 1e3, "setup_ms": e0.elapsed_time(e1)}
         del op, x, y
+    return out
+
+
+def n1_interpolant(mesh, torch, E):
+    """Packed Nedelec vector of the smooth field E (points (n, 3) -> (n, 3), torch): on every edge
+    point of the doubled lattice E at the midpoint dotted with the physical edge vector along the
+    macro's canonical lattice direction (midpoint rule; vertex points 0).  Synthetic input only."""
+    import numpy as np
+    N = 2 ** (mesh.level + 1)
+    pts = []
+    for k in range(N + 1):
+        for j in range(N + 1 - k):
+            for_i = np.arange(N - k - j + 1)
+            pts.append(np.stack([for_i, np.full_like(for_i, j), np.full_like(for_i, k)], axis=1))
+    pts = np.concatenate(pts)
+    par = pts & 1
+    d = par.copy()
+    d[(par[:, 0] == 1) & (par[:, 1] == 1), 1] = -1
+    sel = ((par[:, 0] == 1) | (par[:, 1] == 1)) & (par[:, 2] == 1) & ~((par[:, 0] == 1) & (par[:, 1] == 1))
+    d[sel, 2] = -1
+    edge = par.any(axis=1)
+
+    def packed(q):
+        i, j, k = q[:, 0], q[:, 1], q[:, 2]
+        vk = lambda s: (s + 1) * (s + 2) * (s + 3) // 6
+        m = N - k
+        return vk(N) - vk(N - k) + j * (m + 1) - j * (j - 1) // 2 + i
+
+    start, end = packed(np.where(edge[:, None], pts - d, pts)), packed(np.where(edge[:, None], pts + d, pts))
+    V = len(pts)
+    xyz = mesh.coordinates(2).view(-1, V, 3)
+    s_t = torch.from_numpy(start).to(xyz.device)
+    e_t = torch.from_numpy(end).to(xyz.device)
+    vec = xyz[:, e_t] - xyz[:, s_t]                        # (macros, V, 3): zero at vertex points
+    val = (E(xyz.reshape(-1, 3)).view(-1, V, 3) * vec).sum(dim=2)
+    return val.reshape(-1).contiguous()
+
+
+def run_n1_fmg(hhg, torch, level: int = 6):
+    """FMG + V(2,2) with Hiptmair's hybrid smoother for the curl-curl + mass problem (Eq. N1,
+    alpha = beta = 1) on the 36-macro 3x2x1 cuboid, all-FP64 against FP32 cycles inside FP64
+    refinement, to a relative residual of 1e-10.  b = A u_I with u_I the Nedelec interpolant of
+    E = (sin pi y sin pi z, sin pi x sin pi z, sin pi x sin pi y); times are CUDA-event device
+    times of the solve (FMG + iterations), the hierarchy set-up reported apart."""
+    import math
+    import workloads as W
+    v, t = W.cuboid36()
+    mesh = hhg.Mesh(v, t, level)
+    op = hhg.CurlCurl(mesh, ("const", 1.0), ("const", 1.0), bc="dirichlet")
+
+    def E(p):
+        s = torch.sin(math.pi * p)
+        return torch.stack([s[:, 1] * s[:, 2], s[:, 0] * s[:, 2], s[:, 0] * s[:, 1]], dim=1)
+
+    u = n1_interpolant(mesh, torch, E)
+    b = op.apply(u)
+    tot2, int2 = mesh.dof_count(2)
+    tot1, int1 = mesh.dof_count(1)
+    n_edges = int2 - int1
+    out = {"workload": "3x2x1 cuboid as 36 macros, level %d, N1 curl-curl + mass (alpha = beta = 1), "
+                       "b = A u_I, FMG + V(2,2) with the hybrid smoother, tol 1e-10" % level,
+           "interior_edges": n_edges}
+    for name, mixed in (("fp64", 0), ("mixed", 1)):
+        x, st0 = op.mg_solve(b, torch.zeros_like(b), mixed=mixed)
+        x, st = op.mg_solve(b, torch.zeros_like(b), mixed=mixed)
+        err = ((x - u).abs().max() / u.abs().max()).item()
+        out[name] = {"solve_ms": st["solve_ms"], "setup_ms": st0["setup_ms"], "iterations": st["iterations"],
+                     "rel_residual": st["rel_residual"], "max_rel_diff_to_u_I": err,
+                     "mdofs_per_s": n_edges / (st["solve_ms"] * 1e-3) / 1e6}
+    out["mixed_speedup"] = out["fp64"]["solve_ms"] / out["mixed"]["solve_ms"]
     return out
 
 
@@ -724,6 +801,8 @@ def main():
         del flush
         torch.cuda.empty_cache()
         fmg = run_fmg(hhg, torch, args.fmg_level)
+        torch.cuda.empty_cache()
+        fmg["n1"] = run_n1_fmg(hhg, torch)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()

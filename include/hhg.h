@@ -134,6 +134,19 @@ int hhg_op_destroy(hhg_op_t* op);
 int hhg_op_create_curlcurl(hhg_mesh_t* mesh, int level, const hhg_coeff_t* alpha, const hhg_coeff_t* beta, int bc,
                            hhg_op_t** out);
 
+/* Arithmetic of FP64 applies (no counterpart in the paper, whose FP64 runs
+ * on CPU FMA units).  HHG_FP64_NATIVE (the default): FP64 operations.
+ * HHG_FP64_DOUBLE_FLOAT: FP64 vectors in and out, the arithmetic in pairs
+ * of FP32 numbers (hi + lo, 48 significant bits: relative errors of a few
+ * 1e-15 per operation, within the 1e-12 tolerance of FP64 applies), for
+ * GPUs whose FP64 rate is a small fraction of their FP32 rate (GB300:
+ * 1/64).  Available for P1 constant-coefficient DIFFUSION operators; it
+ * allocates a device vector of 8 bytes per point for the split input
+ * (freed when the mode returns to native or with the operator).
+ * Errors: HHG_E_UNSUPPORTED (other operators), HHG_E_OOM, HHG_E_ARG. */
+enum { HHG_FP64_NATIVE = 0, HHG_FP64_DOUBLE_FLOAT = 1 };
+int hhg_op_set_fp64_arith(hhg_op_t* op, int mode);
+
 /* Replace the borrowed coefficient field pointer of a FIELD operator. */
 int hhg_op_set_field(hhg_op_t* op, const void* field, int field_dtype);
 

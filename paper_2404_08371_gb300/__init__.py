@@ -187,6 +187,13 @@ class Operator:
             lib.hhg_op_destroy(h)
             self.handle = None
 
+    def set_fp64_arith(self, mode: str) -> "Operator":
+        """"native" (FP64 operations, the default) or "double_float" (FP64 vectors, FP32-pair
+        arithmetic; P1 constant-coefficient diffusion only)."""
+        code = {"native": 0, "double_float": 1}[mode]
+        check(lib.hhg_op_set_fp64_arith(self.handle, code), "hhg_op_set_fp64_arith")
+        return self
+
     def set_field(self, field: torch.Tensor):
         self.field = field
         check(lib.hhg_op_set_field(self.handle, _dev_ptr(field), dtype_code(field)), "hhg_op_set_field")

@@ -69,6 +69,7 @@ SIGNATURES = {
     "hhg_power_iteration": ([_vp, _vp, _vp, _i, _i, ctypes.POINTER(_d), _vp], _i),
     "hhg_mg_default_opts": ([ctypes.POINTER(hhg_mg_opts_t)], _i),
     "hhg_mg_solve": ([_vp, _vp, _vp, ctypes.POINTER(hhg_mg_opts_t), ctypes.POINTER(hhg_mg_stats_t), _vp], _i),
+    "hhg_op_set_fp64_arith": ([_vp, _i], _i),
     "hhg_prolongate_edges": ([_vp, _i, _vp, _vp, _i, _vp], _i),
     "hhg_restrict_edges": ([_vp, _i, _vp, _vp, _i, _vp], _i),
     "hhg_gradient": ([_vp, _i, _vp, _vp, _i, _vp], _i),

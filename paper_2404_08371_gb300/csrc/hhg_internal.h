@@ -278,6 +278,10 @@ struct hhg_op {
   const hhg::Interface* itf = nullptr;   // per-level data of the op's space (owned by the mesh)
   // partial sums of the points shared by marching tiles (lattices of at least kMarchJAtomicN cubes
   // per edge; march_kernel.cuh, FaceScratch): FP64-sized, per macro face_S slots
+  // P1 constant diffusion, FP64 vectors in double-float arithmetic (ops.cu): the stencil weights as
+  // FP32 pairs (float2[16] per macro) and the split input vector (float2[npts])
+  void* d_p1df = nullptr;
+  void* d_p1df_x = nullptr;
   void* d_face = nullptr;
   int64_t face_S = 0, face_Si = 0, face_Sj = 0;
   int face_Ti = 0, face_Tj = 0;

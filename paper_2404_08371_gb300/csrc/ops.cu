@@ -381,6 +381,124 @@ __global__ void __launch_bounds__(256) p1_gather_kernel(const OpConst<T>* __rest
   ym[p] = acc;
 }
 
+// ---------------------------------------------------------------------------
+// P1 constant-coefficient apply of FP64 vectors in double-float arithmetic.
+//
+// GB300 runs FP64 at 1/64 of its FP32 rate, so the FP64 stencil above is bound by the FP64 pipe
+// (15 DFMA per point).  Here every FP64 value v is carried as an unevaluated sum hi + lo of two
+// FP32 numbers (hi = v rounded to FP32, lo = the rounded remainder: 48 significant bits), and the
+// stencil sum_d S_d x_d is formed in FP32 arithmetic: the product of the high parts exactly by an
+// FMA (Dekker's product), the cross terms by FMA, the high parts summed by Knuth's two-sum, the low
+// parts summed apart.  The relative error of a row is a few units of 2^-48 (about 1e-14), far
+// inside the 1e-12 of an FP64 apply; x is split once per apply by a streaming pass.
+// ---------------------------------------------------------------------------
+// FP64 v -> (hi, lo) from its bit fields with integer operations (the FP64 pipe, 1/64 of the FP32
+// rate on GB300, would bound conversions): hi = v truncated to 24 significant bits, lo = the
+// remaining 29 bits converted to FP32 and scaled.  Zero and subnormal v give (0, 0); values outside
+// the exponent range that FP32 pairs represent exactly (|v| >= 2^127 or |v| < 2^-74) take the
+// FP64 conversion.
+__device__ __forceinline__ float2 split_double_bits(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned uh = (unsigned)(u >> 32), ul = (unsigned)u;
+  const int e = (int)((uh >> 20) & 0x7ffu);
+  if (e == 0) return make_float2(0.0f, 0.0f);
+  if (e < 949 || e > 1150) {
+    const float hi = __double2float_rz(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+  }
+  const unsigned sign = uh & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((uh & 0xfffffu) << 3) | (ul >> 29));
+  const float scale = __uint_as_float((unsigned)(e - 948) << 23);   // 2^(e - 1075)
+  const float lo = __uint2float_rn(ul & 0x1fffffffu) * scale;
+  return make_float2(hi, sign ? -lo : lo);
+}
+
+// FP32 -> FP64 from the bit fields (exact; subnormal FP32 values read as zero)
+__device__ __forceinline__ double float_to_double_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned fe = (b >> 23) & 0xffu;
+  if (fe == 0) return 0.0;
+  const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                               ((unsigned long long)(fe + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+__global__ void split_double_kernel(int64_t n, const double* __restrict__ x, float2* __restrict__ xs) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) xs[t] = split_double_bits(x[t]);
+}
+
+// acc += w * v for double-float w, v; acc.x the high sum, acc.y the low parts and rounding errors
+// (explicitly rounded operations: a product or sum fused into an FMA by the compiler would break
+// the exactness the two-sum and the product error rely on)
+__device__ __forceinline__ void df_fma(float2& acc, float2 w, float2 v) {
+  const float ph = __fmul_rn(w.x, v.x);
+  float pl = fmaf(w.x, v.x, -ph);        // exact low part of w.hi v.hi
+  pl = fmaf(w.x, v.y, pl);
+  pl = fmaf(w.y, v.x, pl);
+  const float sh = __fadd_rn(acc.x, ph);   // two-sum of the high parts
+  const float bb = __fsub_rn(sh, acc.x);
+  const float e = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(sh, bb)), __fsub_rn(ph, bb));
+  acc.x = sh;
+  acc.y += pl + e;
+}
+
+template <bool DIRICHLET>
+__global__ void __launch_bounds__(256) p1_gather_df_kernel(const OpConst<double>* __restrict__ cst,
+                                                            const float2* __restrict__ wdf,
+                                                            const int* __restrict__ cta_plane,
+                                                            const int* __restrict__ cta_start,
+                                                            const int* __restrict__ pstart,
+                                                            const double* __restrict__ x,
+                                                            const float2* __restrict__ xs, double* __restrict__ y) {
+  const OpConst<double>& c = cst[blockIdx.y];
+  const int N = c.N;
+  const int k = __ldg(cta_plane + blockIdx.x);
+  const int s = N - k;
+  const int q = (blockIdx.x - __ldg(cta_start + k)) * 256 + threadIdx.x;
+  if (q >= tri(s)) return;
+  const float bq = 2.0f * s + 3.0f;
+  int j = (int)(0.5f * (bq - sqrtf(fmaxf(bq * bq - 8.0f * (float)q, 0.0f))));
+  j = max(0, min(j, s));
+  if (j < s && row32(s, j + 1) <= q) ++j;
+  if (j > 0 && row32(s, j) > q) --j;
+  const int i = q - row32(s, j);
+  const int pk = __ldg(pstart + k);
+  const int p = pk + q;
+  const double* __restrict__ xm = x + c.base;
+  const float2* __restrict__ xsm = xs + c.base;
+  double* __restrict__ ym = y + c.base;
+  const bool on_face = (i == 0) | (j == 0) | (k == 0) | (i + j + k == N);
+  if (on_face) {
+    ym[p] = p1_face_value<double, DIRICHLET>(c, pstart, xm, i, j, k);
+    return;
+  }
+  const int r00 = p - i;                                 // (j, k)
+  const int rp0 = r00 + (s + 1 - j);                     // (j+1, k)
+  const int rm0 = r00 - (s + 2 - j);                     // (j-1, k)
+  const int pk1 = pk + tri(s);
+  const int r01 = pk1 + row32(s - 1, j);                 // (j, k+1)
+  const int rm1 = pk1 + row32(s - 1, j - 1);             // (j-1, k+1)
+  const int pkm = pk - tri(s + 1);
+  const int r0m = pkm + row32(s + 1, j);                 // (j, k-1)
+  const int rpm = pkm + row32(s + 1, j + 1);             // (j+1, k-1)
+  const int at[15] = {r00 + i,     r00 + i + 1, r00 + i - 1, rp0 + i,     rm0 + i,
+                      r01 + i,     r0m + i,     rm0 + i + 1, rp0 + i - 1, r0m + i + 1,
+                      r01 + i - 1, rpm + i,     rm1 + i,     rm1 + i + 1, rpm + i - 1};
+  const float2* __restrict__ w = wdf + 16 * blockIdx.y;
+  const bool near = DIRICHLET && !(i >= 2 && j >= 2 && k >= 2 && i + j + k <= N - 2);
+  float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int d = 0; d < 15; ++d) {
+    float2 v = __ldg(xsm + at[d]);
+    // a neighbour on a Dirichlet face: its column is dropped
+    if (near && on_dirichlet(c.bnd_table, N, i + kStencilD[d][0], j + kStencilD[d][1], k + kStencilD[d][2]))
+      v = make_float2(0.0f, 0.0f);
+    df_fma(acc, __ldg(w + d), v);
+  }
+  ym[p] = float_to_double_bits(acc.x) + float_to_double_bits(acc.y);
+}
+
 // The register-climbing P1 FP32 kernel (p1_climb_f32_kernel) stops below the top kP1ClimbTop - 1
 // planes, where rows are too short for its unchecked windows; p1_face_slice writes those points.
 constexpr int kP1ClimbTop = 10;
@@ -1307,6 +1425,23 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
   if (op->kind == HHG_DIFFUSION && op->degree == 1 && op->coeff.type == HHG_COEFF_CONST) {
     (void)V;
     const Interface* I = op->itf;
+    if (sizeof(T) == 8 && op->d_p1df) {
+      // FP64 vectors in double-float arithmetic: split x once, then the stencil on the FP32 pipes
+      const int64_t n = op->npts;
+      split_double_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+          n, (const double*)x, (float2*)op->d_p1df_x);
+      dim3 grid((unsigned)I->ncta, nm);
+      if (op->bc == HHG_DIRICHLET)
+        p1_gather_df_kernel<true><<<grid, 256, 0, s>>>((const OpConst<double>*)op->d_const64, (const float2*)op->d_p1df,
+                                                       I->d_cta_plane, I->d_cta_start, I->d_pstart, (const double*)x,
+                                                       (const float2*)op->d_p1df_x, (double*)y);
+      else
+        p1_gather_df_kernel<false><<<grid, 256, 0, s>>>((const OpConst<double>*)op->d_const64, (const float2*)op->d_p1df,
+                                                        I->d_cta_plane, I->d_cta_start, I->d_pstart, (const double*)x,
+                                                        (const float2*)op->d_p1df_x, (double*)y);
+      HHG_CUDA_TRY(cudaGetLastError());
+      return HHG_OK;
+    }
     if (sizeof(T) == 8) {
       // FP64: the FP64 pipe bounds the apply; one point per thread keeps the most warps in flight
       dim3 grid((unsigned)I->ncta, nm);
@@ -1394,6 +1529,8 @@ hhg_op::~hhg_op() {
   cudaFree(d_p2idx);
   cudaFree(d_elem);
   cudaFree(d_face);
+  cudaFree(d_p1df);
+  cudaFree(d_p1df_x);
 }
 
 static int check_dtype(int dtype) {
@@ -1571,6 +1708,44 @@ extern "C" int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, 
   HHG_TRY(alloc_face_scratch(op.get()));
   HHG_TRY(noalloc_prepare());
   *out = op.release();
+  return HHG_OK;
+}
+
+extern "C" int hhg_op_set_fp64_arith(hhg_op_t* op, int mode) {
+  clear_error();
+  if (!op) return fail(HHG_E_ARG, "set_fp64_arith: null op");
+  if (mode != HHG_FP64_NATIVE && mode != HHG_FP64_DOUBLE_FLOAT) return fail(HHG_E_ARG, "set_fp64_arith: bad mode");
+  if (mode == HHG_FP64_NATIVE) {
+    if (op->d_p1df) {
+      HHG_CUDA_TRY(cudaDeviceSynchronize());   // no apply in flight may still read them
+      cudaFree(op->d_p1df);
+      cudaFree(op->d_p1df_x);
+    }
+    op->d_p1df = op->d_p1df_x = nullptr;
+    return HHG_OK;
+  }
+  if (!(op->kind == HHG_DIFFUSION && op->degree == 1 && op->coeff.type == HHG_COEFF_CONST))
+    return fail(HHG_E_UNSUPPORTED, "set_fp64_arith: double-float arithmetic exists for P1 constant-coefficient "
+                                   "diffusion only");
+  if (op->d_p1df) return HHG_OK;
+  // stencil weights split into FP32 pairs per macro, and the scratch of the split input vector
+  const int nm = op->mesh->nmacro();
+  std::vector<float2> w(16 * (size_t)nm, make_float2(0.0f, 0.0f));
+  for (int m = 0; m < nm; ++m)
+    for (int d = 0; d < 15; ++d) {
+      const double v = op->h_const[m].S[d];
+      const float hi = (float)v;
+      w[16 * m + d] = make_float2(hi, (float)(v - (double)hi));
+    }
+  void *dw = nullptr, *dx = nullptr;
+  HHG_CUDA_TRY(cudaMalloc(&dw, sizeof(float2) * w.size()));
+  if (cudaMalloc(&dx, sizeof(float2) * (size_t)op->npts) != cudaSuccess) {
+    cudaFree(dw);
+    return fail(HHG_E_OOM, "set_fp64_arith: no device memory for the split vector");
+  }
+  HHG_CUDA_TRY(cudaMemcpy(dw, w.data(), sizeof(float2) * w.size(), cudaMemcpyHostToDevice));
+  op->d_p1df = dw;
+  op->d_p1df_x = dx;
   return HHG_OK;
 }
 

@@ -33,6 +33,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--op", default="apply", choices=["apply", "adjoint", "diagonal", "mg"])
     ap.add_argument("--mixed", type=int, default=1, help="--op mg: FP32 cycles inside FP64 refinement (1) or all FP64 (0)")
+    ap.add_argument("--fp64-arith", default="native", choices=["native", "double_float"],
+                    help="arithmetic of FP64 applies (double_float: P1 constant coefficient only)")
     args = ap.parse_args()
 
     import torch
@@ -67,6 +69,8 @@ def main():
         args.degree = 2
     else:
         op = hhg.Operator(mesh, kind=args.kind, degree=args.degree, coeff=coeff, bc=args.bc, quad_degree=qd)
+        if args.fp64_arith != "native":
+            op.set_fp64_arith(args.fp64_arith)
     ncomp = 3 if args.kind == "epsilon" else 1
     n = mesh.vec_size(args.degree) * ncomp * args.nrhs
     x = torch.from_numpy(W.uniform(n, seed=0)).to("cuda", dt)

@@ -170,3 +170,53 @@ def test_p1_const_f32_unaligned_view():
     ref = OA.diffusion_matrix(c.S, ("const", 1.0), 2, "dirichlet") @ xg.astype(np.float32).astype(np.float64)
     got, spread = c.unpack(ybuf[1:])
     assert rel_err(got, ref) <= 1e-5 and spread == 0.0
+
+
+@pytest.mark.parametrize("meshname,level", [("reference_tet", 4), ("reference_tet", 6), ("cube6", 3), ("cube48", 2),
+                                            ("cuboid36", 2)])
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_p1_const_double_float_parity(meshname, level, bc):
+    """FP64 vectors with the arithmetic in FP32 pairs (48 significant bits) meet the FP64 tolerance
+    against the oracle; switching back to native FP64 gives the FP64 kernel's result again."""
+    from gpu_helpers import Case, rel_err
+    import paper_2404_08371_gb300 as hhg
+    c = Case(meshname, level, 1)
+    op = hhg.Operator(c.mesh, degree=1, coeff=("const", 1.7), bc=bc)
+    xg = W.uniform(c.S.ndof, seed=7)
+    x = c.packed(xg)
+    y_native = op.apply(x).clone()
+    y = op.set_fp64_arith("double_float").apply(x)
+    ref = OA.diffusion_matrix(c.S, ("const", 1.7), 2, bc) @ xg
+    got, spread = c.unpack(y)
+    assert rel_err(got, ref) <= 1e-12, rel_err(got, ref)
+    assert spread == 0.0
+    assert torch.equal(op.set_fp64_arith("native").apply(x), y_native)
+
+
+def test_p1_const_double_float_level9_sampled():
+    """The double-float apply at the bench's size (level 9, 22.6 M points): sampled rows against the
+    oracle at the FP64 tolerance."""
+    import paper_2404_08371_gb300 as hhg
+    v, t = W.reference_tet()
+    level = 9
+    N = 2 ** level
+    mesh = hhg.Mesh(v, t, level)
+    op = hhg.Operator(mesh, degree=1, coeff=("const", 1.0), bc="dirichlet").set_fp64_arith("double_float")
+    n = mesh.vec_size(1)
+    xp = W.uniform(n, seed=11)
+    y = op.apply(torch.tensor(xp, device="cuda")).cpu().numpy()
+    pts = OM.lattice_points(N)
+    rng = np.random.default_rng(12)
+    near = np.nonzero((pts.min(axis=1) <= 1) | (pts.sum(axis=1) >= N - 1))[0]
+    sample = np.concatenate([rng.choice(n, 400, replace=False), rng.choice(near, 200, replace=False)])
+    ref = OA.sampled_diffusion_rows(v[t[0]], level, 1, ("const", 1.0), 2, "dirichlet", xp, pts[sample])
+    assert np.abs(y[sample] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_double_float_refused_for_other_operators():
+    import paper_2404_08371_gb300 as hhg
+    v, t = W.reference_tet()
+    mesh = hhg.Mesh(v, t, 2)
+    op = hhg.Operator(mesh, degree=2, coeff=("const", 1.0), bc="dirichlet")
+    with pytest.raises(RuntimeError, match="P1 constant"):
+        op.set_fp64_arith("double_float")
