@@ -79,8 +79,7 @@ def capture(leg: str) -> dict:
     return {"bytes_per_launch": int(tot["dram__bytes_read.sum"] + tot["dram__bytes_write.sum"]),
             "read": int(tot["dram__bytes_read.sum"]), "write": int(tot["dram__bytes_write.sum"]),
             "ncu_ms": tot["gpu__time_duration.sum"], "kernel": " + ".join(n.split("(")[0] for n in names),
-            "workload": workload, "sources": files, "sources_sha256": sources_sha256(files),
-            "summary": "profiles/dram_traffic_per_kernel.md"}
+            "workload": workload, "sources": files, "sources_sha256": sources_sha256(files)}
 
 
 def main(argv):
