@@ -249,8 +249,11 @@ __device__ __forceinline__ void sincos2pi<float>(float x, float* s, float* c) {
 
 // AFF (P2, variable coefficient, APPLY): affine gradient + moment test (rules of many points) or the
 // tabulated direct form (rules of few points).
+// The stored variant streams its local matrices from HBM: two CTAs per SM (at most 128 registers a
+// thread) keep enough loads in flight; the variants that compute their matrices keep one CTA per SM
+// and all the registers they ask for.
 template <typename T, int R, int COEF, int MODE, bool DIR, bool AFF = true, bool JATOM = false>
-__global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __restrict__ cst,
+__global__ void __launch_bounds__(32 * kWarps, COEF == kCoefStored ? 2 : 1) march_kernel(const OpConst<T>* __restrict__ cst,
                                                             const int4* __restrict__ tasks, int kChunk,
                                                             const T* __restrict__ x, const T* __restrict__ g,
                                                             const T* __restrict__ kf, T* __restrict__ out,
@@ -286,7 +289,8 @@ __global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __
   const int64_t base = c.base;
   const uint32_t table = c.bnd_table;
   // owned local index ranges in i (lanes) and j (warps)
-  // (JATOM: lane 0 also owns its low face and lane 31 its high face, both added atomically)
+  // (JATOM: lane 0 also owns its low face and lane 31 its high face, shared with the neighbouring
+  // tiles through the face scratch)
   const int a_lo = lane == 0 ? (JATOM ? 0 : R) : 1, a_hi = (lane == 31 && !JATOM) ? R - 1 : R;
   const int b_lo = warp == 0 ? (JATOM ? 0 : R) : 1, b_hi = (warp == kWarps - 1 && !JATOM) ? R - 1 : R;
 
