@@ -86,7 +86,8 @@ struct Interface {
   int64_t n_march_tasks = 0;
   int march_kchunk = 32;
   // task lists of the plane-tile kernels: (i-chunk, row group, k-chunk, macro), heaviest first;
-  // tile[0] for chunks of 128 points along i, tile[1] for chunks of 64
+  // tile[0]: chunks of 128 points along i on one macro (launched once per macro), tile[1]: chunks
+  // of 64 on all macros (one launch)
   TileTasks tile[2];
   ~Interface();
 };
@@ -94,9 +95,9 @@ struct Interface {
 // Tile shape of the marching kernels (march.cu): 32 lanes along i, kMarchWarps warps along j,
 // march_kchunk cube layers along k.  Below kMarchJAtomicN cubes per edge the tiles overlap their
 // neighbours below by one cube in i and j (31 x (kMarchWarps - 1) owned) and every point is stored
-// once; from kMarchJAtomicN on all 32 x kMarchWarps columns of cubes are the tile's own and the
-// points on the tile's i- and j-faces are summed into the zeroed output with atomic adds (no cube is
-// integrated twice along i or j).
+// once; from kMarchJAtomicN on all 32 x kMarchWarps columns of cubes are the tile's own (no cube is
+// integrated twice along i or j) and the points on the tile's i- and j-faces get partial sums from
+// two or four tiles, added in a fixed order by march_finish_kernel (march_kernel.cuh).
 constexpr int kMarchWarps = 8;
 constexpr int kMarchJAtomicN = 64;
 __host__ __device__ constexpr int march_iw(int n) { return n >= kMarchJAtomicN ? 32 : 31; }
@@ -127,7 +128,7 @@ struct hhg_mesh {
   size_t scratch_bytes = 0;
   int nmacro() const { return (int)macros.size(); }
   int interface(int level, int degree, const hhg::Interface** out);
-  int build_tile_tasks(int64_t N, int64_t iw, int64_t jw, hhg::TileTasks* out) const;
+  int build_tile_tasks(int64_t N, int64_t iw, int64_t jw, int copies, int64_t min_tasks, hhg::TileTasks* out) const;
   int scratch_reserve(size_t bytes);
   ~hhg_mesh();
 };
@@ -222,11 +223,6 @@ int launch_l2_error(const struct ::hhg_op* op, const double* uh, double* partial
 }  // namespace hhg
 
 namespace hhg {
-// Hoisted per-class data of the Nedelec operator (one block per macro), in the macro's canonical
-// edge orientation (the local orientation a -> b times s_e = +-1, folded into the entries) and
-// stored as the upper triangle e <= f (index n1_sym(e, f)):
-//   C[o][.] = s_e s_f |T| curl phi_e . curl phi_f   (curl phi_e = 2 grad l_a x grad l_b, constant)
-//   M[o][v][.] = s_e s_f int_T lambda_v phi_e . phi_f  (exact)
 // P2 constant-coefficient stencils: the row of a point of the doubled lattice is fixed by the
 // parity (I & 1, J & 1, K & 1) of its coordinates and by the macro faces it lies on (zero mask z).
 // The 8 parities have 65, 27, 19, 27, 27, 19, 27, 19 structural neighbours (230 in all); entry d of
@@ -241,7 +237,17 @@ template <typename T>
 struct alignas(16) P2Stencil {
   T w[16][kP2StTotal];
 };
+// The FP32 weights of the rows off the macro faces (mask 0) of one macro, passed by value to the
+// FP32 plane-tile kernel so that its FMAs read them from the kernel's parameter bank.
+struct P2ParamW {
+  float w[kP2StTotal];
+};
 
+// Hoisted per-class data of the Nedelec operator (one block per macro), in the macro's canonical
+// edge orientation (the local orientation a -> b times s_e = +-1, folded into the entries) and
+// stored as the upper triangle e <= f (index n1_sym(e, f)):
+//   C[o][.] = s_e s_f |T| curl phi_e . curl phi_f   (curl phi_e = 2 grad l_a x grad l_b, constant)
+//   M[o][v][.] = s_e s_f int_T lambda_v phi_e . phi_f  (exact)
 constexpr int kN1Sym = 21;
 __host__ __device__ constexpr int n1_sym(int e, int f) { return e * 6 - e * (e - 1) / 2 + (f - e); }
 template <typename T>
@@ -260,6 +266,7 @@ struct hhg_op {
   void* d_p2st64 = nullptr;  // P2Stencil<double>[nmacro] (P2 constant-coefficient diffusion)
   void* d_p2st32 = nullptr;
   void* d_p2idx = nullptr;   // P2StencilIndex (structural neighbour lists)
+  std::vector<hhg::P2ParamW> h_p2w32;   // per macro: FP32 weights of the rows off the faces
   // stored local matrices (hhg_op_store_element_matrices): [macro][class][entry][cube], cube =
   // packed index of its origin in the lattice of resolution 2^level - 1; entries 55 (P2) or 1 (P1)
   void* d_elem = nullptr;
@@ -276,12 +283,12 @@ struct hhg_op {
   hhg::QuadRule rule;
   std::vector<hhg::OpConst<double>> h_const;
   const hhg::Interface* itf = nullptr;   // per-level data of the op's space (owned by the mesh)
-  // partial sums of the points shared by marching tiles (lattices of at least kMarchJAtomicN cubes
-  // per edge; march_kernel.cuh, FaceScratch): FP64-sized, per macro face_S slots
   // P1 constant diffusion, FP64 vectors in double-float arithmetic (ops.cu): the stencil weights as
   // FP32 pairs (float2[16] per macro) and the split input vector (float2[npts])
   void* d_p1df = nullptr;
   void* d_p1df_x = nullptr;
+  // partial sums of the points shared by marching tiles (lattices of at least kMarchJAtomicN cubes
+  // per edge; march_kernel.cuh, FaceScratch): FP64-sized, per macro face_S slots
   void* d_face = nullptr;
   int64_t face_S = 0, face_Si = 0, face_Sj = 0;
   int face_Ti = 0, face_Tj = 0;

@@ -365,8 +365,10 @@ extern "C" int hhg_mesh_destroy(hhg_mesh_t* mesh) {
 
 // Build (once) the interface groups of (level, degree).
 // Tasks of a plane-tile kernel on one macro lattice of resolution N: tiles of iw points along i
-// and jw rows, k-chunks halved until the list (times the macros) fills the GPU, heaviest first.
-int hhg_mesh::build_tile_tasks(int64_t N, int64_t iw, int64_t jw, TileTasks* out) const {
+// and jw rows, k-chunks (from 32) halved until the list (times the macros it holds) has min_tasks
+// tasks, heaviest first.  copies: the macros the list holds (nmacro() for one launch over all
+// macros, 1 for a launch per macro, whose tasks then carry macro 0).
+int hhg_mesh::build_tile_tasks(int64_t N, int64_t iw, int64_t jw, int copies, int64_t min_tasks, TileTasks* out) const {
   int kch = 32;
   std::vector<std::pair<int64_t, int4>> tasks;
   for (;;) {
@@ -382,11 +384,11 @@ int hhg_mesh::build_tile_tasks(int64_t N, int64_t iw, int64_t jw, TileTasks* out
             }
           tasks.push_back({work, int4{(int)tx, (int)ty, (int)kc, 0}});
         }
-    if (kch <= 4 || (int64_t)tasks.size() * nmacro() >= 8 * 152) break;
+    if (kch <= 4 || (int64_t)tasks.size() * copies >= min_tasks) break;
     kch /= 2;
   }
   std::vector<std::pair<int64_t, int4>> all;
-  for (int mac = 0; mac < nmacro(); ++mac)
+  for (int mac = 0; mac < copies; ++mac)
     for (auto& t : tasks) all.push_back({t.first, int4{t.second.x, t.second.y, t.second.z, mac}});
   std::stable_sort(all.begin(), all.end(), [](const std::pair<int64_t, int4>& a, const std::pair<int64_t, int4>& b) {
     return a.first > b.first;
@@ -556,8 +558,10 @@ int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
     HHG_CUDA_TRY(cudaMemcpy(I->d_march_tasks, tv.data(), sizeof(int4) * tv.size(), cudaMemcpyHostToDevice));
   }
   // plane-tile kernel tasks: (i-chunk, row group, k-chunk), sorted by their number of points
-  HHG_TRY(build_tile_tasks(N, 128, kStencilWarps, &I->tile[0]));
-  HHG_TRY(build_tile_tasks(N, 64, kStencilWarps, &I->tile[1]));
+  // the per-macro list of the two-plane FP32 P2 kernel: longer k-chunks (its 8-plane prologue is paid
+  // once per task) for about 4 tasks per SM; the others about 8 per SM
+  HHG_TRY(build_tile_tasks(N, 128, kStencilWarps, 1, 4 * 152, &I->tile[0]));
+  HHG_TRY(build_tile_tasks(N, 64, kStencilWarps, nmacro(), 8 * 152, &I->tile[1]));
   I->h_ptr = ptr;
   I->h_idx = idx;
   I->h_bnd = bnd;

@@ -890,8 +890,8 @@ __global__ void __launch_bounds__(256, PT == 4 ? 2 : 3) p1_climb_f32_kernel(cons
 }
 
 // ---------------------------------------------------------------------------
-// P2 constant-coefficient apply from shared-memory plane tiles.  A CTA owns rows j0..j0+7 and
-// points i0..i0+TI-1 of a k-chunk and climbs its planes.  Each plane of the tile plus a halo of two
+// P2 constant-coefficient apply in FP64 from shared-memory plane tiles (FP32: p2_quad_f32_kernel
+// below).  A CTA owns rows j0..j0+7 and points i0..i0+TI-1 of a k-chunk and climbs its planes.  Each plane of the tile plus a halo of two
 // points (the reach of a P2 row) is staged with cp.async into a ring of planes, kP2Ahead planes
 // beyond the k+2 that the plane k being computed needs; staged Dirichlet points are zeroed on
 // arrival.  A lane evaluates the points i0 + 64 v + 2 lane + {0, 1}: both node parities of its row,
@@ -904,12 +904,9 @@ constexpr int kP2TileH = kP2TileJ + 4;
 constexpr int kP2Ahead = 2;
 constexpr int kP2Ring = kP2Ahead + 5;   // planes k-2 .. k+2+kP2Ahead; one barrier per plane
 
-template <typename T>
-struct P2W;
-
 template <typename T, int TI>
 constexpr size_t p2_tile_smem() {
-  return sizeof(T) * kP2Ring * (TI + 4) * kP2TileH + sizeof(typename P2W<T>::type) * kP2StTotal;
+  return sizeof(T) * kP2Ring * (TI + 4) * kP2TileH + sizeof(T) * kP2StTotal;
 }
 
 __host__ __device__ constexpr int p2_scol(int c, int W) { return (c & 1) * (W / 2) + (c >> 1); }
@@ -972,68 +969,30 @@ __device__ __forceinline__ void p2_mask_plane(T* slot, int N, uint32_t table, in
   }
 }
 
-// Weights of the interior rows in shared memory: FP32 weights stored twice (w, w), so that one
-// 8-byte load feeds a packed FMA over the lane's two points 64 apart.
-template <typename T>
-struct P2W {
-  using type = T;
-};
-template <>
-struct P2W<float> {
-  using type = float2;
-};
-
 // Cell C of the union list of row parity PA (even point) for the lane; ob = r W + 1 + lane.
 template <typename T, int W, int NV, int PA, int C>
-__device__ __forceinline__ void p2_tile_cell(const typename P2W<T>::type* w, const T* const (&pl)[5], int ob,
-                                             T (&a0)[NV], T (&a1)[NV]) {
+__device__ __forceinline__ void p2_tile_cell(const T* w, const T* const (&pl)[5], int ob, T (&a0)[NV], T (&a1)[NV]) {
   constexpr int O = P2UCell<PA, C>::off, IA = P2UCell<PA, C>::ia, IB = P2UCell<PA, C>::ib;
   constexpr int dx = (O & 15) - 2, dy = ((O >> 4) & 15) - 2, dz = ((O >> 8) & 15) - 2;
   constexpr int off = dy * W + (dx & 1) * (W / 2) + ((dx + 4) >> 1) - 2;   // staged column 2 + 2 lane + dx
   const T* p = pl[dz + 2] + ob + off;
-  if constexpr (std::is_same<T, float>::value && NV == 2) {
-    const float2 xv = make_float2(p[0], p[32]);
-    if constexpr (IA >= 0) {
-      float2 acc = make_float2(a0[0], a0[1]);
-      acc = __ffma2_rn(w[P2Start<PA>::v + IA], xv, acc);
-      a0[0] = acc.x;
-      a0[1] = acc.y;
-    }
-    if constexpr (IB >= 0) {
-      float2 acc = make_float2(a1[0], a1[1]);
-      acc = __ffma2_rn(w[P2Start<PA | 1>::v + IB], xv, acc);
-      a1[0] = acc.x;
-      a1[1] = acc.y;
-    }
-  } else {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T xv = p[32 * v];
-      if constexpr (IA >= 0) {
-        if constexpr (std::is_same<T, float>::value)
-          a0[v] += w[P2Start<PA>::v + IA].x * xv;
-        else
-          a0[v] += w[P2Start<PA>::v + IA] * xv;
-      }
-      if constexpr (IB >= 0) {
-        if constexpr (std::is_same<T, float>::value)
-          a1[v] += w[P2Start<PA | 1>::v + IB].x * xv;
-        else
-          a1[v] += w[P2Start<PA | 1>::v + IB] * xv;
-      }
-    }
+  for (int v = 0; v < NV; ++v) {
+    const T xv = p[32 * v];
+    if constexpr (IA >= 0) a0[v] += w[P2Start<PA>::v + IA] * xv;
+    if constexpr (IB >= 0) a1[v] += w[P2Start<PA | 1>::v + IB] * xv;
   }
 }
 
 template <typename T, int W, int NV, int PA, int... C>
-__device__ __forceinline__ void p2_tile_cells(const typename P2W<T>::type* w, const T* const (&pl)[5], int ob,
+__device__ __forceinline__ void p2_tile_cells(const T* w, const T* const (&pl)[5], int ob,
                                               T (&a0)[NV], T (&a1)[NV], std::integer_sequence<int, C...>) {
   (p2_tile_cell<T, W, NV, PA, C>(w, pl, ob, a0, a1), ...);
 }
 
 // Interior rows of parities PA (even i) and PA | 1 (odd i) over the union of their cells.
 template <typename T, int W, int NV, int PA>
-__device__ __forceinline__ void p2_tile_pair(const typename P2W<T>::type* w, const T* const (&pl)[5], int ob,
+__device__ __forceinline__ void p2_tile_pair(const T* w, const T* const (&pl)[5], int ob,
                                              T (&a0)[NV], T (&a1)[NV]) {
   p2_tile_cells<T, W, NV, PA>(w, pl, ob, a0, a1, std::make_integer_sequence<int, P2UCnt<PA>::v>{});
 }
@@ -1041,7 +1000,7 @@ __device__ __forceinline__ void p2_tile_pair(const typename P2W<T>::type* w, con
 // Interior points of one tile row (row parity PA): the second half of a 128-point tile only when
 // the row reaches into it.  Points on macro faces are left to p2_face_point.
 template <typename T, int W, int NV, int PA>
-__device__ __forceinline__ void p2_tile_row(const typename P2W<T>::type* w, const T* const (&pl)[5], int ob, int i0,
+__device__ __forceinline__ void p2_tile_row(const T* w, const T* const (&pl)[5], int ob, int i0,
                                             int len, T* __restrict__ yrow) {
   const int lane = threadIdx.x & 31;
   if (NV == 2 && len - i0 <= 64) {
@@ -1141,22 +1100,16 @@ __global__ void __launch_bounds__(256) p2_tile_kernel(const OpConst<T>* __restri
     p2_face_point<T, DIRICHLET>(cst[macro], st[macro], offs, starts, pstart, x, y, f, (r - f * nfb) * 256 + threadIdx.x);
     return;
   }
-  using WT = typename P2W<T>::type;
+  static_assert(std::is_same<T, double>::value, "FP32 runs p2_quad_f32_kernel");
   T* buf = reinterpret_cast<T*>(p2_tile_smem_raw);
-  WT* w0 = reinterpret_cast<WT*>(buf + kP2Ring * SLOT);
+  T* w0 = buf + kP2Ring * SLOT;
   const int4 task = tasks[blockIdx.x];
   const OpConst<T>& c = cst[task.w];
   const int N = c.N;
   const int i0 = task.x * TI, j0 = task.y * kP2TileJ, k0 = task.z * kch;
   const int k_end = min(k0 + kch - 1, N - j0 - i0);
   if (k_end < k0) return;   // uniform over the CTA
-  for (int t = threadIdx.x; t < kP2StTotal; t += blockDim.x) {
-    const T wt = st[task.w].w[0][t];
-    if constexpr (std::is_same<T, float>::value)
-      w0[t] = make_float2(wt, wt);
-    else
-      w0[t] = wt;
-  }
+  for (int t = threadIdx.x; t < kP2StTotal; t += blockDim.x) w0[t] = st[task.w].w[0][t];
   const uint32_t table = c.bnd_table;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const T* __restrict__ xm = x + c.base;
@@ -1204,6 +1157,377 @@ __global__ void __launch_bounds__(256) p2_tile_kernel(const OpConst<T>* __restri
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------
+// P2 constant-coefficient apply in FP32, two planes per step, weights in the parameter bank.  The
+// launch covers one macro; its 230 interior weights come by value (P2ParamW), so every FMA takes its
+// weight from the constant bank and no load feeds it.  The tiles and the staging are those of
+// p2_tile_kernel (8 rows x 128 points plus a halo of two, even and odd columns apart), but a step
+// evaluates the planes k and k+1 together: a lane's four points (even and odd i, planes k and k+1)
+// share the union of their cells, which is loaded from shared memory once (2.8 x fewer loads per
+// point than one plane at a time).  The ring holds 10 planes: at step k the planes k-2 .. k+3 are
+// read, k+4 and k+5 (landed) get their Dirichlet points zeroed, k+6 and k+7 are being copied; one
+// barrier per step.
+constexpr int kP2QRing = 10;
+constexpr size_t kP2QSmem = sizeof(float) * kP2QRing * (128 + 4) * kP2TileH;   // 63,360 bytes
+
+// Union of the cells of the four points of a lane in one step, as offsets from the even point of
+// plane k (packed (dx+2) | (dy+2) << 4 | (dz+2) << 8, dx in -2..3, dz in -2..3), sorted; e[c][q]:
+// the entry of point q's stencil that uses cell c (-1: none).  q = 0 / 1: even / odd point of
+// plane k (parities PA, PA | 1), q = 2 / 3: the same on plane k+1 (parities PA ^ 4, (PA ^ 4) | 1).
+struct P2QuadList {
+  int n;
+  int off[128];
+  int e[128][4];
+};
+__host__ __device__ constexpr int p2q_par(int pa, int q) { return ((q & 2) ? (pa ^ 4) : pa) | (q & 1); }
+__host__ __device__ constexpr P2QuadList p2_quad_list(int pa) {
+  P2QuadList U{};
+  for (int q = 0; q < 4; ++q) {
+    const P2OffList L = p2_struct_list(p2q_par(pa, q));
+    for (int d = 0; d < L.n; ++d) {
+      const int v = L.off[d] + (q & 1) + ((q >> 1) << 8);   // dx + 1 for the odd point, dz + 1 for plane k+1
+      int pos = 0;
+      while (pos < U.n && U.off[pos] < v) ++pos;
+      if (!(pos < U.n && U.off[pos] == v)) {
+        for (int t = U.n; t > pos; --t) {
+          U.off[t] = U.off[t - 1];
+          for (int r = 0; r < 4; ++r) U.e[t][r] = U.e[t - 1][r];
+        }
+        U.off[pos] = v;
+        for (int r = 0; r < 4; ++r) U.e[pos][r] = -1;
+        ++U.n;
+      }
+      U.e[pos][q] = d;
+    }
+  }
+  return U;
+}
+template <int PA>
+struct P2QCnt {
+  static constexpr int v = p2_quad_list(PA).n;
+};
+template <int PA, int C>
+struct P2QCell {
+  static constexpr P2QuadList L = p2_quad_list(PA);   // host-side constant only, read below
+  static constexpr int off = L.off[C];
+  static constexpr int e0 = L.e[C][0], e1 = L.e[C][1], e2 = L.e[C][2], e3 = L.e[C][3];
+};
+// first weight of parity p in the 230-entry list
+__host__ __device__ constexpr int p2_start(int p) {
+  int s = 0;
+  for (int t = 0; t < p; ++t) s += p2_struct_list(t).n;
+  return s;
+}
+template <int PA, int Q>
+struct P2QStart {
+  static constexpr int v = p2_start(p2q_par(PA, Q));
+};
+
+// Staging plan of p2_quad_f32_kernel.  A plane of the tile is 12 rows of W = 132 columns, 5 chunks
+// of 32 columns per row (the last one 4 wide).  Warp w copies row w whole (h = 0) and chunks 0-2
+// (w < 4) or 3-4 (w >= 4) of row 8 + (w & 3) (h = 1), 7 to 8 chunks per warp.  Per row the plan keeps
+// what does not change from plane to plane: the row j, the packed offset of its column 0 without
+// the plane terms, and the column limit, so that plane kk costs one multiply-add per row:
+// start(j, kk) = pstart[kk] + row32(N - kk, j) = pstart[kk] + j (2N + 3 - j) / 2 - j kk.
+struct P2QStage {
+  int jr[2];        // row j of the staged row (h = 0, 1)
+  int off[2];       // j (2N + 3 - j) / 2 + i0 - 2 + lane: add pstart[kk] - j kk
+  int lim[2];       // N - j + 3 - i0: staged column col < lim - kk lies inside the row (very negative
+                    // for rows j < 0)
+  unsigned dst[2];  // shared address of the lane's column in ring slot 0
+  int r[2];
+};
+
+__device__ __forceinline__ bool p2q_mine(int h, int t, int warp) { return h == 0 || ((warp < 4) == (t < 3)); }
+
+template <int TI>
+__device__ __forceinline__ P2QStage p2q_plan(float* buf, int N, int i0, int j0) {
+  constexpr int W = TI + 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int s0 = (lane & 1) * (W / 2) + (lane >> 1);
+  P2QStage st;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = h == 0 ? warp : 8 + (warp & 3);
+    const int jr = j0 - 2 + r;
+    st.r[h] = r;
+    st.jr[h] = jr;
+    st.off[h] = ((jr * (2 * N + 3 - jr)) >> 1) + i0 - 2 + lane;
+    st.lim[h] = jr >= 0 ? N - jr + 3 - i0 : -(1 << 30);
+    st.dst[h] = (unsigned)__cvta_generic_to_shared(buf + r * W + s0);
+  }
+  return st;
+}
+
+// Chunk T of a staged row: columns lane + 32 T, at byte offsets 64 T (shared) and 128 T (global).
+template <int T>
+__device__ __forceinline__ void p2q_copy(unsigned dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0+%2], [%1+%3], 4;\n" ::"r"(dst), "l"(src), "n"(64 * T), "n"(128 * T));
+}
+
+// Copy plane kk (first packed position pk) into ring slot `slot` by the plan.  Columns outside the
+// row (before i = 0, after i = len - 1) feed only points the tile does not store, so a row whose
+// window of W values lies inside the vector (packed offsets gmin .. gmax of its first value) is
+// copied whole without tests; only rows at the two ends of the vector test each column.
+template <int TI>
+__device__ __forceinline__ void p2q_issue_plane(const P2QStage& st, int slot, const float* __restrict__ xm, int pk,
+                                                int N, int i0, int kk, int gmin, int gmax) {
+  constexpr int W = TI + 4;
+  constexpr unsigned SLOT_BYTES = sizeof(float) * W * kP2TileH;
+  static_assert((W + 31) / 32 == 5 && W - 128 == 4, "five chunks per staged row, the last 4 columns wide");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (kk < 0 || kk > N) return;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int jr = st.jr[h];
+    const int lim = st.lim[h] - kk;   // staged column col holds i = i0 - 2 + col < len
+    if (lim + i0 - 2 <= 0) continue;  // no row (j < 0 or beyond the plane)
+    const int g = pk - jr * kk + st.off[h] - lane;   // packed offset of column 0
+    const float* __restrict__ src = xm + (g + lane);
+    const unsigned dst = st.dst[h] + slot * SLOT_BYTES;
+    const bool lo = h == 0 || warp < 4, hi = h == 0 || warp >= 4;   // chunks 0-2 / 3-4 of this warp
+    if (g >= gmin && g <= gmax) {
+      if (lo) {
+        p2q_copy<0>(dst, src);
+        p2q_copy<1>(dst, src);
+        p2q_copy<2>(dst, src);
+      }
+      if (hi) {
+        p2q_copy<3>(dst, src);
+        if (lane < 4) p2q_copy<4>(dst, src);
+      }
+    } else {
+#pragma unroll 1
+      for (int t = lo ? 0 : 3; t < (hi ? 5 : 3); ++t) {
+        const int col = lane + 32 * t;
+        if (col < W && col < lim && col + i0 >= 2) {
+          const unsigned sa = dst + 64 * t;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + 32 * t));
+        }
+      }
+    }
+  }
+}
+
+// Dirichlet points of staged planes, zeroed once the copies are visible to the whole CTA (after a
+// barrier, before the barrier that precedes their first read).  A row with j, k >= 1 meets the
+// macro faces only at i = 0 (zero set {i}, or {i, diagonal} for a row of one point) and i = len - 1
+// ({diagonal}, or {i, diagonal}): one thread per (plane, row, end) checks and zeroes that point.
+// Rows j = 0 and k = 0 lie on a face: a warp looks up each of their points (p2q_mask_face_row).
+template <int TI>
+__device__ __forceinline__ void p2q_mask_end(float* buf, int slot, int N, uint32_t table, int i0, int j0, int kk, int r,
+                                             int end) {
+  constexpr int W = TI + 4;
+  const int jr = j0 - 2 + r;
+  const int len = N - jr - kk + 1;
+  if (jr < 1 || kk < 1 || len < 1) return;
+  const bool one = len == 1;
+  const int col = end == 0 ? 2 - i0 : len + 1 - i0;   // column of i = 0 / i = len - 1
+  const bool dir = (table >> (one ? 3 : (end == 0 ? 2 : 1))) & 1u;
+  if (dir && (unsigned)col < (unsigned)W) buf[slot * (W * kP2TileH) + r * W + p2_scol(col, W)] = 0.0f;
+}
+
+template <int TI>
+__device__ __forceinline__ void p2q_mask_face_row(float* buf, int slot, int N, uint32_t table, int i0, int j0, int kk,
+                                                  int r) {
+  constexpr int W = TI + 4;
+  const int lane = threadIdx.x & 31;
+  const int jr = j0 - 2 + r;
+  const int len = N - jr - kk + 1;
+  if (jr < 0 || kk < 0 || len < 1 || !(jr == 0 || kk == 0)) return;
+#pragma unroll 1
+  for (int col = lane; col < W; col += 32) {
+    const int ii = i0 - 2 + col;
+    if (ii >= 0 && ii < len && on_dirichlet(table, N, ii, jr, kk)) buf[slot * (W * kP2TileH) + r * W + p2_scol(col, W)] = 0.0f;
+  }
+}
+
+template <int W, int NV, int PA, int C>
+__device__ __forceinline__ void p2q_cell(const P2ParamW& wp, const float* const (&pl)[6], int ob,
+                                         float (&acc)[4][NV]) {
+  using Cell = P2QCell<PA, C>;
+  constexpr int O = Cell::off;
+  constexpr int dx = (O & 15) - 2, dy = ((O >> 4) & 15) - 2, dz = ((O >> 8) & 15) - 2;
+  constexpr int off = dy * W + (dx & 1) * (W / 2) + ((dx + 4) >> 1) - 2;   // staged column 2 + 2 lane + dx
+  const float* p = pl[dz + 2] + ob + off;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float xv = p[32 * v];
+    if constexpr (Cell::e0 >= 0) acc[0][v] = fmaf(wp.w[P2QStart<PA, 0>::v + Cell::e0], xv, acc[0][v]);
+    if constexpr (Cell::e1 >= 0) acc[1][v] = fmaf(wp.w[P2QStart<PA, 1>::v + Cell::e1], xv, acc[1][v]);
+    if constexpr (Cell::e2 >= 0) acc[2][v] = fmaf(wp.w[P2QStart<PA, 2>::v + Cell::e2], xv, acc[2][v]);
+    if constexpr (Cell::e3 >= 0) acc[3][v] = fmaf(wp.w[P2QStart<PA, 3>::v + Cell::e3], xv, acc[3][v]);
+  }
+}
+
+template <int W, int NV, int PA, int... C>
+__device__ __forceinline__ void p2q_cells(const P2ParamW& wp, const float* const (&pl)[6], int ob, float (&acc)[4][NV],
+                                          std::integer_sequence<int, C...>) {
+  (p2q_cell<W, NV, PA, C>(wp, pl, ob, acc), ...);
+}
+
+// Points of row j on planes k (length len0) and k+1 (len0 - 1; only if wk1) for row parity PA
+// (of plane k): the interior points among i0 + 64 v + 2 lane + {0, 1}.
+template <int W, int NV, int PA>
+__device__ __forceinline__ void p2q_rows(const P2ParamW& wp, const float* const (&pl)[6], int ob, int i0, int len0,
+                                         bool wk0, bool wk1, float* __restrict__ y0, float* __restrict__ y1) {
+  const int lane = threadIdx.x & 31;
+  float acc[4][NV];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[q][v] = 0.0f;
+  p2q_cells<W, NV, PA>(wp, pl, ob, acc, std::make_integer_sequence<int, P2QCnt<PA>::v>{});
+  if (i0 > 0 && i0 + 64 * NV + 1 < len0 && wk0 && wk1) {
+    // every point of the lane on both planes is off the macro faces
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int ii = i0 + 64 * v + 2 * lane;
+      y0[ii] = acc[0][v];
+      y0[ii + 1] = acc[1][v];
+      y1[ii] = acc[2][v];
+      y1[ii + 1] = acc[3][v];
+    }
+    return;
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int ii = i0 + 64 * v + 2 * lane;
+    if (wk0) {
+      if (ii > 0 && ii < len0 - 1) y0[ii] = acc[0][v];
+      if (ii + 1 < len0 - 1) y0[ii + 1] = acc[1][v];
+    }
+    if (wk1) {
+      if (ii > 0 && ii < len0 - 2) y1[ii] = acc[2][v];
+      if (ii + 1 < len0 - 2) y1[ii + 1] = acc[3][v];
+    }
+  }
+}
+
+template <int W, int PA>
+__device__ __forceinline__ void p2q_step(const P2ParamW& wp, const float* const (&pl)[6], int ob, int i0, int len0,
+                                         bool wk0, bool wk1, float* __restrict__ y0, float* __restrict__ y1) {
+  // the second 64 points only when the longer row reaches into them
+  if (len0 - i0 <= 64)
+    p2q_rows<W, 1, PA>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1);
+  else
+    p2q_rows<W, 2, PA>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1);
+}
+
+// One macro (cm = its constants, stm = its face stencils); blocks after the tile tasks write the
+// macro's face points (4 faces x nfb blocks).
+template <bool DIRICHLET>
+__global__ void __launch_bounds__(256, 3) p2_quad_f32_kernel(const __grid_constant__ P2ParamW wp,
+                                                          const OpConst<float>* __restrict__ cm,
+                                                          const P2Stencil<float>* __restrict__ stm,
+                                                          const P2StencilIndex* __restrict__ sidx,
+                                                          const int4* __restrict__ tasks, int ntasks, int kch, int nfb,
+                                                          const int* __restrict__ pstart, const float* __restrict__ x,
+                                                          float* __restrict__ y, int64_t npts) {
+  constexpr int TI = 128;
+  constexpr int W = TI + 4;
+  constexpr int SLOT = W * kP2TileH;
+  extern __shared__ __align__(16) unsigned char p2_quad_smem_raw[];
+  if ((int)blockIdx.x >= ntasks) {
+    int* offs = reinterpret_cast<int*>(p2_quad_smem_raw);
+    int* starts = offs + kP2StTotal;
+    for (int t = threadIdx.x; t < kP2StTotal; t += blockDim.x) offs[t] = sidx->off[t];
+    if (threadIdx.x < 9) starts[threadIdx.x] = sidx->start[threadIdx.x];
+    __syncthreads();
+    const int b = blockIdx.x - ntasks;
+    const int f = b / nfb;
+    p2_face_point<float, DIRICHLET>(*cm, *stm, offs, starts, pstart, x, y, f, (b - f * nfb) * 256 + threadIdx.x);
+    return;
+  }
+  float* buf = reinterpret_cast<float*>(p2_quad_smem_raw);
+  const int4 task = tasks[blockIdx.x];
+  const OpConst<float>& c = *cm;
+  const int N = c.N;
+  const int i0 = task.x * TI, j0 = task.y * kP2TileJ, k0 = task.z * kch;
+  const int k_end = min(k0 + kch - 1, N - j0 - i0);
+  if (k_end < k0) return;   // uniform over the CTA
+  const uint32_t table = c.bnd_table;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float* __restrict__ xm = x + c.base;
+  float* __restrict__ ym = y + c.base;
+  const P2QStage st = p2q_plan<TI>(buf, N, i0, j0);
+  auto plane_start = [&](int kk) { return (kk >= 0 && kk <= N) ? __ldg(pstart + kk) : 0; };
+  // a staged row's W values (first at packed offset g of the macro) lie inside the vector
+  const int gmin = c.base >= 2 ? -2 : -(int)c.base;
+  const int gmax = (int)min(npts - c.base - W, (int64_t)INT_MAX);
+  // plane kk sits in ring slot (kk - k0 + 2) mod 10; planes k0-2 .. k0+5 first, their Dirichlet points
+  // zeroed before the first step
+#pragma unroll 1
+  for (int q = 0; q < 8; ++q) {
+    const int kk = k0 - 2 + q;
+    if (kk <= k_end + 3) p2q_issue_plane<TI>(st, q, xm, plane_start(kk), N, i0, kk, gmin, gmax);
+  }
+  cp_async_commit();
+  // a staged plane can hold points of a macro face only if the tile touches i = 0, j = 0, k = 0 or
+  // reaches i + j + k = N; only then are its Dirichlet points looked for (uniform over the CTA)
+  const bool edge_tile = i0 == 0 || j0 == 0 || i0 + TI + 1 + j0 + kP2TileJ + 1 + k_end + 3 >= N;
+  if (DIRICHLET && (edge_tile || k0 <= 2)) {
+    cp_async_wait<0>();
+    __syncthreads();
+    // 8 planes x 12 rows x 2 ends: 192 threads; the rows on a face: warp w for plane k0-2+w
+    if (threadIdx.x < 192) {
+      const int q = threadIdx.x / 24, rr = threadIdx.x % 24;
+      p2q_mask_end<TI>(buf, q, N, table, i0, j0, k0 - 2 + q, rr >> 1, rr & 1);
+    }
+    if ((j0 <= 2 || k0 <= 2) && k0 - 2 + warp <= k_end + 3) {
+#pragma unroll 1
+      for (int r = 0; r < kP2TileH; ++r) p2q_mask_face_row<TI>(buf, warp, N, table, i0, j0, k0 - 2 + warp, r);
+    }
+  }
+  const int j = j0 + warp;
+  const int ob = (warp + 2) * W + 1 + lane;
+  int sq = 0;   // ring slot of plane k - 2
+  for (int k = k0; k <= k_end; k += 2) {
+    const int q = k - k0;
+    const int pk6 = plane_start(k + 6), pk7 = plane_start(k + 7);
+    auto slot = [&](int t) { const int v = sq + t; return v >= kP2QRing ? v - kP2QRing : v; };
+    cp_async_wait<0>();   // planes up to k+5 have landed
+    __syncthreads();      // ... and are visible; planes up to k+3 have their Dirichlet points zeroed
+    if (DIRICHLET && edge_tile && q > 0) {
+      // planes k+4, k+5 (first read in step k+2)
+      if (threadIdx.x < 48) {
+        const int p = threadIdx.x / 24, rr = threadIdx.x % 24;
+        p2q_mask_end<TI>(buf, slot(6 + p), N, table, i0, j0, k + 4 + p, rr >> 1, rr & 1);
+      }
+      if (j0 <= 2 && warp >= 6) p2q_mask_face_row<TI>(buf, slot(warp), N, table, i0, j0, k + warp - 2, 2 - j0);
+    }
+    // planes k+6, k+7 into the slots of k-4, k-3, read for the last time in step k-2
+    if (k + 6 <= k_end + 3) p2q_issue_plane<TI>(st, slot(8), xm, pk6, N, i0, k + 6, gmin, gmax);
+    if (k + 7 <= k_end + 3) p2q_issue_plane<TI>(st, slot(9), xm, pk7, N, i0, k + 7, gmin, gmax);
+    cp_async_commit();
+    const int len0 = N - j - k + 1;
+    // rows j = 0 and planes k = 0 hold only points on macro faces
+    const bool wk0 = k > 0 && k <= k_end, wk1 = k + 1 <= k_end;
+    if (j > 0 && len0 > 0 && i0 < len0) {
+      const float* pl[6];
+#pragma unroll
+      for (int t = 0; t < 6; ++t) pl[t] = buf + slot(t) * SLOT;
+      float* __restrict__ y0 = ym + __ldg(pstart + k) + row32(N - k, j);
+      float* __restrict__ y1 = ym + __ldg(pstart + k + 1) + row32(N - k - 1, j);
+      switch ((j & 1) | ((k & 1) << 1)) {
+        case 0: p2q_step<W, 0>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
+        case 1: p2q_step<W, 2>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
+        case 2: p2q_step<W, 4>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
+        default: p2q_step<W, 6>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
+      }
+    }
+    sq = slot(2);
+  }
+  cp_async_wait<0>();
+}
+
+// The two-plane kernel's ring exceeds the default 48 KB of dynamic shared memory.
+static int p2_quad_prepare() {
+  static_assert(kP2QSmem >= sizeof(int) * (kP2StTotal + 9), "face blocks stage the stencil index in the tile's shared memory");
+  HHG_CUDA_TRY(cudaFuncSetAttribute(p2_quad_f32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2QSmem));
+  HHG_CUDA_TRY(cudaFuncSetAttribute(p2_quad_f32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2QSmem));
+  return HHG_OK;
+}
 
 // diag(A) for the constant-coefficient operators: sum of A_T[a][a] over the incident micro-tets.
 template <typename T>
@@ -1470,30 +1794,54 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
     return HHG_OK;
   }
   // P2 constant coefficient: stencil rows (28.75 FMA per point against about 74 in element form)
-  // from shared-memory plane tiles; 128-point tiles in FP32, 64-point tiles in FP64
-  // (small lattices in FP32, the coarse levels of mixed-precision multigrid, run one marching launch
-  // instead: there a launch costs more than the work; in FP64 the few CTAs of a small march would
-  // leave the FP64 pipes of most SMs idle)
-  if (op->kind == HHG_DIFFUSION && op->degree == 2 && op->coeff.type == HHG_COEFF_CONST && op->d_p2st64 &&
-      (sizeof(T) == 8 || op->N > 32)) {
-    const Interface* I = op->itf;
-    const P2Stencil<T>* st = (const P2Stencil<T>*)(sizeof(T) == 8 ? op->d_p2st64 : op->d_p2st32);
-    constexpr int TI = sizeof(T) == 8 ? 64 : 128;
-    const TileTasks& tt = I->tile[sizeof(T) == 8 ? 1 : 0];
-    constexpr size_t smem = p2_tile_smem<T, TI>();
-    static_assert(smem <= 48 * 1024, "P2 tile exceeds the default dynamic shared memory");
-    const P2StencilIndex* ix = (const P2StencilIndex*)op->d_p2idx;
-    static_assert(smem >= sizeof(int) * (kP2StTotal + 9), "face blocks stage the stencil index in the tile's shared memory");
-    const int nfb = (int)((tri_host(op->N) + 255) / 256);
-    const unsigned grid = (unsigned)(tt.n + (int64_t)nm * 4 * nfb);
-    if (op->bc == HHG_DIRICHLET)
-      p2_tile_kernel<T, TI, true><<<grid, 256, smem, s>>>(dconst<T>(op), st, ix, tt.d, (int)tt.n, tt.kchunk, nfb,
-                                                          I->d_pstart, x, y);
-    else
-      p2_tile_kernel<T, TI, false><<<grid, 256, smem, s>>>(dconst<T>(op), st, ix, tt.d, (int)tt.n, tt.kchunk, nfb,
-                                                           I->d_pstart, x, y);
-    HHG_CUDA_TRY(cudaGetLastError());
-    return HHG_OK;
+  // from shared-memory plane tiles.  FP32: two planes per step, one launch per macro with its
+  // weights in the parameter bank (p2_quad_f32_kernel); small lattices in FP32, the coarse levels of
+  // mixed-precision multigrid, run one marching launch instead (there a launch costs more than the
+  // work).  FP64: one plane per step, all macros in one launch (p2_tile_kernel; in FP64 the few CTAs
+  // of a small march would leave the FP64 pipes of most SMs idle).
+  if constexpr (sizeof(T) == 4) {
+    if (op->kind == HHG_DIFFUSION && op->degree == 2 && op->coeff.type == HHG_COEFF_CONST && op->d_p2st64 &&
+        op->N > 32) {
+      const Interface* I = op->itf;
+      const P2Stencil<float>* st = (const P2Stencil<float>*)op->d_p2st32;
+      const OpConst<float>* cf = (const OpConst<float>*)op->d_const32;
+      const TileTasks& tt = I->tile[0];
+      const P2StencilIndex* ix = (const P2StencilIndex*)op->d_p2idx;
+      const int nfb = (int)((tri_host(op->N) + 255) / 256);
+      const unsigned grid = (unsigned)(tt.n + 4 * nfb);
+      for (int m = 0; m < nm; ++m) {
+        if (op->bc == HHG_DIRICHLET)
+          p2_quad_f32_kernel<true><<<grid, 256, kP2QSmem, s>>>(op->h_p2w32[m], cf + m, st + m, ix, tt.d, (int)tt.n,
+                                                               tt.kchunk, nfb, I->d_pstart, x, y, op->npts);
+        else
+          p2_quad_f32_kernel<false><<<grid, 256, kP2QSmem, s>>>(op->h_p2w32[m], cf + m, st + m, ix, tt.d, (int)tt.n,
+                                                                tt.kchunk, nfb, I->d_pstart, x, y, op->npts);
+        HHG_CUDA_TRY(cudaGetLastError());
+      }
+      return HHG_OK;
+    }
+  }
+  if constexpr (sizeof(T) == 8) {
+    if (op->kind == HHG_DIFFUSION && op->degree == 2 && op->coeff.type == HHG_COEFF_CONST && op->d_p2st64) {
+      const Interface* I = op->itf;
+      const P2Stencil<T>* st = (const P2Stencil<T>*)op->d_p2st64;
+      constexpr int TI = 64;
+      const TileTasks& tt = I->tile[1];
+      constexpr size_t smem = p2_tile_smem<T, TI>();
+      static_assert(smem <= 48 * 1024, "P2 tile exceeds the default dynamic shared memory");
+      const P2StencilIndex* ix = (const P2StencilIndex*)op->d_p2idx;
+      static_assert(smem >= sizeof(int) * (kP2StTotal + 9), "face blocks stage the stencil index in the tile's shared memory");
+      const int nfb = (int)((tri_host(op->N) + 255) / 256);
+      const unsigned grid = (unsigned)(tt.n + (int64_t)nm * 4 * nfb);
+      if (op->bc == HHG_DIRICHLET)
+        p2_tile_kernel<T, TI, true><<<grid, 256, smem, s>>>(dconst<T>(op), st, ix, tt.d, (int)tt.n, tt.kchunk, nfb,
+                                                            I->d_pstart, x, y);
+      else
+        p2_tile_kernel<T, TI, false><<<grid, 256, smem, s>>>(dconst<T>(op), st, ix, tt.d, (int)tt.n, tt.kchunk, nfb,
+                                                             I->d_pstart, x, y);
+      HHG_CUDA_TRY(cudaGetLastError());
+      return HHG_OK;
+    }
   }
   if (op->kind == HHG_DIFFUSION) return launch_march<T>(op, dconst<T>(op), 0, x, nullptr, field_ptr<T>(op), y, s);
   return fail(HHG_E_UNSUPPORTED, "apply: operator kind %d degree %d coefficient %d not implemented", op->kind,
@@ -1695,15 +2043,19 @@ extern "C" int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, 
     std::vector<P2Stencil<double>> w64;
     HHG_TRY(build_p2_stencil(op.get(), ix, w64));
     std::vector<P2Stencil<float>> w32(nm);
-    for (int m = 0; m < nm; ++m)
+    op->h_p2w32.resize(nm);
+    for (int m = 0; m < nm; ++m) {
       for (int z = 0; z < 16; ++z)
         for (int t = 0; t < kP2StTotal; ++t) w32[m].w[z][t] = (float)w64[m].w[z][t];
+      for (int t = 0; t < kP2StTotal; ++t) op->h_p2w32[m].w[t] = w32[m].w[0][t];
+    }
     HHG_CUDA_TRY(cudaMalloc(&op->d_p2idx, sizeof(P2StencilIndex)));
     HHG_CUDA_TRY(cudaMemcpy(op->d_p2idx, &ix, sizeof(P2StencilIndex), cudaMemcpyHostToDevice));
     HHG_CUDA_TRY(cudaMalloc(&op->d_p2st64, sizeof(P2Stencil<double>) * nm));
     HHG_CUDA_TRY(cudaMalloc(&op->d_p2st32, sizeof(P2Stencil<float>) * nm));
     HHG_CUDA_TRY(cudaMemcpy(op->d_p2st64, w64.data(), sizeof(P2Stencil<double>) * nm, cudaMemcpyHostToDevice));
     HHG_CUDA_TRY(cudaMemcpy(op->d_p2st32, w32.data(), sizeof(P2Stencil<float>) * nm, cudaMemcpyHostToDevice));
+    HHG_TRY(p2_quad_prepare());
   }
   HHG_TRY(alloc_face_scratch(op.get()));
   HHG_TRY(noalloc_prepare());

@@ -48,11 +48,12 @@ def test_apply_parity(meshname, level, degree, kind, bc, dtype):
     assert spread == 0.0
 
 
-@pytest.mark.parametrize("meshname,level", [("reference_tet", 5), ("cube6", 4), ("cuboid36", 3)])
+@pytest.mark.parametrize("meshname,level", [("reference_tet", 5), ("cube6", 4), ("cube6", 5), ("cuboid36", 3)])
 @pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_p2_const_parity_large(meshname, level, bc, dtype):
-    """P2 constant coefficient (stencil rows per node parity) at sizes with many interior rows."""
+    """P2 constant coefficient (stencil rows per node parity) at sizes with many interior rows; from 64
+    intervals per edge on, FP32 runs the plane-tile kernel launched once per macro (cube6 level 5)."""
     from gpu_helpers import Case, rel_err
     import paper_2404_08371_gb300 as hhg
     c = Case(meshname, level, 2)
