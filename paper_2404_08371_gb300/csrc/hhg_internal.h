@@ -267,6 +267,10 @@ struct hhg_op {
   void* d_p2st32 = nullptr;
   void* d_p2idx = nullptr;   // P2StencilIndex (structural neighbour lists)
   std::vector<hhg::P2ParamW> h_p2w32;   // per macro: FP32 weights of the rows off the faces
+  // several macros: their per-macro launches run on these streams side by side, forked from and
+  // joined back into the caller's stream by the events (created with the op; no apply allocates)
+  std::vector<cudaStream_t> aux_streams;
+  std::vector<cudaEvent_t> aux_events;   // [0]: fork, [1 + i]: join of stream i
   // stored local matrices (hhg_op_store_element_matrices): [macro][class][entry][cube], cube =
   // packed index of its origin in the lattice of resolution 2^level - 1; entries 55 (P2) or 1 (P1)
   void* d_elem = nullptr;

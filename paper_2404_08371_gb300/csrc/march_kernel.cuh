@@ -249,15 +249,12 @@ __device__ __forceinline__ void sincos2pi<float>(float x, float* s, float* c) {
 
 // AFF (P2, variable coefficient, APPLY): affine gradient + moment test (rules of many points) or the
 // tabulated direct form (rules of few points).
-// The stored variant streams its local matrices from HBM: two CTAs per SM (at most 128 registers a
-// thread) keep enough loads in flight; the variants that compute their matrices keep one CTA per SM
-// and all the registers they ask for.
-template <typename T, int R, int COEF, int MODE, bool DIR, bool AFF = true, bool JATOM = false>
-__global__ void __launch_bounds__(32 * kWarps, COEF == kCoefStored ? 2 : 1) march_kernel(const OpConst<T>* __restrict__ cst,
-                                                            const int4* __restrict__ tasks, int kChunk,
-                                                            const T* __restrict__ x, const T* __restrict__ g,
-                                                            const T* __restrict__ kf, T* __restrict__ out,
-                                                            N1Args<T> n1a, FaceScratch<T> fs) {
+// The body of both entry points below.
+template <typename T, int R, int COEF, int MODE, bool DIR, bool AFF, bool JATOM>
+__device__ __forceinline__ void march_body(const OpConst<T>* __restrict__ cst, const int4* __restrict__ tasks, int kChunk,
+                                           const T* __restrict__ x, const T* __restrict__ g,
+                                           const T* __restrict__ kf, T* __restrict__ out, N1Args<T> n1a,
+                                           FaceScratch<T> fs) {
   constexpr int P = R + 1;
   constexpr int P3 = P * P * P;
   constexpr int NL = R == 1 ? 4 : 10;
@@ -658,6 +655,38 @@ __global__ void __launch_bounds__(32 * kWarps, COEF == kCoefStored ? 2 : 1) marc
   }
 }
 
+// The variants that compute their local matrices: the compiler's own register choice (an explicit
+// minimum of one CTA per SM makes it take up to 60% more registers and halves the CTAs of the FP32
+// variants).
+template <typename T, int R, int COEF, int MODE, bool DIR, bool AFF = true, bool JATOM = false>
+__global__ void __launch_bounds__(32 * kWarps) march_kernel(const OpConst<T>* __restrict__ cst,
+                                                            const int4* __restrict__ tasks, int kChunk,
+                                                            const T* __restrict__ x, const T* __restrict__ g,
+                                                            const T* __restrict__ kf, T* __restrict__ out,
+                                                            N1Args<T> n1a, FaceScratch<T> fs) {
+  march_body<T, R, COEF, MODE, DIR, AFF, JATOM>(cst, tasks, kChunk, x, g, kf, out, n1a, fs);
+}
+
+// The stored variant streams its local matrices from HBM: two CTAs per SM (at most 128 registers a
+// thread) keep enough loads in flight.
+template <typename T, int R, int MODE, bool DIR, bool AFF = true, bool JATOM = false>
+__global__ void __launch_bounds__(32 * kWarps, 2) march_stored_kernel(const OpConst<T>* __restrict__ cst,
+                                                                      const int4* __restrict__ tasks, int kChunk,
+                                                                      const T* __restrict__ x, const T* __restrict__ g,
+                                                                      const T* __restrict__ kf, T* __restrict__ out,
+                                                                      N1Args<T> n1a, FaceScratch<T> fs) {
+  march_body<T, R, kCoefStored, MODE, DIR, AFF, JATOM>(cst, tasks, kChunk, x, g, kf, out, n1a, fs);
+}
+
+template <typename T, int R, int COEF, int MODE, bool DIR, bool AFF, bool JATOM>
+void launch_march_grid(unsigned grid, cudaStream_t s, const OpConst<T>* cst, const int4* tasks, int kChunk, const T* x,
+                       const T* g, const T* kf, T* out, N1Args<T> n1a, FaceScratch<T> fs) {
+  if constexpr (COEF == kCoefStored)
+    march_stored_kernel<T, R, MODE, DIR, AFF, JATOM><<<grid, 32 * kWarps, 0, s>>>(cst, tasks, kChunk, x, g, kf, out, n1a, fs);
+  else
+    march_kernel<T, R, COEF, MODE, DIR, AFF, JATOM><<<grid, 32 * kWarps, 0, s>>>(cst, tasks, kChunk, x, g, kf, out, n1a, fs);
+}
+
 // Row and position of entry r of a triangle of rows 0..m, row q holding m - q + 1 entries.
 __device__ __forceinline__ void tri_decode(int m, int64_t r, int& row, int& pos) {
   const float bq = 2.0f * m + 3.0f;
@@ -766,11 +795,11 @@ int launch_march_t(const hhg_op* op, const OpConst<T>* cst, const T* x, const T*
     if (!op->d_face) return fail(HHG_E_CUDA, "march: the operator has no tile-face scratch");
     const FaceScratch<T> fs = face_scratch<T>(op);
     if (dir)
-      march_kernel<T, R, COEF, MODE, true, AFF, true><<<grid, 32 * kWarps, 0, s>>>(
-          cst, I->d_march_tasks, I->march_kchunk, x, g, kf, out, n1a, fs);
+      launch_march_grid<T, R, COEF, MODE, true, AFF, true>(grid, s, cst, I->d_march_tasks, I->march_kchunk, x, g, kf,
+                                                           out, n1a, fs);
     else
-      march_kernel<T, R, COEF, MODE, false, AFF, true><<<grid, 32 * kWarps, 0, s>>>(
-          cst, I->d_march_tasks, I->march_kchunk, x, g, kf, out, n1a, fs);
+      launch_march_grid<T, R, COEF, MODE, false, AFF, true>(grid, s, cst, I->d_march_tasks, I->march_kchunk, x, g, kf,
+                                                            out, n1a, fs);
     HHG_CUDA_TRY(cudaGetLastError());
     const bool rows = dir && MODE != MODE_ADJ;
     const int nfb = (int)((fs.Si + fs.Sj + 255) / 256);
@@ -783,11 +812,11 @@ int launch_march_t(const hhg_op* op, const OpConst<T>* cst, const T* x, const T*
     return HHG_OK;
   }
   if (dir)
-    march_kernel<T, R, COEF, MODE, true, AFF><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x, g,
-                                                                            kf, out, n1a, FaceScratch<T>());
+    launch_march_grid<T, R, COEF, MODE, true, AFF, false>(grid, s, cst, I->d_march_tasks, I->march_kchunk, x, g, kf, out,
+                                                          n1a, FaceScratch<T>());
   else
-    march_kernel<T, R, COEF, MODE, false, AFF><<<grid, 32 * kWarps, 0, s>>>(cst, I->d_march_tasks, I->march_kchunk, x,
-                                                                             g, kf, out, n1a, FaceScratch<T>());
+    launch_march_grid<T, R, COEF, MODE, false, AFF, false>(grid, s, cst, I->d_march_tasks, I->march_kchunk, x, g, kf, out,
+                                                           n1a, FaceScratch<T>());
   HHG_CUDA_TRY(cudaGetLastError());
   return HHG_OK;
 }

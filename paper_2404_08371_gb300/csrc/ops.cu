@@ -1169,6 +1169,7 @@ __global__ void __launch_bounds__(256) p2_tile_kernel(const OpConst<T>* __restri
 // barrier per step.
 constexpr int kP2QRing = 10;
 constexpr size_t kP2QSmem = sizeof(float) * kP2QRing * (128 + 4) * kP2TileH;   // 63,360 bytes
+constexpr int kP2QStreams = 4;   // streams the per-macro launches of a multi-macro apply share
 
 // Union of the cells of the four points of a lane in one step, as offsets from the even point of
 // plane k (packed (dx+2) | (dy+2) << 4 | (dz+2) << 8, dx in -2..3, dz in -2..3), sorted; e[c][q]:
@@ -1809,14 +1810,26 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
       const P2StencilIndex* ix = (const P2StencilIndex*)op->d_p2idx;
       const int nfb = (int)((tri_host(op->N) + 255) / 256);
       const unsigned grid = (unsigned)(tt.n + 4 * nfb);
+      // one macro: the caller's stream; several: the op's streams side by side (a launch per macro
+      // alone leaves the GPU part empty while its last tiles run)
+      const int ns = (int)op->aux_streams.size();
+      if (ns > 0) {
+        HHG_CUDA_TRY(cudaEventRecord(op->aux_events[0], s));
+        for (int i = 0; i < ns; ++i) HHG_CUDA_TRY(cudaStreamWaitEvent(op->aux_streams[i], op->aux_events[0], 0));
+      }
       for (int m = 0; m < nm; ++m) {
+        const cudaStream_t sm = ns > 0 ? op->aux_streams[m % ns] : s;
         if (op->bc == HHG_DIRICHLET)
-          p2_quad_f32_kernel<true><<<grid, 256, kP2QSmem, s>>>(op->h_p2w32[m], cf + m, st + m, ix, tt.d, (int)tt.n,
-                                                               tt.kchunk, nfb, I->d_pstart, x, y, op->npts);
-        else
-          p2_quad_f32_kernel<false><<<grid, 256, kP2QSmem, s>>>(op->h_p2w32[m], cf + m, st + m, ix, tt.d, (int)tt.n,
+          p2_quad_f32_kernel<true><<<grid, 256, kP2QSmem, sm>>>(op->h_p2w32[m], cf + m, st + m, ix, tt.d, (int)tt.n,
                                                                 tt.kchunk, nfb, I->d_pstart, x, y, op->npts);
+        else
+          p2_quad_f32_kernel<false><<<grid, 256, kP2QSmem, sm>>>(op->h_p2w32[m], cf + m, st + m, ix, tt.d, (int)tt.n,
+                                                                 tt.kchunk, nfb, I->d_pstart, x, y, op->npts);
         HHG_CUDA_TRY(cudaGetLastError());
+      }
+      for (int i = 0; i < ns; ++i) {
+        HHG_CUDA_TRY(cudaEventRecord(op->aux_events[1 + i], op->aux_streams[i]));
+        HHG_CUDA_TRY(cudaStreamWaitEvent(s, op->aux_events[1 + i], 0));
       }
       return HHG_OK;
     }
@@ -1879,6 +1892,8 @@ hhg_op::~hhg_op() {
   cudaFree(d_face);
   cudaFree(d_p1df);
   cudaFree(d_p1df_x);
+  for (cudaStream_t t : aux_streams) cudaStreamDestroy(t);
+  for (cudaEvent_t e : aux_events) cudaEventDestroy(e);
 }
 
 static int check_dtype(int dtype) {
@@ -2056,6 +2071,19 @@ extern "C" int hhg_op_create(hhg_mesh_t* mesh, int level, int kind, int degree, 
     HHG_CUDA_TRY(cudaMemcpy(op->d_p2st64, w64.data(), sizeof(P2Stencil<double>) * nm, cudaMemcpyHostToDevice));
     HHG_CUDA_TRY(cudaMemcpy(op->d_p2st32, w32.data(), sizeof(P2Stencil<float>) * nm, cudaMemcpyHostToDevice));
     HHG_TRY(p2_quad_prepare());
+    if (nm > 1) {
+      const int ns = std::min(nm, kP2QStreams);
+      for (int i = 0; i < ns; ++i) {
+        cudaStream_t t;
+        HHG_CUDA_TRY(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+        op->aux_streams.push_back(t);
+      }
+      for (int i = 0; i <= ns; ++i) {
+        cudaEvent_t e;
+        HHG_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        op->aux_events.push_back(e);
+      }
+    }
   }
   HHG_TRY(alloc_face_scratch(op.get()));
   HHG_TRY(noalloc_prepare());
