@@ -267,6 +267,20 @@ def run_fmg(hhg, torch, level: int, reps: int = 1):
                 out[name] = {"solve_ms": min(ms), "setup_ms": st0["setup_ms"], "iterations": st["iterations"],
                              "rel_residual": st["rel_residual"], "l2_error": e, "dofs": inner,
                              "mdofs_per_s": inner / (min(ms) * 1e-3) / 1e6}
+        if lvl == level:
+            # the same solves with the FP64 applies in double-float arithmetic (FP32 pairs), coarse
+            # operators included: all cycles, and the FP64 residuals of the mixed solve
+            opd = hhg.Operator(mesh, degree=2, coeff=("const", 1.0), bc="dirichlet", quad_degree=4)
+            opd.set_fp64_arith("double_float")
+            for name, mixed in (("fp64_double_float", 0), ("mixed_double_float", 1)):
+                x, st0 = opd.mg_solve(b, torch.zeros_like(b), mixed=mixed)
+                ms = []
+                for _ in range(reps):
+                    x, st = opd.mg_solve(b, torch.zeros_like(b), mixed=mixed)
+                    ms.append(st["solve_ms"])
+                out[name] = {"solve_ms": min(ms), "iterations": st["iterations"], "rel_residual": st["rel_residual"],
+                             "l2_error": mesh.l2_error_sin3(x, 2)}
+            del opd
         del op, mesh
     for name in ("fp64", "mixed"):
         out[name]["l2_error_ratio_vs_level_%d" % (level - 1)] = errs[(name, level - 1)] / errs[(name, level)]
@@ -314,9 +328,8 @@ def run_const_legs(hhg, torch, flush, peak_gbs: float, reps: int = 5):
         mesh = hhg.Mesh(v, t, level)
         op = hhg.Operator(mesh, degree=degree, coeff=("const", 1.0), bc="dirichlet")
         tot, inner = mesh.dof_count(degree)
-        variants = [("f64", torch.float64, "native"), ("f32", torch.float32, "native")]
-        if degree == 1:
-            variants.append(("df64", torch.float64, "double_float"))   # FP64 vectors, FP32-pair arithmetic
+        variants = [("f64", torch.float64, "native"), ("f32", torch.float32, "native"),
+                    ("df64", torch.float64, "double_float")]   # FP64 vectors, FP32-pair arithmetic
         for dt, tdt, arith in variants:
             op.set_fp64_arith(arith) if tdt == torch.float64 else None
             x = torch.from_numpy(W.uniform(mesh.vec_size(degree), seed=0)).to("cuda", tdt)

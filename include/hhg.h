@@ -140,9 +140,13 @@ int hhg_op_create_curlcurl(hhg_mesh_t* mesh, int level, const hhg_coeff_t* alpha
  * of FP32 numbers (hi + lo, 48 significant bits: relative errors of a few
  * 1e-15 per operation, within the 1e-12 tolerance of FP64 applies), for
  * GPUs whose FP64 rate is a small fraction of their FP32 rate (GB300:
- * 1/64).  Available for P1 constant-coefficient DIFFUSION operators; it
- * allocates a device vector of 8 bytes per point for the split input
- * (freed when the mode returns to native or with the operator).
+ * 1/64).  Available for P1 and P2 constant-coefficient DIFFUSION operators
+ * (P2: lattices of more than 32 intervals per edge; smaller ones keep FP64
+ * operations); it allocates a device vector of 8 bytes per point for the
+ * split input (freed when the mode returns to native or with the operator).
+ * The operator's other calls (diagonal, multigrid) use its applies as set;
+ * a multigrid hierarchy built while the mode is set (the first
+ * hhg_mg_solve) gives its coarse operators the same mode.
  * Errors: HHG_E_UNSUPPORTED (other operators), HHG_E_OOM, HHG_E_ARG. */
 enum { HHG_FP64_NATIVE = 0, HHG_FP64_DOUBLE_FLOAT = 1 };
 int hhg_op_set_fp64_arith(hhg_op_t* op, int mode);

@@ -189,7 +189,7 @@ class Operator:
 
     def set_fp64_arith(self, mode: str) -> "Operator":
         """"native" (FP64 operations, the default) or "double_float" (FP64 vectors, FP32-pair
-        arithmetic; P1 constant-coefficient diffusion only)."""
+        arithmetic; P1 and P2 constant-coefficient diffusion)."""
         code = {"native": 0, "double_float": 1}[mode]
         check(lib.hhg_op_set_fp64_arith(self.handle, code), "hhg_op_set_fp64_arith")
         return self

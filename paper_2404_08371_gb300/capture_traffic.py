@@ -32,12 +32,15 @@ LEGS = {
     "p2_sin3_f32": ("march_kernel", 1, "--level 8 --degree 2 --coeff sin3 --dtype f32", MARCH, "reference macro, level 8"),
     "p1_sin3_f32": ("march_kernel", 1, "--level 8 --degree 1 --coeff sin3 --dtype f32", MARCH, "reference macro, level 8"),
     "p2_const_f64": ("p2_tile_kernel", 1, "--level 8 --degree 2 --coeff const --dtype f64", OPS, "reference macro, level 8"),
-    "p2_const_f32": ("p2_quad_f32_kernel", 1, "--level 8 --degree 2 --coeff const --dtype f32", OPS, "reference macro, level 8"),
+    "p2_const_f32": ("p2_quad_kernel", 1, "--level 8 --degree 2 --coeff const --dtype f32", OPS, "reference macro, level 8"),
     "p1_const_f64": ("p1_gather_kernel", 1, "--level 9 --degree 1 --coeff const --dtype f64", OPS,
                      "reference macro, level 9"),
     "p1_const_df64": ("split_double_kernel|p1_gather_df_kernel", 2,
                       "--level 9 --degree 1 --coeff const --dtype f64 --fp64-arith double_float", OPS,
                       "reference macro, level 9"),
+    "p2_const_df64": ("split_double_kernel|p2_quad_kernel", 2,
+                      "--level 8 --degree 2 --coeff const --dtype f64 --fp64-arith double_float", OPS,
+                      "reference macro, level 8"),
     "p1_const_f32": ("p1_climb_f32_kernel", 1, "--level 9 --degree 1 --coeff const --dtype f32", OPS,
                      "reference macro, level 9"),
     "n1_f64": ("march_kernel", 1, "--mesh cuboid36 --level 7 --kind curlcurl --coeff field_p1 --dtype f64", MARCH,

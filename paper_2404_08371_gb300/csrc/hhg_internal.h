@@ -87,8 +87,8 @@ struct Interface {
   int march_kchunk = 32;
   // task lists of the plane-tile kernels: (i-chunk, row group, k-chunk, macro), heaviest first;
   // tile[0]: chunks of 128 points along i on one macro (launched once per macro), tile[1]: chunks
-  // of 64 on all macros (one launch)
-  TileTasks tile[2];
+  // of 64 on all macros (one launch), tile[2]: chunks of 64 on one macro
+  TileTasks tile[3];
   ~Interface();
 };
 
@@ -237,10 +237,14 @@ template <typename T>
 struct alignas(16) P2Stencil {
   T w[16][kP2StTotal];
 };
-// The FP32 weights of the rows off the macro faces (mask 0) of one macro, passed by value to the
-// FP32 plane-tile kernel so that its FMAs read them from the kernel's parameter bank.
+// The weights of the rows off the macro faces (mask 0) of one macro, passed by value to the
+// two-plane kernel so that its FMAs read them from the kernel's parameter bank: in FP32, and as FP32
+// pairs (hi, lo) for double-float arithmetic.
 struct P2ParamW {
   float w[kP2StTotal];
+};
+struct P2ParamWDF {
+  float2 w[kP2StTotal];
 };
 
 // Hoisted per-class data of the Nedelec operator (one block per macro), in the macro's canonical
@@ -267,6 +271,7 @@ struct hhg_op {
   void* d_p2st32 = nullptr;
   void* d_p2idx = nullptr;   // P2StencilIndex (structural neighbour lists)
   std::vector<hhg::P2ParamW> h_p2w32;   // per macro: FP32 weights of the rows off the faces
+  std::vector<hhg::P2ParamWDF> h_p2wdf; // the same as FP32 pairs (double-float FP64 applies, if set)
   // several macros: their per-macro launches run on these streams side by side, forked from and
   // joined back into the caller's stream by the events (created with the op; no apply allocates)
   std::vector<cudaStream_t> aux_streams;
@@ -287,10 +292,10 @@ struct hhg_op {
   hhg::QuadRule rule;
   std::vector<hhg::OpConst<double>> h_const;
   const hhg::Interface* itf = nullptr;   // per-level data of the op's space (owned by the mesh)
-  // P1 constant diffusion, FP64 vectors in double-float arithmetic (ops.cu): the stencil weights as
-  // FP32 pairs (float2[16] per macro) and the split input vector (float2[npts])
+  // FP64 vectors in double-float arithmetic (ops.cu): the P1 stencil weights as FP32 pairs
+  // (float2[16] per macro) and the split input vector of P1 or P2 applies (float2[npts])
   void* d_p1df = nullptr;
-  void* d_p1df_x = nullptr;
+  void* d_dfx = nullptr;
   // partial sums of the points shared by marching tiles (lattices of at least kMarchJAtomicN cubes
   // per edge; march_kernel.cuh, FaceScratch): FP64-sized, per macro face_S slots
   void* d_face = nullptr;

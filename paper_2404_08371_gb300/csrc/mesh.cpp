@@ -54,8 +54,7 @@ Interface::~Interface() {
   cudaFree(d_cta_start);
   cudaFree(d_pstart);
   cudaFree(d_march_tasks);
-  cudaFree(tile[0].d);
-  cudaFree(tile[1].d);
+  for (TileTasks& t : tile) cudaFree(t.d);
   cudaFree(d_sign);
 }
 
@@ -562,6 +561,7 @@ int hhg_mesh::interface(int lvl, int degree, const Interface** out) {
   // once per task) for about 4 tasks per SM; the others about 8 per SM
   HHG_TRY(build_tile_tasks(N, 128, kStencilWarps, 1, 4 * 152, &I->tile[0]));
   HHG_TRY(build_tile_tasks(N, 64, kStencilWarps, nmacro(), 8 * 152, &I->tile[1]));
+  HHG_TRY(build_tile_tasks(N, 64, kStencilWarps, 1, 4 * 152, &I->tile[2]));
   I->h_ptr = ptr;
   I->h_idx = idx;
   I->h_bnd = bnd;

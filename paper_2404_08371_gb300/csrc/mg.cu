@@ -1143,6 +1143,8 @@ static int setup_mg(hhg_op* op, const hhg_mg_opts_t* o, cudaStream_t s) {
         HHG_TRY(hhg_op_create(op->mesh, l, op->kind, op->degree, &op->coeff, op->bc, op->quad_degree, &c));
       lv.op = c;
       lv.owned = true;
+      // the coarse operators take the fine one's FP64 arithmetic (double-float where it is set)
+      if (op->d_dfx) HHG_TRY(hhg_op_set_fp64_arith(c, HHG_FP64_DOUBLE_FLOAT));
     }
     lv.n = lv.op->npts;
     for (double** p : {&lv.dinv64, &lv.x64, &lv.b64, &lv.r64, &lv.y64, &lv.d64})

@@ -890,8 +890,8 @@ __global__ void __launch_bounds__(256, PT == 4 ? 2 : 3) p1_climb_f32_kernel(cons
 }
 
 // ---------------------------------------------------------------------------
-// P2 constant-coefficient apply in FP64 from shared-memory plane tiles (FP32: p2_quad_f32_kernel
-// below).  A CTA owns rows j0..j0+7 and points i0..i0+TI-1 of a k-chunk and climbs its planes.  Each plane of the tile plus a halo of two
+// P2 constant-coefficient apply in FP64 from shared-memory plane tiles (FP32 and double-float:
+// p2_quad_kernel below).  A CTA owns rows j0..j0+7 and points i0..i0+TI-1 of a k-chunk and climbs its planes.  Each plane of the tile plus a halo of two
 // points (the reach of a P2 row) is staged with cp.async into a ring of planes, kP2Ahead planes
 // beyond the k+2 that the plane k being computed needs; staged Dirichlet points are zeroed on
 // arrival.  A lane evaluates the points i0 + 64 v + 2 lane + {0, 1}: both node parities of its row,
@@ -1100,7 +1100,7 @@ __global__ void __launch_bounds__(256) p2_tile_kernel(const OpConst<T>* __restri
     p2_face_point<T, DIRICHLET>(cst[macro], st[macro], offs, starts, pstart, x, y, f, (r - f * nfb) * 256 + threadIdx.x);
     return;
   }
-  static_assert(std::is_same<T, double>::value, "FP32 runs p2_quad_f32_kernel");
+  static_assert(std::is_same<T, double>::value, "FP32 runs p2_quad_kernel");
   T* buf = reinterpret_cast<T*>(p2_tile_smem_raw);
   T* w0 = buf + kP2Ring * SLOT;
   const int4 task = tasks[blockIdx.x];
@@ -1158,18 +1158,44 @@ __global__ void __launch_bounds__(256) p2_tile_kernel(const OpConst<T>* __restri
 }
 
 // ---------------------------------------------------------------------------
-// P2 constant-coefficient apply in FP32, two planes per step, weights in the parameter bank.  The
-// launch covers one macro; its 230 interior weights come by value (P2ParamW), so every FMA takes its
-// weight from the constant bank and no load feeds it.  The tiles and the staging are those of
-// p2_tile_kernel (8 rows x 128 points plus a halo of two, even and odd columns apart), but a step
-// evaluates the planes k and k+1 together: a lane's four points (even and odd i, planes k and k+1)
-// share the union of their cells, which is loaded from shared memory once (2.8 x fewer loads per
-// point than one plane at a time).  The ring holds 10 planes: at step k the planes k-2 .. k+3 are
-// read, k+4 and k+5 (landed) get their Dirichlet points zeroed, k+6 and k+7 are being copied; one
-// barrier per step.
+// P2 constant-coefficient apply with two planes per step and the weights in the parameter bank, in
+// FP32 or in double-float arithmetic (FP64 vectors, FP32 pairs).  The launch covers one macro; its
+// 230 interior weights come by value (P2ParamW / P2ParamWDF), so every FMA takes its weight from the
+// constant bank and no load feeds it.  The tiles and the staging are those of p2_tile_kernel (8 rows
+// x TI points plus a halo of two, even and odd columns apart), but a step evaluates the planes k and
+// k+1 together: a lane's four points (even and odd i, planes k and k+1) share the union of their
+// cells, which is loaded from shared memory once (2.8 x fewer loads per point than one plane at a
+// time).  The ring holds 10 planes: at step k the planes k-2 .. k+3 are read, k+4 and k+5 (landed)
+// get their Dirichlet points zeroed, k+6 and k+7 are being copied; one barrier per step.
 constexpr int kP2QRing = 10;
-constexpr size_t kP2QSmem = sizeof(float) * kP2QRing * (128 + 4) * kP2TileH;   // 63,360 bytes
 constexpr int kP2QStreams = 4;   // streams the per-macro launches of a multi-macro apply share
+
+// FP32: 128-point tiles, staged values and weights in FP32.
+struct P2QF32 {
+  using E = float;    // staged value
+  using V = float;    // vector entry
+  using WP = P2ParamW;
+  static constexpr int TI = 128;
+  __device__ __forceinline__ static void fma(float& acc, float w, float v) { acc = fmaf(w, v, acc); }
+  __device__ __forceinline__ static float out(float acc) { return acc; }
+};
+// Double-float: FP64 vectors split into FP32 pairs by a streaming pass, weights split on the host,
+// products and sums by df_fma (exact products, two-sum of the high parts); 64-point tiles (the
+// staged pairs take twice the shared memory).
+struct P2QDF {
+  using E = float2;
+  using V = double;
+  using WP = P2ParamWDF;
+  static constexpr int TI = 64;
+  __device__ __forceinline__ static void fma(float2& acc, float2 w, float2 v) { df_fma(acc, w, v); }
+  __device__ __forceinline__ static double out(float2 acc) {
+    return float_to_double_bits(acc.x) + float_to_double_bits(acc.y);
+  }
+};
+template <class A>
+constexpr size_t p2q_smem() {
+  return sizeof(typename A::E) * kP2QRing * (A::TI + 4) * kP2TileH;   // FP32 63,360, double-float 65,280 bytes
+}
 
 // Union of the cells of the four points of a lane in one step, as offsets from the even point of
 // plane k (packed (dx+2) | (dy+2) << 4 | (dz+2) << 8, dx in -2..3, dz in -2..3), sorted; e[c][q]:
@@ -1224,11 +1250,11 @@ struct P2QStart {
   static constexpr int v = p2_start(p2q_par(PA, Q));
 };
 
-// Staging plan of p2_quad_f32_kernel.  A plane of the tile is 12 rows of W = 132 columns, 5 chunks
-// of 32 columns per row (the last one 4 wide).  Warp w copies row w whole (h = 0) and chunks 0-2
-// (w < 4) or 3-4 (w >= 4) of row 8 + (w & 3) (h = 1), 7 to 8 chunks per warp.  Per row the plan keeps
-// what does not change from plane to plane: the row j, the packed offset of its column 0 without
-// the plane terms, and the column limit, so that plane kk costs one multiply-add per row:
+// Staging plan.  A plane of the tile is 12 rows of W = TI + 4 columns, chunks of 32 columns per row
+// (5 for TI = 128, 3 for TI = 64, the last one 4 wide).  Warp w copies row w whole (h = 0) and of
+// row 8 + (w & 3) (h = 1) chunks 0-2 (w < 4) and 3-4 (w >= 4).  Per row the plan keeps what does not
+// change from plane to plane: the row j, the packed offset of its column 0 without the plane terms,
+// and the column limit, so that plane kk costs one multiply-add per row:
 // start(j, kk) = pstart[kk] + row32(N - kk, j) = pstart[kk] + j (2N + 3 - j) / 2 - j kk.
 struct P2QStage {
   int jr[2];        // row j of the staged row (h = 0, 1)
@@ -1239,10 +1265,12 @@ struct P2QStage {
   int r[2];
 };
 
-__device__ __forceinline__ bool p2q_mine(int h, int t, int warp) { return h == 0 || ((warp < 4) == (t < 3)); }
+// chunks 0 .. kP2QLo - 1 of an h = 1 row are copied by warps 0-3, the others by warps 4-7
+constexpr int kP2QLo = 3;
+__device__ __forceinline__ bool p2q_mine(int h, int t, int warp) { return h == 0 || ((warp < 4) == (t < kP2QLo)); }
 
-template <int TI>
-__device__ __forceinline__ P2QStage p2q_plan(float* buf, int N, int i0, int j0) {
+template <int TI, typename E>
+__device__ __forceinline__ P2QStage p2q_plan(E* buf, int N, int i0, int j0) {
   constexpr int W = TI + 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int s0 = (lane & 1) * (W / 2) + (lane >> 1);
@@ -1260,22 +1288,26 @@ __device__ __forceinline__ P2QStage p2q_plan(float* buf, int N, int i0, int j0) 
   return st;
 }
 
-// Chunk T of a staged row: columns lane + 32 T, at byte offsets 64 T (shared) and 128 T (global).
-template <int T>
-__device__ __forceinline__ void p2q_copy(unsigned dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0+%2], [%1+%3], 4;\n" ::"r"(dst), "l"(src), "n"(64 * T), "n"(128 * T));
+// Chunk T of a staged row of B-byte values: columns lane + 32 T, at byte offsets 16 B T (shared)
+// and 32 B T (global).
+template <int T, int B>
+__device__ __forceinline__ void p2q_copy(unsigned dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0+%2], [%1+%3], %4;\n" ::"r"(dst), "l"(src), "n"(16 * B * T),
+               "n"(32 * B * T), "n"(B));
 }
 
 // Copy plane kk (first packed position pk) into ring slot `slot` by the plan.  Columns outside the
 // row (before i = 0, after i = len - 1) feed only points the tile does not store, so a row whose
 // window of W values lies inside the vector (packed offsets gmin .. gmax of its first value) is
 // copied whole without tests; only rows at the two ends of the vector test each column.
-template <int TI>
-__device__ __forceinline__ void p2q_issue_plane(const P2QStage& st, int slot, const float* __restrict__ xm, int pk,
-                                                int N, int i0, int kk, int gmin, int gmax) {
+template <int TI, typename E>
+__device__ __forceinline__ void p2q_issue_plane(const P2QStage& st, int slot, const E* __restrict__ xm, int pk, int N,
+                                                int i0, int kk, int gmin, int gmax) {
   constexpr int W = TI + 4;
-  constexpr unsigned SLOT_BYTES = sizeof(float) * W * kP2TileH;
-  static_assert((W + 31) / 32 == 5 && W - 128 == 4, "five chunks per staged row, the last 4 columns wide");
+  constexpr int B = (int)sizeof(E);
+  constexpr unsigned SLOT_BYTES = B * W * kP2TileH;
+  constexpr int NCH = (W + 31) / 32;
+  static_assert(W - 32 * (NCH - 1) == 4 && NCH >= kP2QLo, "chunks of 32 columns, the last 4 wide");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (kk < 0 || kk > N) return;
 #pragma unroll
@@ -1284,26 +1316,27 @@ __device__ __forceinline__ void p2q_issue_plane(const P2QStage& st, int slot, co
     const int lim = st.lim[h] - kk;   // staged column col holds i = i0 - 2 + col < len
     if (lim + i0 - 2 <= 0) continue;  // no row (j < 0 or beyond the plane)
     const int g = pk - jr * kk + st.off[h] - lane;   // packed offset of column 0
-    const float* __restrict__ src = xm + (g + lane);
+    const E* __restrict__ src = xm + (g + lane);
     const unsigned dst = st.dst[h] + slot * SLOT_BYTES;
-    const bool lo = h == 0 || warp < 4, hi = h == 0 || warp >= 4;   // chunks 0-2 / 3-4 of this warp
+    const bool lo = h == 0 || warp < 4, hi = h == 0 || warp >= 4;   // chunks below / from kP2QLo
     if (g >= gmin && g <= gmax) {
       if (lo) {
-        p2q_copy<0>(dst, src);
-        p2q_copy<1>(dst, src);
-        p2q_copy<2>(dst, src);
+        p2q_copy<0, B>(dst, src);
+        p2q_copy<1, B>(dst, src);
+        if (NCH == 5) p2q_copy<2, B>(dst, src);
+        else if (lane < 4) p2q_copy<2, B>(dst, src);
       }
-      if (hi) {
-        p2q_copy<3>(dst, src);
-        if (lane < 4) p2q_copy<4>(dst, src);
+      if (NCH == 5 && hi) {
+        p2q_copy<3, B>(dst, src);
+        if (lane < 4) p2q_copy<4, B>(dst, src);
       }
     } else {
 #pragma unroll 1
-      for (int t = lo ? 0 : 3; t < (hi ? 5 : 3); ++t) {
+      for (int t = lo ? 0 : kP2QLo; t < (hi ? NCH : kP2QLo); ++t) {
         const int col = lane + 32 * t;
         if (col < W && col < lim && col + i0 >= 2) {
-          const unsigned sa = dst + 64 * t;
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + 32 * t));
+          const unsigned sa = dst + 16 * B * t;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(src + 32 * t), "n"(B));
         }
       }
     }
@@ -1315,8 +1348,8 @@ __device__ __forceinline__ void p2q_issue_plane(const P2QStage& st, int slot, co
 // macro faces only at i = 0 (zero set {i}, or {i, diagonal} for a row of one point) and i = len - 1
 // ({diagonal}, or {i, diagonal}): one thread per (plane, row, end) checks and zeroes that point.
 // Rows j = 0 and k = 0 lie on a face: a warp looks up each of their points (p2q_mask_face_row).
-template <int TI>
-__device__ __forceinline__ void p2q_mask_end(float* buf, int slot, int N, uint32_t table, int i0, int j0, int kk, int r,
+template <int TI, typename E>
+__device__ __forceinline__ void p2q_mask_end(E* buf, int slot, int N, uint32_t table, int i0, int j0, int kk, int r,
                                              int end) {
   constexpr int W = TI + 4;
   const int jr = j0 - 2 + r;
@@ -1325,11 +1358,11 @@ __device__ __forceinline__ void p2q_mask_end(float* buf, int slot, int N, uint32
   const bool one = len == 1;
   const int col = end == 0 ? 2 - i0 : len + 1 - i0;   // column of i = 0 / i = len - 1
   const bool dir = (table >> (one ? 3 : (end == 0 ? 2 : 1))) & 1u;
-  if (dir && (unsigned)col < (unsigned)W) buf[slot * (W * kP2TileH) + r * W + p2_scol(col, W)] = 0.0f;
+  if (dir && (unsigned)col < (unsigned)W) buf[slot * (W * kP2TileH) + r * W + p2_scol(col, W)] = E{};
 }
 
-template <int TI>
-__device__ __forceinline__ void p2q_mask_face_row(float* buf, int slot, int N, uint32_t table, int i0, int j0, int kk,
+template <int TI, typename E>
+__device__ __forceinline__ void p2q_mask_face_row(E* buf, int slot, int N, uint32_t table, int i0, int j0, int kk,
                                                   int r) {
   constexpr int W = TI + 4;
   const int lane = threadIdx.x & 31;
@@ -1339,55 +1372,56 @@ __device__ __forceinline__ void p2q_mask_face_row(float* buf, int slot, int N, u
 #pragma unroll 1
   for (int col = lane; col < W; col += 32) {
     const int ii = i0 - 2 + col;
-    if (ii >= 0 && ii < len && on_dirichlet(table, N, ii, jr, kk)) buf[slot * (W * kP2TileH) + r * W + p2_scol(col, W)] = 0.0f;
+    if (ii >= 0 && ii < len && on_dirichlet(table, N, ii, jr, kk)) buf[slot * (W * kP2TileH) + r * W + p2_scol(col, W)] = E{};
   }
 }
 
-template <int W, int NV, int PA, int C>
-__device__ __forceinline__ void p2q_cell(const P2ParamW& wp, const float* const (&pl)[6], int ob,
-                                         float (&acc)[4][NV]) {
+template <class A, int W, int NV, int PA, int C>
+__device__ __forceinline__ void p2q_cell(const typename A::WP& wp, const typename A::E* const (&pl)[6], int ob,
+                                         typename A::E (&acc)[4][NV]) {
   using Cell = P2QCell<PA, C>;
   constexpr int O = Cell::off;
   constexpr int dx = (O & 15) - 2, dy = ((O >> 4) & 15) - 2, dz = ((O >> 8) & 15) - 2;
   constexpr int off = dy * W + (dx & 1) * (W / 2) + ((dx + 4) >> 1) - 2;   // staged column 2 + 2 lane + dx
-  const float* p = pl[dz + 2] + ob + off;
+  const typename A::E* p = pl[dz + 2] + ob + off;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const float xv = p[32 * v];
-    if constexpr (Cell::e0 >= 0) acc[0][v] = fmaf(wp.w[P2QStart<PA, 0>::v + Cell::e0], xv, acc[0][v]);
-    if constexpr (Cell::e1 >= 0) acc[1][v] = fmaf(wp.w[P2QStart<PA, 1>::v + Cell::e1], xv, acc[1][v]);
-    if constexpr (Cell::e2 >= 0) acc[2][v] = fmaf(wp.w[P2QStart<PA, 2>::v + Cell::e2], xv, acc[2][v]);
-    if constexpr (Cell::e3 >= 0) acc[3][v] = fmaf(wp.w[P2QStart<PA, 3>::v + Cell::e3], xv, acc[3][v]);
+    const typename A::E xv = p[32 * v];
+    if constexpr (Cell::e0 >= 0) A::fma(acc[0][v], wp.w[P2QStart<PA, 0>::v + Cell::e0], xv);
+    if constexpr (Cell::e1 >= 0) A::fma(acc[1][v], wp.w[P2QStart<PA, 1>::v + Cell::e1], xv);
+    if constexpr (Cell::e2 >= 0) A::fma(acc[2][v], wp.w[P2QStart<PA, 2>::v + Cell::e2], xv);
+    if constexpr (Cell::e3 >= 0) A::fma(acc[3][v], wp.w[P2QStart<PA, 3>::v + Cell::e3], xv);
   }
 }
 
-template <int W, int NV, int PA, int... C>
-__device__ __forceinline__ void p2q_cells(const P2ParamW& wp, const float* const (&pl)[6], int ob, float (&acc)[4][NV],
-                                          std::integer_sequence<int, C...>) {
-  (p2q_cell<W, NV, PA, C>(wp, pl, ob, acc), ...);
+template <class A, int W, int NV, int PA, int... C>
+__device__ __forceinline__ void p2q_cells(const typename A::WP& wp, const typename A::E* const (&pl)[6], int ob,
+                                          typename A::E (&acc)[4][NV], std::integer_sequence<int, C...>) {
+  (p2q_cell<A, W, NV, PA, C>(wp, pl, ob, acc), ...);
 }
 
 // Points of row j on planes k (length len0) and k+1 (len0 - 1; only if wk1) for row parity PA
 // (of plane k): the interior points among i0 + 64 v + 2 lane + {0, 1}.
-template <int W, int NV, int PA>
-__device__ __forceinline__ void p2q_rows(const P2ParamW& wp, const float* const (&pl)[6], int ob, int i0, int len0,
-                                         bool wk0, bool wk1, float* __restrict__ y0, float* __restrict__ y1) {
+template <class A, int W, int NV, int PA>
+__device__ __forceinline__ void p2q_rows(const typename A::WP& wp, const typename A::E* const (&pl)[6], int ob, int i0,
+                                         int len0, bool wk0, bool wk1, typename A::V* __restrict__ y0,
+                                         typename A::V* __restrict__ y1) {
   const int lane = threadIdx.x & 31;
-  float acc[4][NV];
+  typename A::E acc[4][NV];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[q][v] = 0.0f;
-  p2q_cells<W, NV, PA>(wp, pl, ob, acc, std::make_integer_sequence<int, P2QCnt<PA>::v>{});
+    for (int v = 0; v < NV; ++v) acc[q][v] = typename A::E{};
+  p2q_cells<A, W, NV, PA>(wp, pl, ob, acc, std::make_integer_sequence<int, P2QCnt<PA>::v>{});
   if (i0 > 0 && i0 + 64 * NV + 1 < len0 && wk0 && wk1) {
     // every point of the lane on both planes is off the macro faces
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const int ii = i0 + 64 * v + 2 * lane;
-      y0[ii] = acc[0][v];
-      y0[ii + 1] = acc[1][v];
-      y1[ii] = acc[2][v];
-      y1[ii + 1] = acc[3][v];
+      y0[ii] = A::out(acc[0][v]);
+      y0[ii + 1] = A::out(acc[1][v]);
+      y1[ii] = A::out(acc[2][v]);
+      y1[ii + 1] = A::out(acc[3][v]);
     }
     return;
   }
@@ -1395,37 +1429,43 @@ __device__ __forceinline__ void p2q_rows(const P2ParamW& wp, const float* const 
   for (int v = 0; v < NV; ++v) {
     const int ii = i0 + 64 * v + 2 * lane;
     if (wk0) {
-      if (ii > 0 && ii < len0 - 1) y0[ii] = acc[0][v];
-      if (ii + 1 < len0 - 1) y0[ii + 1] = acc[1][v];
+      if (ii > 0 && ii < len0 - 1) y0[ii] = A::out(acc[0][v]);
+      if (ii + 1 < len0 - 1) y0[ii + 1] = A::out(acc[1][v]);
     }
     if (wk1) {
-      if (ii > 0 && ii < len0 - 2) y1[ii] = acc[2][v];
-      if (ii + 1 < len0 - 2) y1[ii + 1] = acc[3][v];
+      if (ii > 0 && ii < len0 - 2) y1[ii] = A::out(acc[2][v]);
+      if (ii + 1 < len0 - 2) y1[ii + 1] = A::out(acc[3][v]);
     }
   }
 }
 
-template <int W, int PA>
-__device__ __forceinline__ void p2q_step(const P2ParamW& wp, const float* const (&pl)[6], int ob, int i0, int len0,
-                                         bool wk0, bool wk1, float* __restrict__ y0, float* __restrict__ y1) {
+template <class A, int W, int PA>
+__device__ __forceinline__ void p2q_step(const typename A::WP& wp, const typename A::E* const (&pl)[6], int ob, int i0,
+                                         int len0, bool wk0, bool wk1, typename A::V* __restrict__ y0,
+                                         typename A::V* __restrict__ y1) {
   // the second 64 points only when the longer row reaches into them
-  if (len0 - i0 <= 64)
-    p2q_rows<W, 1, PA>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1);
+  if (A::TI == 64 || len0 - i0 <= 64)
+    p2q_rows<A, W, 1, PA>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1);
   else
-    p2q_rows<W, 2, PA>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1);
+    p2q_rows<A, W, A::TI / 64, PA>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1);
 }
 
 // One macro (cm = its constants, stm = its face stencils); blocks after the tile tasks write the
-// macro's face points (4 faces x nfb blocks).
-template <bool DIRICHLET>
-__global__ void __launch_bounds__(256, 3) p2_quad_f32_kernel(const __grid_constant__ P2ParamW wp,
-                                                          const OpConst<float>* __restrict__ cm,
-                                                          const P2Stencil<float>* __restrict__ stm,
-                                                          const P2StencilIndex* __restrict__ sidx,
-                                                          const int4* __restrict__ tasks, int ntasks, int kch, int nfb,
-                                                          const int* __restrict__ pstart, const float* __restrict__ x,
-                                                          float* __restrict__ y, int64_t npts) {
-  constexpr int TI = 128;
+// macro's face points (4 faces x nfb blocks, from x in the vector type).  xs: the staged vector
+// (x itself in FP32, its split pairs in double-float).
+template <class A, bool DIRICHLET>
+__global__ void __launch_bounds__(256, 3) p2_quad_kernel(const __grid_constant__ typename A::WP wp,
+                                                      const OpConst<typename A::V>* __restrict__ cm,
+                                                      const P2Stencil<typename A::V>* __restrict__ stm,
+                                                      const P2StencilIndex* __restrict__ sidx,
+                                                      const int4* __restrict__ tasks, int ntasks, int kch, int nfb,
+                                                      const int* __restrict__ pstart,
+                                                      const typename A::E* __restrict__ xs,
+                                                      const typename A::V* __restrict__ x,
+                                                      typename A::V* __restrict__ y, int64_t npts) {
+  using E = typename A::E;
+  using V = typename A::V;
+  constexpr int TI = A::TI;
   constexpr int W = TI + 4;
   constexpr int SLOT = W * kP2TileH;
   extern __shared__ __align__(16) unsigned char p2_quad_smem_raw[];
@@ -1437,20 +1477,20 @@ __global__ void __launch_bounds__(256, 3) p2_quad_f32_kernel(const __grid_consta
     __syncthreads();
     const int b = blockIdx.x - ntasks;
     const int f = b / nfb;
-    p2_face_point<float, DIRICHLET>(*cm, *stm, offs, starts, pstart, x, y, f, (b - f * nfb) * 256 + threadIdx.x);
+    p2_face_point<V, DIRICHLET>(*cm, *stm, offs, starts, pstart, x, y, f, (b - f * nfb) * 256 + threadIdx.x);
     return;
   }
-  float* buf = reinterpret_cast<float*>(p2_quad_smem_raw);
+  E* buf = reinterpret_cast<E*>(p2_quad_smem_raw);
   const int4 task = tasks[blockIdx.x];
-  const OpConst<float>& c = *cm;
+  const OpConst<V>& c = *cm;
   const int N = c.N;
   const int i0 = task.x * TI, j0 = task.y * kP2TileJ, k0 = task.z * kch;
   const int k_end = min(k0 + kch - 1, N - j0 - i0);
   if (k_end < k0) return;   // uniform over the CTA
   const uint32_t table = c.bnd_table;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float* __restrict__ xm = x + c.base;
-  float* __restrict__ ym = y + c.base;
+  const E* __restrict__ xm = xs + c.base;
+  V* __restrict__ ym = y + c.base;
   const P2QStage st = p2q_plan<TI>(buf, N, i0, j0);
   auto plane_start = [&](int kk) { return (kk >= 0 && kk <= N) ? __ldg(pstart + kk) : 0; };
   // a staged row's W values (first at packed offset g of the macro) lie inside the vector
@@ -1505,16 +1545,16 @@ __global__ void __launch_bounds__(256, 3) p2_quad_f32_kernel(const __grid_consta
     // rows j = 0 and planes k = 0 hold only points on macro faces
     const bool wk0 = k > 0 && k <= k_end, wk1 = k + 1 <= k_end;
     if (j > 0 && len0 > 0 && i0 < len0) {
-      const float* pl[6];
+      const E* pl[6];
 #pragma unroll
       for (int t = 0; t < 6; ++t) pl[t] = buf + slot(t) * SLOT;
-      float* __restrict__ y0 = ym + __ldg(pstart + k) + row32(N - k, j);
-      float* __restrict__ y1 = ym + __ldg(pstart + k + 1) + row32(N - k - 1, j);
+      V* __restrict__ y0 = ym + __ldg(pstart + k) + row32(N - k, j);
+      V* __restrict__ y1 = ym + __ldg(pstart + k + 1) + row32(N - k - 1, j);
       switch ((j & 1) | ((k & 1) << 1)) {
-        case 0: p2q_step<W, 0>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
-        case 1: p2q_step<W, 2>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
-        case 2: p2q_step<W, 4>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
-        default: p2q_step<W, 6>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
+        case 0: p2q_step<A, W, 0>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
+        case 1: p2q_step<A, W, 2>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
+        case 2: p2q_step<A, W, 4>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
+        default: p2q_step<A, W, 6>(wp, pl, ob, i0, len0, wk0, wk1, y0, y1); break;
       }
     }
     sq = slot(2);
@@ -1524,9 +1564,15 @@ __global__ void __launch_bounds__(256, 3) p2_quad_f32_kernel(const __grid_consta
 
 // The two-plane kernel's ring exceeds the default 48 KB of dynamic shared memory.
 static int p2_quad_prepare() {
-  static_assert(kP2QSmem >= sizeof(int) * (kP2StTotal + 9), "face blocks stage the stencil index in the tile's shared memory");
-  HHG_CUDA_TRY(cudaFuncSetAttribute(p2_quad_f32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2QSmem));
-  HHG_CUDA_TRY(cudaFuncSetAttribute(p2_quad_f32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2QSmem));
+  static_assert(p2q_smem<P2QF32>() >= sizeof(int) * (kP2StTotal + 9), "face blocks stage the stencil index in the tile's shared memory");
+  HHG_CUDA_TRY(cudaFuncSetAttribute(p2_quad_kernel<P2QF32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)p2q_smem<P2QF32>()));
+  HHG_CUDA_TRY(cudaFuncSetAttribute(p2_quad_kernel<P2QF32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)p2q_smem<P2QF32>()));
+  HHG_CUDA_TRY(cudaFuncSetAttribute(p2_quad_kernel<P2QDF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)p2q_smem<P2QDF>()));
+  HHG_CUDA_TRY(cudaFuncSetAttribute(p2_quad_kernel<P2QDF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)p2q_smem<P2QDF>()));
   return HHG_OK;
 }
 
@@ -1741,6 +1787,44 @@ const T* field_ptr(const hhg_op* op) {
 
 static inline int64_t tri_host(int64_t s) { return (s + 1) * (s + 2) / 2; }
 
+// The two-plane P2 kernel over every macro of the op: one launch per macro (its weights w[m] in the
+// parameter bank), on the caller's stream or, for several macros, side by side on the op's streams
+// (a launch per macro alone leaves the GPU part empty while its last tiles run), forked from and
+// joined back into the caller's stream.
+template <class A>
+static int launch_p2_quad(const hhg_op* op, const typename A::WP* w, const typename A::E* xs, const typename A::V* x,
+                          typename A::V* y, cudaStream_t s) {
+  using V = typename A::V;
+  const Interface* I = op->itf;
+  const int nm = op->mesh->nmacro();
+  const OpConst<V>* cst = (const OpConst<V>*)(sizeof(V) == 8 ? op->d_const64 : op->d_const32);
+  const P2Stencil<V>* st = (const P2Stencil<V>*)(sizeof(V) == 8 ? op->d_p2st64 : op->d_p2st32);
+  const TileTasks& tt = I->tile[A::TI == 128 ? 0 : 2];
+  const P2StencilIndex* ix = (const P2StencilIndex*)op->d_p2idx;
+  const int nfb = (int)((tri_host(op->N) + 255) / 256);
+  const unsigned grid = (unsigned)(tt.n + 4 * nfb);
+  const int ns = (int)op->aux_streams.size();
+  if (ns > 0) {
+    HHG_CUDA_TRY(cudaEventRecord(op->aux_events[0], s));
+    for (int i = 0; i < ns; ++i) HHG_CUDA_TRY(cudaStreamWaitEvent(op->aux_streams[i], op->aux_events[0], 0));
+  }
+  for (int m = 0; m < nm; ++m) {
+    const cudaStream_t sm = ns > 0 ? op->aux_streams[m % ns] : s;
+    if (op->bc == HHG_DIRICHLET)
+      p2_quad_kernel<A, true><<<grid, 256, p2q_smem<A>(), sm>>>(w[m], cst + m, st + m, ix, tt.d, (int)tt.n, tt.kchunk,
+                                                                nfb, I->d_pstart, xs, x, y, op->npts);
+    else
+      p2_quad_kernel<A, false><<<grid, 256, p2q_smem<A>(), sm>>>(w[m], cst + m, st + m, ix, tt.d, (int)tt.n, tt.kchunk,
+                                                                 nfb, I->d_pstart, xs, x, y, op->npts);
+    HHG_CUDA_TRY(cudaGetLastError());
+  }
+  for (int i = 0; i < ns; ++i) {
+    HHG_CUDA_TRY(cudaEventRecord(op->aux_events[1 + i], op->aux_streams[i]));
+    HHG_CUDA_TRY(cudaStreamWaitEvent(s, op->aux_events[1 + i], 0));
+  }
+  return HHG_OK;
+}
+
 template <typename T>
 int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
   const int64_t V = lattice_size(op->N);
@@ -1754,16 +1838,16 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
       // FP64 vectors in double-float arithmetic: split x once, then the stencil on the FP32 pipes
       const int64_t n = op->npts;
       split_double_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
-          n, (const double*)x, (float2*)op->d_p1df_x);
+          n, (const double*)x, (float2*)op->d_dfx);
       dim3 grid((unsigned)I->ncta, nm);
       if (op->bc == HHG_DIRICHLET)
         p1_gather_df_kernel<true><<<grid, 256, 0, s>>>((const OpConst<double>*)op->d_const64, (const float2*)op->d_p1df,
                                                        I->d_cta_plane, I->d_cta_start, I->d_pstart, (const double*)x,
-                                                       (const float2*)op->d_p1df_x, (double*)y);
+                                                       (const float2*)op->d_dfx, (double*)y);
       else
         p1_gather_df_kernel<false><<<grid, 256, 0, s>>>((const OpConst<double>*)op->d_const64, (const float2*)op->d_p1df,
                                                         I->d_cta_plane, I->d_cta_start, I->d_pstart, (const double*)x,
-                                                        (const float2*)op->d_p1df_x, (double*)y);
+                                                        (const float2*)op->d_dfx, (double*)y);
       HHG_CUDA_TRY(cudaGetLastError());
       return HHG_OK;
     }
@@ -1795,43 +1879,22 @@ int launch_apply(const hhg_op* op, const T* x, T* y, cudaStream_t s) {
     return HHG_OK;
   }
   // P2 constant coefficient: stencil rows (28.75 FMA per point against about 74 in element form)
-  // from shared-memory plane tiles.  FP32: two planes per step, one launch per macro with its
-  // weights in the parameter bank (p2_quad_f32_kernel); small lattices in FP32, the coarse levels of
-  // mixed-precision multigrid, run one marching launch instead (there a launch costs more than the
-  // work).  FP64: one plane per step, all macros in one launch (p2_tile_kernel; in FP64 the few CTAs
-  // of a small march would leave the FP64 pipes of most SMs idle).
-  if constexpr (sizeof(T) == 4) {
-    if (op->kind == HHG_DIFFUSION && op->degree == 2 && op->coeff.type == HHG_COEFF_CONST && op->d_p2st64 &&
-        op->N > 32) {
-      const Interface* I = op->itf;
-      const P2Stencil<float>* st = (const P2Stencil<float>*)op->d_p2st32;
-      const OpConst<float>* cf = (const OpConst<float>*)op->d_const32;
-      const TileTasks& tt = I->tile[0];
-      const P2StencilIndex* ix = (const P2StencilIndex*)op->d_p2idx;
-      const int nfb = (int)((tri_host(op->N) + 255) / 256);
-      const unsigned grid = (unsigned)(tt.n + 4 * nfb);
-      // one macro: the caller's stream; several: the op's streams side by side (a launch per macro
-      // alone leaves the GPU part empty while its last tiles run)
-      const int ns = (int)op->aux_streams.size();
-      if (ns > 0) {
-        HHG_CUDA_TRY(cudaEventRecord(op->aux_events[0], s));
-        for (int i = 0; i < ns; ++i) HHG_CUDA_TRY(cudaStreamWaitEvent(op->aux_streams[i], op->aux_events[0], 0));
-      }
-      for (int m = 0; m < nm; ++m) {
-        const cudaStream_t sm = ns > 0 ? op->aux_streams[m % ns] : s;
-        if (op->bc == HHG_DIRICHLET)
-          p2_quad_f32_kernel<true><<<grid, 256, kP2QSmem, sm>>>(op->h_p2w32[m], cf + m, st + m, ix, tt.d, (int)tt.n,
-                                                                tt.kchunk, nfb, I->d_pstart, x, y, op->npts);
-        else
-          p2_quad_f32_kernel<false><<<grid, 256, kP2QSmem, sm>>>(op->h_p2w32[m], cf + m, st + m, ix, tt.d, (int)tt.n,
-                                                                 tt.kchunk, nfb, I->d_pstart, x, y, op->npts);
+  // from shared-memory plane tiles.  FP32 and double-float: two planes per step, one launch per macro
+  // with its weights in the parameter bank (p2_quad_kernel); small lattices, the coarse levels of
+  // multigrid, run one marching launch (FP32) or the FP64 tile kernel instead (there a launch costs
+  // more than the work).  FP64: one plane per step, all macros in one launch (p2_tile_kernel; in
+  // FP64 the few CTAs of a small march would leave the FP64 pipes of most SMs idle).
+  if (op->kind == HHG_DIFFUSION && op->degree == 2 && op->coeff.type == HHG_COEFF_CONST && op->d_p2st64 &&
+      op->N > 32) {
+    if constexpr (sizeof(T) == 4) return launch_p2_quad<P2QF32>(op, op->h_p2w32.data(), x, x, y, s);
+    if constexpr (sizeof(T) == 8) {
+      if (!op->h_p2wdf.empty()) {
+        const int64_t n = op->npts;
+        split_double_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+            n, (const double*)x, (float2*)op->d_dfx);
         HHG_CUDA_TRY(cudaGetLastError());
+        return launch_p2_quad<P2QDF>(op, op->h_p2wdf.data(), (const float2*)op->d_dfx, x, y, s);
       }
-      for (int i = 0; i < ns; ++i) {
-        HHG_CUDA_TRY(cudaEventRecord(op->aux_events[1 + i], op->aux_streams[i]));
-        HHG_CUDA_TRY(cudaStreamWaitEvent(s, op->aux_events[1 + i], 0));
-      }
-      return HHG_OK;
     }
   }
   if constexpr (sizeof(T) == 8) {
@@ -1891,7 +1954,7 @@ hhg_op::~hhg_op() {
   cudaFree(d_elem);
   cudaFree(d_face);
   cudaFree(d_p1df);
-  cudaFree(d_p1df_x);
+  cudaFree(d_dfx);
   for (cudaStream_t t : aux_streams) cudaStreamDestroy(t);
   for (cudaEvent_t e : aux_events) cudaEventDestroy(e);
 }
@@ -2095,37 +2158,52 @@ extern "C" int hhg_op_set_fp64_arith(hhg_op_t* op, int mode) {
   clear_error();
   if (!op) return fail(HHG_E_ARG, "set_fp64_arith: null op");
   if (mode != HHG_FP64_NATIVE && mode != HHG_FP64_DOUBLE_FLOAT) return fail(HHG_E_ARG, "set_fp64_arith: bad mode");
+  const bool set = op->d_dfx != nullptr;
   if (mode == HHG_FP64_NATIVE) {
-    if (op->d_p1df) {
+    if (set) {
       HHG_CUDA_TRY(cudaDeviceSynchronize());   // no apply in flight may still read them
       cudaFree(op->d_p1df);
-      cudaFree(op->d_p1df_x);
+      cudaFree(op->d_dfx);
     }
-    op->d_p1df = op->d_p1df_x = nullptr;
+    op->d_p1df = op->d_dfx = nullptr;
+    op->h_p2wdf.clear();
     return HHG_OK;
   }
-  if (!(op->kind == HHG_DIFFUSION && op->degree == 1 && op->coeff.type == HHG_COEFF_CONST))
-    return fail(HHG_E_UNSUPPORTED, "set_fp64_arith: double-float arithmetic exists for P1 constant-coefficient "
+  const bool p1 = op->kind == HHG_DIFFUSION && op->degree == 1 && op->coeff.type == HHG_COEFF_CONST;
+  const bool p2 = op->kind == HHG_DIFFUSION && op->degree == 2 && op->coeff.type == HHG_COEFF_CONST && op->d_p2st64;
+  if (!p1 && !p2)
+    return fail(HHG_E_UNSUPPORTED, "set_fp64_arith: double-float arithmetic exists for P1 and P2 constant-coefficient "
                                    "diffusion only");
-  if (op->d_p1df) return HHG_OK;
-  // stencil weights split into FP32 pairs per macro, and the scratch of the split input vector
+  if (set) return HHG_OK;
+  // the weights split into FP32 pairs per macro (hi = the value rounded to FP32, lo = the rest), and
+  // the scratch of the split input vector
   const int nm = op->mesh->nmacro();
-  std::vector<float2> w(16 * (size_t)nm, make_float2(0.0f, 0.0f));
-  for (int m = 0; m < nm; ++m)
-    for (int d = 0; d < 15; ++d) {
-      const double v = op->h_const[m].S[d];
-      const float hi = (float)v;
-      w[16 * m + d] = make_float2(hi, (float)(v - (double)hi));
-    }
+  auto split = [](double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  };
   void *dw = nullptr, *dx = nullptr;
-  HHG_CUDA_TRY(cudaMalloc(&dw, sizeof(float2) * w.size()));
+  std::vector<hhg::P2ParamWDF> w2;
+  if (p1) {
+    std::vector<float2> w(16 * (size_t)nm, make_float2(0.0f, 0.0f));
+    for (int m = 0; m < nm; ++m)
+      for (int d = 0; d < 15; ++d) w[16 * m + d] = split(op->h_const[m].S[d]);
+    HHG_CUDA_TRY(cudaMalloc(&dw, sizeof(float2) * w.size()));
+    HHG_CUDA_TRY(cudaMemcpy(dw, w.data(), sizeof(float2) * w.size(), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<P2Stencil<double>> w64(nm);
+    HHG_CUDA_TRY(cudaMemcpy(w64.data(), op->d_p2st64, sizeof(P2Stencil<double>) * nm, cudaMemcpyDeviceToHost));
+    w2.resize(nm);
+    for (int m = 0; m < nm; ++m)
+      for (int t = 0; t < kP2StTotal; ++t) w2[m].w[t] = split(w64[m].w[0][t]);
+  }
   if (cudaMalloc(&dx, sizeof(float2) * (size_t)op->npts) != cudaSuccess) {
     cudaFree(dw);
     return fail(HHG_E_OOM, "set_fp64_arith: no device memory for the split vector");
   }
-  HHG_CUDA_TRY(cudaMemcpy(dw, w.data(), sizeof(float2) * w.size(), cudaMemcpyHostToDevice));
   op->d_p1df = dw;
-  op->d_p1df_x = dx;
+  op->d_dfx = dx;
+  op->h_p2wdf = std::move(w2);
   return HHG_OK;
 }
 

@@ -34,7 +34,7 @@ def main():
     ap.add_argument("--op", default="apply", choices=["apply", "adjoint", "diagonal", "mg"])
     ap.add_argument("--mixed", type=int, default=1, help="--op mg: FP32 cycles inside FP64 refinement (1) or all FP64 (0)")
     ap.add_argument("--fp64-arith", default="native", choices=["native", "double_float"],
-                    help="arithmetic of FP64 applies (double_float: P1 constant coefficient only)")
+                    help="arithmetic of FP64 applies (double_float: P1 and P2 constant coefficient)")
     args = ap.parse_args()
 
     import torch

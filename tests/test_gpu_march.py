@@ -68,6 +68,27 @@ def test_p2_const_parity_large(meshname, level, bc, dtype):
     assert spread == 0.0
 
 
+@pytest.mark.parametrize("meshname,level", [("reference_tet", 3), ("reference_tet", 5), ("cube6", 5), ("cuboid36", 3)])
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_p2_const_double_float_parity(meshname, level, bc):
+    """P2 constant coefficient with FP64 vectors and the arithmetic in FP32 pairs (the two-plane kernel
+    from 64 intervals per edge on, FP64 below) meets the FP64 tolerance against the oracle; switching
+    back to native FP64 gives the FP64 kernel's result again."""
+    from gpu_helpers import Case, rel_err
+    import paper_2404_08371_gb300 as hhg
+    c = Case(meshname, level, 2)
+    op = hhg.Operator(c.mesh, degree=2, coeff=("const", 0.8), bc=bc, quad_degree=QD[2])
+    xg = W.uniform(c.S.ndof, seed=5)
+    x = c.packed(xg)
+    y_native = op.apply(x).clone()
+    y = op.set_fp64_arith("double_float").apply(x)
+    ref = OA.diffusion_matrix(c.S, ("const", 0.8), QD[2], bc) @ xg
+    got, spread = c.unpack(y)
+    assert rel_err(got, ref) <= TOL[torch.float64], rel_err(got, ref)
+    assert spread == 0.0
+    assert torch.equal(op.set_fp64_arith("native").apply(x), y_native)
+
+
 @pytest.mark.parametrize("meshname,level", [("reference_tet", 2), ("cube6", 1), ("cube48", 1)])
 @pytest.mark.parametrize("degree,kind", [(1, "sin3"), (1, "field"), (2, "const"), (2, "sin3"), (2, "field")])
 @pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
@@ -278,6 +299,23 @@ def test_bench_legs_full_size_sampled(degree, coeff, level, stored, dtype):
     ref = OA.sampled_diffusion_rows(v[t[0]], level, degree, lc, QD[degree], "dirichlet", xp, pts)
     tol = 1e-12 if dtype == torch.float64 else 1e-5
     assert np.abs(y[sample] - ref).max() <= tol * np.abs(y).max(), np.abs(y[sample] - ref).max() / np.abs(y).max()
+
+
+def test_p2_const_double_float_level8_sampled():
+    """The double-float P2 constant-coefficient apply at the bench's size (level 8, 22.6 M points):
+    sampled rows against the oracle's per-point sums at the FP64 tolerance."""
+    import paper_2404_08371_gb300 as hhg
+    v, t = W.reference_tet()
+    level, degree = 8, 2
+    mesh = hhg.Mesh(v, t, level)
+    op = hhg.Operator(mesh, degree=2, coeff=("const", 1.0), bc="dirichlet", quad_degree=QD[2])
+    op.set_fp64_arith("double_float")
+    n = mesh.vec_size(2)
+    xp = W.uniform(n, seed=13)
+    y = op.apply(torch.tensor(xp, device="cuda")).cpu().numpy()
+    sample, pts = _sampled_points(degree * 2 ** level, n, np.random.default_rng(14))
+    ref = OA.sampled_diffusion_rows(v[t[0]], level, degree, ("const", 1.0), QD[2], "dirichlet", xp, pts)
+    assert np.abs(y[sample] - ref).max() <= 1e-12 * np.abs(y).max(), np.abs(y[sample] - ref).max() / np.abs(y).max()
 
 
 @pytest.mark.parametrize("case", ["p2_sin3_f64_level8_apply", "p1_sin3_f32_level8_apply", "p1_field_f64_level7_adjoint",

@@ -217,6 +217,6 @@ def test_double_float_refused_for_other_operators():
     import paper_2404_08371_gb300 as hhg
     v, t = W.reference_tet()
     mesh = hhg.Mesh(v, t, 2)
-    op = hhg.Operator(mesh, degree=2, coeff=("const", 1.0), bc="dirichlet")
-    with pytest.raises(RuntimeError, match="P1 constant"):
+    op = hhg.Operator(mesh, degree=2, coeff=("sin3",), bc="dirichlet", quad_degree=4)
+    with pytest.raises(RuntimeError, match="P1 and P2 constant"):
         op.set_fp64_arith("double_float")
