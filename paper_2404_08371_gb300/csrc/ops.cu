@@ -721,7 +721,7 @@ __device__ __forceinline__ void p1_climb_row(float (&v)[SHI - SLO + 1][PT], cons
 // DRAM latency: the three rows that step k + kClimbAhead loads are prefetched into L2 at step k
 // (0 or 1: no prefetch).  The window [ib-1, ib+32 PT] spans at most PT + 2 lines of 32 floats;
 // lane l <= PT + 1 touches the line at offset min(32 l, 32 PT + 1).
-constexpr int kClimbAhead = 3;
+constexpr int kClimbAhead = 2;
 
 __device__ __forceinline__ void p1_climb_prefetch(const float* a) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
