@@ -102,9 +102,8 @@ constexpr int kMarchWarps = 8;
 constexpr int kMarchJAtomicN = 64;
 __host__ __device__ constexpr int march_iw(int n) { return n >= kMarchJAtomicN ? 32 : 31; }
 __host__ __device__ constexpr int march_jw(int n) { return n >= kMarchJAtomicN ? kMarchWarps : kMarchWarps - 1; }
-// Tile of the P1 stencil kernel (ops.cu): 8 warps = 8 rows j, 32 lanes x kStencilV points along i.
+// Rows j of the plane-tile tasks (ops.cu): one per warp of an 8-warp CTA.
 constexpr int kStencilWarps = 8;
-constexpr int kStencilV = 4;
 
 // Quadrature rule on the reference tetrahedron (volume 1/6).
 struct QuadRule {
