@@ -318,6 +318,41 @@ def test_p2_const_double_float_level8_sampled():
     assert np.abs(y[sample] - ref).max() <= 1e-12 * np.abs(y).max(), np.abs(y[sample] - ref).max() / np.abs(y).max()
 
 
+@pytest.mark.parametrize("arith", ["f32", "double_float"])
+def test_p2_const_multi_macro_level7_sampled(arith):
+    """The two-plane P2 kernel on the cube of 6 macros at level 7 (256 intervals per edge), one launch
+    per macro on the op's streams: sampled rows off the macro faces of every macro against the
+    oracle's per-point sums on that macro alone (Neumann, so an interior row sums only its own
+    macro's micro-tets and reads only its own copy of the face points)."""
+    import paper_2404_08371_gb300 as hhg
+    from oracle import mesh as OM
+    v, t = W.cube6()
+    level, degree = 7, 2
+    N = degree * 2 ** level
+    mesh = hhg.Mesh(v, t, level)
+    op = hhg.Operator(mesh, degree=2, coeff=("const", 1.3), bc="neumann", quad_degree=QD[2])
+    dtype = torch.float32 if arith == "f32" else torch.float64
+    if arith == "double_float":
+        op.set_fp64_arith("double_float")
+    n = mesh.vec_size(2)
+    V = n // len(t)
+    xp = W.uniform(n, seed=21)
+    if dtype == torch.float32:
+        xp = xp.astype(np.float32).astype(np.float64)
+    y = op.apply(torch.tensor(xp, dtype=dtype, device="cuda")).double().cpu().numpy()
+    pts = OM.lattice_points(N)
+    inner = np.nonzero((pts.min(axis=1) >= 1) & (pts.sum(axis=1) <= N - 1))[0]
+    rng = np.random.default_rng(22)
+    tol = 1e-12 if arith == "double_float" else 1e-5
+    for m in range(len(t)):
+        sample = rng.choice(inner, 150, replace=False)
+        ref = OA.sampled_diffusion_rows(v[t[m]], level, degree, ("const", 1.3), QD[2], "neumann",
+                                        xp[m * V:(m + 1) * V], pts[sample])
+        got = y[m * V + sample]
+        scale = np.abs(y[m * V:(m + 1) * V]).max()
+        assert np.abs(got - ref).max() <= tol * scale, (m, np.abs(got - ref).max() / scale)
+
+
 @pytest.mark.parametrize("case", ["p2_sin3_f64_level8_apply", "p1_sin3_f32_level8_apply", "p1_field_f64_level7_adjoint",
                                   "p2_sin3_f64_level7_diag", "n1_cube6_level6_apply"])
 def test_march_bitwise_repeatable(case):
