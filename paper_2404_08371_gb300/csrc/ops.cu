@@ -1168,7 +1168,7 @@ __global__ void __launch_bounds__(256) p2_tile_kernel(const OpConst<T>* __restri
 // time).  The ring holds 10 planes: at step k the planes k-2 .. k+3 are read, k+4 and k+5 (landed)
 // get their Dirichlet points zeroed, k+6 and k+7 are being copied; one barrier per step.
 constexpr int kP2QRing = 10;
-constexpr int kP2QStreams = 4;   // streams the per-macro launches of a multi-macro apply share
+constexpr int kP2QStreams = 8;   // streams the per-macro launches of a multi-macro apply share
 
 // FP32: 128-point tiles, staged values and weights in FP32.
 struct P2QF32 {
